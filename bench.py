@@ -1,0 +1,328 @@
+"""Benchmark of the nucleon MD hot path on one B300 (or N replicas).
+
+Default workload: the 409,600-nucleon run (Yp = 0.40, T = 0.5 MeV, start
+density 0.080 fm^-3 with the box growing at xi = 7.5e-5 c/fm, FP32 pair
+arithmetic / FP64 state, pair lists rebuilt within 10 steps with a 1 fm
+skin, thermostat every 100 steps, energies every step, final cluster
+analysis).  One timed "step" is one pass of the whole hot path: kick-drift,
+rebuild decision (and rebuild when due), pair forces with energies, kick,
+box growth and thermostat; the cluster analysis runs once at the end of the
+timed region and its time is included.
+
+Prints one JSON line (see the keys below).  Timing: CUDA events on the
+library's stream around every step, with an L2 flush (a 256 MB write,
+larger than the 126 MB L2) between timed steps, outside the events.
+
+--impl reference times the FP64 CPU oracle on this host's cores on a bounded
+sample of the same workload (forces on a contiguous range of targets against
+all sources, plus their Verlet update).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+MEASURED = ROOT / "MEASURED_PEAKS.json"
+TRAFFIC = ROOT / "profiles" / "force_split_409600_traffic.json"
+FORCE_SRC = ROOT / "paper_1412_8502_b300" / "csrc" / "k_force.cu"
+
+WORKLOADS = {
+    "md409600": dict(N=409600, Yp=0.40, T=0.5, rho=0.080, seed=3, xi=7.5e-5,
+                     desc="409,600 nucleons, Yp=0.40, T=0.5 MeV, rho 0.080 fm^-3 expanding at 7.5e-5 c/fm "
+                          "(to 0.00125 over 20,000 steps), split FP32/FP64, 1 fm skin, rebuild <= 10 steps"),
+    "md51200": dict(N=51200, Yp=0.30, T=1.0, rho=0.080, seed=2, xi=7.5e-5,
+                    desc="51,200 nucleons, Yp=0.30, T=1.0 MeV, rho 0.080 fm^-3 expanding at 7.5e-5 c/fm"),
+    "md2000": dict(N=2000, Yp=0.30, T=1.0, rho=0.080, seed=1, xi=0.0,
+                   desc="2,000 nucleons, Yp=0.30, T=1.0 MeV, rho 0.080 fm^-3, no expansion"),
+}
+
+# nominal algorithmic FP32 flops per in-range ordered pair (FMA = 2 flops;
+# the ex2 / rsqrt special-function operations are not counted)
+FLOP_NUC, FLOP_COUL = 20.0, 30.0
+SMS, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), hw=f[5], hwt=f[6], swt=f[7], pcap=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = sorted(r["sm"] for r in rows)
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                            ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": rows[0]["smax"], "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    if MEASURED.exists():
+        return json.loads(MEASURED.read_text()), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def force_traffic():
+    """DRAM bytes per force launch from the committed ncu summary, if the
+    force kernel source is unchanged since it was taken."""
+    if not TRAFFIC.exists():
+        return None
+    d = json.loads(TRAFFIC.read_text())
+    sha = hashlib.sha256(FORCE_SRC.read_bytes()).hexdigest()[:16]
+    return d.get("dram_bytes_per_launch") if d.get("k_force_sha") == sha else None
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1412_8502_b300 import md
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    W = WORKLOADS[args.workload]
+    N = W["N"]
+    p = md.md_params_default()
+    p.energy_every = 1
+    p.T = W["T"]
+    sys_ = md.System(N, W["Yp"], W["rho"], W["T"], W["seed"] + 1000 * rank, p)
+    stream = torch.cuda.Stream()
+    sys_.set_stream(stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sys_.step(1, W["xi"])
+    torch.cuda.synchronize()
+    sys_.set_timing(True)
+    launches0 = sys_.info()["launches"]
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K + 1)]
+    pairs_nuc = pairs_coul = 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(K):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                evs[k][0].record(stream)
+                sys_.step(1, W["xi"])
+                evs[k][1].record(stream)
+            e = sys_.step_energy()
+            pairs_nuc += e["pairs_nuc"]
+            pairs_coul += e["pairs_coul"]
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            evs[K][0].record(stream)
+            _, hA, hZ, cst = sys_.clusters(labels=False)
+            evs[K][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs[:K]]
+    cl_ms = evs[K][0].elapsed_time(evs[K][1])
+    total_ms = sum(step_ms) + cl_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    launches = sys_.info()["launches"] - launches0 + 6   # + the cluster kernels
+    kt = sys_.kernel_times()
+    sys_.set_timing(False)
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        xs = torch.empty((N, 3), dtype=torch.float64, pin_memory=True).numpy()
+        vs = torch.empty((N, 3), dtype=torch.float64, pin_memory=True).numpy()
+        st = sys_.state(out=(xs, vs))
+        Ke = max(3, min(K, 20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            sys_.set_state(xs, vs, st["L"], L_base=st["L_base"], t=st["t"], t_base=st["t_base"],
+                           xi_dot=st["xi_dot"], step=st["step"])
+            sys_.step(1, W["xi"])
+            st = sys_.state(out=(xs, vs))
+            sys_.step_energy()
+        wall = time.perf_counter() - t0
+        e2e = {"value": N * Ke / wall, "unit": "nucleon-steps/s", "h2d_bytes_per_step": 2 * 24 * N,
+               "d2h_bytes_per_step": 2 * 24 * N + 8 * 9, "steps": Ke,
+               "note": "per step: md_set_state from pinned host x,v; md_step; md_get_state to pinned host; "
+                       "md_step_energy"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+
+    force_ms, force_n = kt.get("force", (0, 0.0))[1], kt.get("force", (0, 0.0))[0]
+    peaks, src = measured_peaks()
+    flops = FLOP_NUC * pairs_nuc + FLOP_COUL * pairs_coul
+    fp32_peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12          # TFLOP/s at max clock
+    achieved = flops / (force_ms * 1e-3) / 1e12 if force_ms > 0 else None
+    line = {
+        "metric": "nucleon-steps/s",
+        "value": world * N * K / (total_ms * 1e-3),
+        "unit": "nucleon-steps/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 pair math / f64 state",
+        "data": "synthetic: seeded uniform positions + 500 steepest-descent iterations, Maxwell velocities",
+        "config": {"workload": W["desc"], "N": N, "Yp": W["Yp"], "T_MeV": W["T"], "rho_start": W["rho"],
+                   "xi_dot": W["xi"], "window": "first steps of the expansion (densest, slowest)",
+                   "clusters": "one cluster analysis inside the timed region",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "kernel": "k_force_split", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": (achieved / fp32_peak) if achieved else None,
+                     "traffic": force_traffic(),
+                     "peak_note": "FP32 FMA issue peak 148 SM x 128 lanes x 2 flop x 2032 MHz (derived; "
+                                  "MEASURED_PEAKS has no FP32 figure)",
+                     "algorithmic": {"pairs_nuc_per_step": pairs_nuc / K, "pairs_coul_per_step": pairs_coul / K,
+                                     "flop_per_pair": {"nuclear": FLOP_NUC, "coulomb": FLOP_COUL},
+                                     "force_ms_per_launch": force_ms / max(force_n, 1)}},
+        "kernel_ms_per_step": {k: v[1] / max(K, 1) for k, v in kt.items()},
+        "step_ms_p50": sorted(step_ms)[len(step_ms) // 2],
+        "step_ms_p99": sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)],
+        "cluster_ms": cl_ms,
+        "clusters": {"n": cst["n_clusters"], "m_free_n": cst["m_free_n"]},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "peaks_source": src,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(W, args.cpu_seconds)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+# ------------------------------------------------------------------ oracle
+def cpu_baseline(W, seconds):
+    """The FP64 oracle, as it stands, on this host's cores: forces on a
+    contiguous range of targets against all N sources, plus their Verlet
+    update, at the workload's start state (seeded uniform positions)."""
+    import numpy as np
+    import oracle
+
+    N = W["N"]
+    p = oracle.params(min(40.0, 0.5 * (N / W["rho"]) ** (1 / 3)))
+    x, v, t, L = oracle.init(N, W["Yp"], W["rho"], W["T"], W["seed"], p)
+    n = 16
+    t0 = time.perf_counter()
+    oracle.forces(x, t, L, p, 0, n)
+    dt = time.perf_counter() - t0
+    n = int(max(16, min(N, n * seconds / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    F, _ = oracle.forces(x, t, L, p, 0, n)
+    h = 0.5 * 2.0 / 939.0
+    vv = v[:n] + h * F[:n]
+    xx = x[:n] + 2.0 * vv
+    _ = xx.sum()
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n / dt, "unit": "nucleon-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} targets x {N} sources (brute-force FP64 pair sum + Verlet update), "
+                      f"{dt:.1f} s, start density"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    W = WORKLOADS[args.workload]
+    per = max(2.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(W, per)
+    vals = [cpu_baseline(W, per) for _ in range(args.steps)]
+    v = sum(x["value"] for x in vals) / len(vals)
+    return {"impl": "reference", "metric": "nucleon-steps/s", "value": v, "unit": "nucleon-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * W["N"] / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": W["desc"], "N": W["N"]},
+            "cpu_baseline": {"value": v, "unit": "nucleon-steps/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "nucleon-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="md409600", choices=list(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * md.h -- C ABI of the B300 (sm_103a) nucleon molecular-dynamics library.
+ *
+ * Method: Caplan, Schneider, Horowitz & Berry, "Pasta Nucleosynthesis:
+ * Molecular dynamics simulations of nuclear statistical equilibrium"
+ * (arXiv:1412.8502).  Point protons and neutrons in a periodic cube interact
+ * through the Eq. (1) potentials (Table I constants, screening length fixed
+ * at 10 fm, Sec. II.A); positions and velocities advance by velocity Verlet,
+ * the box side grows as Eq. (3) without rescaling positions, and velocities
+ * are rescaled to 3/2 kT per particle every 100 steps (Sec. II.A).  Nuclei
+ * are found by the distance-linkage cluster algorithm of Sec. II.C.
+ *
+ * Conventions for every call:
+ *  - Units: fm, MeV, fm/c (c = k_B = 1).
+ *  - Return value: MD_OK (0) or a negative MD_E* code; md_last_error()
+ *    returns a message for the calling thread's last failure.
+ *  - The library owns all device memory.  Host buffers belong to the caller,
+ *    who sizes them as documented; the library never keeps a host pointer
+ *    after the call returns.
+ *  - Particle arrays on the host are particle-major: x[3*i + a] is axis a of
+ *    particle i, in the ORIGINAL particle order.  Particles 0 .. Np-1 are
+ *    protons and Np .. N-1 neutrons, Np = floor(Yp*N + 0.5).
+ *  - There is no CPU fallback: without a usable CUDA device md_create
+ *    returns MD_ENODEV.
+ *  - A handle may be used by one host thread at a time.
+ */
+#ifndef PASTA_MD_H
+#define PASTA_MD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MD_API __attribute__((visibility("default")))
+#else
+#define MD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MD_OK 0
+#define MD_EINVAL (-1)    /* invalid argument */
+#define MD_ENOMEM (-2)    /* device allocation failed or HBM budget exceeded */
+#define MD_ECUDA (-3)     /* a CUDA runtime call failed */
+#define MD_ETIMEOUT (-4)  /* a bounded device or host wait gave up */
+#define MD_ENUMERIC (-5)  /* a non-finite force or energy was produced */
+#define MD_ENODEV (-6)    /* no CUDA device */
+#define MD_EAGAIN (-7)    /* md_server_poll: no finished job yet */
+
+#define MD_PREC_SPLIT 0   /* FP32 pair arithmetic, FP64 state and reductions */
+#define MD_PREC_FP64 1    /* FP64 everywhere (validation mode) */
+
+typedef struct md_system md_system;
+typedef struct md_batch md_batch;
+typedef struct md_server md_server;
+
+/* Tunable parameters.  md_params_default() fills the paper's values. */
+typedef struct {
+    double dt;               /* time step, fm/c (Sec. III: 2 fm/c) */
+    double r_nuc;            /* nuclear cutoff, fm (Sec. II.A: 11.5) */
+    double r_C;              /* Coulomb cutoff, fm; <= 0 means min(40, L0/2).
+                                Must not exceed L0/2 (MD_EINVAL). */
+    double lambda_s;         /* Coulomb screening length, fm (Sec. II.A: 10) */
+    double skin;             /* pair-list skin, fm (default 1) */
+    int64_t rebuild_every;   /* rebuild pair lists at least every k steps (10) */
+    int64_t thermostat_every;/* velocity rescale period in steps (100); 0 = off */
+    double T;                /* rescale temperature, MeV (md_create sets it) */
+    int32_t precision;       /* MD_PREC_SPLIT (default) or MD_PREC_FP64 */
+    int32_t coulomb;         /* 1 = include the screened Coulomb term (default) */
+    double r_pp, r_np;       /* cluster link radii, fm (Sec. II.C: 4.5, 3) */
+    int64_t relax_iters;     /* steepest-descent iterations in md_create (500) */
+    double relax_gamma;      /* steepest-descent step, fm^2/MeV (0.002) */
+    double relax_dmax;       /* per-iteration displacement clamp, fm (0.1) */
+    int64_t energy_every;    /* md_step records energies every k steps; 0 = off */
+    int32_t sort_bits;       /* spatial-sort bits per axis, 2..7; 0 = from N */
+    int32_t reserved0;
+} md_params;
+
+typedef struct {
+    double KE;       /* 1/2 M sum v^2 */
+    double PE_nuc;   /* sum over pairs i<j of the nuclear part of Eq. (1) */
+    double PE_coul;  /* sum over proton pairs i<j of the screened Coulomb part */
+    double virial;   /* sum over pairs i<j of (x_i - x_j) . F_ij */
+    double L;        /* box side the energies were evaluated with */
+    double t;        /* simulated time, fm/c */
+    int64_t step;    /* steps taken since md_create */
+    int64_t pairs_nuc;   /* ordered pairs inside r_nuc in that force pass */
+    int64_t pairs_coul;  /* ordered proton pairs inside r_C in that pass */
+} md_energy_t;
+
+/* State exchange (md_get_state / md_set_state).  The caller owns x, v
+ * ([N][3] doubles, original order) and type ([N], 1 = proton); any of the
+ * three pointers may be NULL on md_get_state to skip that array.
+ * L(t) = L_base * (1 + xi_dot * (t - t_base)) is Eq. (3) re-based at t_base.
+ * L_F is the box side the cached forces were evaluated with (the forces
+ * that the next half-kick uses). */
+typedef struct {
+    int64_t N, Np;
+    double* x;
+    double* v;
+    int8_t* type;
+    double L, L_base, t, t_base, xi_dot, L_F;
+    int64_t step;
+} md_state_view;
+
+typedef struct {
+    int64_t n_clusters;      /* clusters (connected proton groups) */
+    int64_t n_free;          /* neutrons in no cluster */
+    int64_t n_big;           /* clusters with A >= 12 */
+    double m_free_n;         /* n_free / N (mass fraction of free neutrons) */
+    double A_mean, Z_mean;   /* means over clusters with A >= 12 (0 if none) */
+} md_cluster_stats;
+
+typedef struct {
+    int64_t N, Np;
+    int64_t tiles;           /* 32-particle tiles (proton tiles first) */
+    int64_t rebuilds;        /* pair-list rebuilds so far */
+    int64_t list_entries;    /* tile pairs in the current force list */
+    int64_t launches;        /* kernels launched so far by this handle */
+    int64_t device_bytes;    /* device memory owned by this handle */
+    int32_t need_wrap;       /* 1 if the box is too small for tile images */
+    int32_t sort_bits;
+} md_info_t;
+
+/* Fill the defaults listed above. */
+MD_API void md_params_default(md_params* p);
+
+/* Create a system of N nucleons with proton fraction Yp at density rho
+ * (fm^-3) and temperature T (MeV) from `seed`: SplitMix64 uniform positions
+ * in the cube of side L0 = cbrt(N/rho), Maxwell velocities rescaled to
+ * KE = 3/2 N T with zero total momentum, then params.relax_iters steepest-
+ * descent iterations (a reading of the paper's equilibration from random
+ * positions, Sec. III.B).  Errors: MD_EINVAL if N < 2, Yp outside [0,1],
+ * rho <= 0, T < 0 or r_C > L0/2; MD_ENOMEM; MD_ENODEV; MD_ECUDA. */
+MD_API int md_create(int64_t N, double Yp, double rho, double T, uint64_t seed, md_system** out);
+/* As md_create with explicit parameters (p may be NULL for defaults). */
+MD_API int md_create_ex(int64_t N, double Yp, double rho, double T, uint64_t seed,
+                 const md_params* p, md_system** out);
+MD_API int md_destroy(md_system* s);
+
+MD_API int md_get_params(const md_system* s, md_params* p);
+/* Change parameters between steps (r_C > L0/2 gives MD_EINVAL).  Forces are
+ * re-evaluated before the next step. */
+MD_API int md_set_params(md_system* s, const md_params* p);
+/* Launch on `stream` (a cudaStream_t of the caller's context; NULL = the
+ * library's own stream).  The stream must outlive its use by the handle. */
+MD_API int md_set_stream(md_system* s, void* stream);
+
+/* Advance n >= 0 velocity-Verlet steps (Sec. II.A) with box growth at
+ * expansion rate xi_dot (c/fm, Eq. 3).  When xi_dot differs from the rate
+ * in use, Eq. (3) is re-based at the current time so L stays continuous.
+ * Synchronises the stream once at the end to report MD_ENUMERIC. */
+MD_API int md_step(md_system* s, int64_t n, double xi_dot);
+
+/* Forces of the last force evaluation ([N][3] doubles, original order). */
+MD_API int md_forces(md_system* s, double* f_out);
+
+/* Energies of the current state with the current box side (the potential
+ * energy is re-evaluated on the device; the cached forces are untouched). */
+MD_API int md_energy(md_system* s, md_energy_t* out);
+/* Energies recorded by the last md_step that computed them (energy_every);
+ * MD_EAGAIN if none was recorded. */
+MD_API int md_step_energy(md_system* s, md_energy_t* out);
+
+/* Distance-linkage clusters of Sec. II.C at the current positions.
+ * labels [N] (may be NULL): smallest original proton index of the cluster,
+ * -1 for a free neutron.  hist_A [N+1], hist_Z [Np+1] (may be NULL): number
+ * of clusters with mass number A / charge Z.  Distances are FP64 nearest
+ * images; results are exact (bit-identical to a serial FP64 evaluation). */
+MD_API int md_clusters(md_system* s, int32_t* labels, int64_t* hist_A, int64_t* hist_Z,
+                md_cluster_stats* stats);
+
+/* Copy the state to the caller (md_state_view above). */
+MD_API int md_get_state(md_system* s, md_state_view* view);
+/* Replace x, v (and the clock fields) from the caller; N and Np must match,
+ * x is wrapped into [0, L).  Forces are re-evaluated at the new state.  Used
+ * for resume and for parity checks. */
+MD_API int md_set_state(md_system* s, const md_state_view* view);
+
+MD_API int md_get_info(const md_system* s, md_info_t* info);
+
+/* Per-kernel device timing.  When on, md_step records CUDA events around
+ * every kernel of each step; md_kernel_times returns, for up to `max`
+ * kernels, the name, launch count and summed milliseconds since the last
+ * reset, and the number of kernels available in *n. */
+MD_API int md_set_timing(md_system* s, int on);
+MD_API int md_kernel_times(md_system* s, int max, const char** names, int64_t* launches,
+                    double* ms, int* n);
+
+/* Thread-local message describing the last error of this thread. */
+MD_API const char* md_last_error(void);
+
+/* ---- batched ensemble: many independent systems advanced together ---- */
+
+typedef struct {
+    int64_t N;
+    double Yp, rho, T;
+    uint64_t seed;
+    double xi_dot;      /* expansion rate for this job (c/fm) */
+    int64_t steps;      /* steps the job asks for (server) */
+} md_job;
+
+/* Create n independent systems (md_create semantics per job) advanced by
+ * one graph launch per step that covers all of them. */
+MD_API int md_batch_create(int n, const md_job* jobs, const md_params* p, md_batch** out);
+MD_API int md_batch_step(md_batch* b, int64_t n);
+/* Borrow system i of the batch (owned by the batch; do not destroy). */
+MD_API int md_batch_system(md_batch* b, int i, md_system** out);
+MD_API int md_batch_destroy(md_batch* b);
+
+/* ---- serving: continuous batching of MD jobs under an HBM budget ---- */
+
+typedef struct {
+    int64_t id;
+    int32_t status;         /* MD_OK or an error code */
+    int32_t reserved0;
+    int64_t N, steps;
+    md_energy_t energy;     /* energies at the end of the job */
+    double wait_ms;         /* submit -> admission */
+    double run_ms;          /* admission -> completion */
+    double step_p50_ms, step_p99_ms;  /* per-step latency of this job */
+} md_result;
+
+MD_API int md_server_create(size_t hbm_budget_bytes, const md_params* p, md_server** out);
+/* Queue a job; returns its id.  Thread-safe with respect to poll. */
+MD_API int md_server_submit(md_server* sv, const md_job* job, int64_t* id);
+/* Pop one finished job (MD_OK) or MD_EAGAIN if none has finished yet. */
+MD_API int md_server_poll(md_server* sv, md_result* out);
+/* Block until every submitted job has finished (bounded by timeout_s). */
+MD_API int md_server_drain(md_server* sv, double timeout_s);
+MD_API int md_server_destroy(md_server* sv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

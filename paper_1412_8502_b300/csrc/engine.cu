@@ -1,0 +1,698 @@
+// Host engine of the nucleon MD library (see engine.h).
+#include "engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace pasta {
+
+namespace {
+thread_local std::string g_err;
+
+void rec_cb(void* o, const char* name, cudaStream_t s) { static_cast<Engine*>(o)->on_rec(name, s); }
+void count_cb(void* o, int n) { static_cast<Engine*>(o)->on_count(n); }
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(MD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+int dalloc(SysHost& h, T** p, size_t count) {
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MD_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    h.allocs.push_back(*p);
+    h.bytes += bytes;
+    cudaError_t z = cudaMemset(*p, 0, bytes);
+    if (z != cudaSuccess) return fail(MD_ECUDA, cudaGetErrorString(z));
+    return MD_OK;
+}
+
+int auto_bits(int64_t N) {
+    int b = (int)std::ceil(std::log2(std::cbrt(2.0 * (double)N)));
+    return std::min(7, std::max(2, b));
+}
+}  // namespace
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+const char* last_error_cstr() { return g_err.c_str(); }
+
+Engine::Engine() {
+    cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking);
+    stream_ = own_stream_;
+    H_.owner = this;
+    H_.rec_fn = rec_cb;
+    H_.count_fn = count_cb;
+}
+
+Engine::~Engine() {
+    cudaStreamSynchronize(stream_);
+    drop_graphs();
+    for (size_t i = 0; i < sys.size(); ++i) {
+        for (void* p : sys[i]->allocs) cudaFree(p);
+        delete sys[i];
+    }
+    sys.clear();
+    free_tables();
+    if (own_stream_) cudaStreamDestroy(own_stream_);
+}
+
+void Engine::free_tables() {
+    void* ptrs[] = {d_sys_, d_tile_sys_, d_hist_, d_binstart_, d_cursor_, d_blocksum_, d_any_, d_out_, d_clock_,
+                    d_seeds_};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    d_sys_ = nullptr;
+    d_tile_sys_ = nullptr;
+    d_hist_ = d_binstart_ = d_cursor_ = d_blocksum_ = nullptr;
+    d_any_ = nullptr;
+    d_out_ = d_clock_ = nullptr;
+    d_seeds_ = nullptr;
+    table_bytes_ = 0;
+}
+
+void Engine::drop_graphs() {
+    GraphRec* gs[] = {&g_step_[0], &g_step_[1], &g_relax_};
+    for (GraphRec* g : gs) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        for (cudaEvent_t e : g->events) cudaEventDestroy(e);
+        *g = GraphRec();
+    }
+}
+
+size_t Engine::device_bytes() const {
+    size_t b = table_bytes_;
+    for (auto* h : sys) b += h->bytes;
+    return b;
+}
+
+void Engine::set_stream(cudaStream_t s) { stream_ = s ? s : own_stream_; }
+
+void Engine::set_timing(bool on) {
+    if (on != timing_) {
+        cudaStreamSynchronize(stream_);
+        drop_graphs();
+        timing_ = on;
+    }
+    ktimes_.clear();
+    korder_.clear();
+}
+
+void Engine::on_rec(const char* name, cudaStream_t s) {
+    if (!(capturing_ && timing_ && cur_rec_)) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    cur_rec_->names.push_back(name);
+    cur_rec_->events.push_back(e);
+}
+
+void Engine::on_count(int n) {
+    if (capturing_) capture_nodes_ += n;
+    else launches += n;
+}
+
+int Engine::kernel_times(int max, const char** names, int64_t* nl, double* ms, int* n) {
+    int k = 0;
+    for (const std::string& nm : korder_) {
+        if (k < max) {
+            if (names) names[k] = ktimes_.find(nm)->first.c_str();
+            if (nl) nl[k] = ktimes_[nm].first;
+            if (ms) ms[k] = ktimes_[nm].second;
+        }
+        ++k;
+    }
+    if (n) *n = k;
+    return MD_OK;
+}
+
+// ------------------------------------------------------------------ systems
+int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed, const md_params& p) {
+    if (N < 2 || N > (1ll << 26)) return fail(MD_EINVAL, "N must be in [2, 2^26]");
+    if (!(Yp >= 0.0 && Yp <= 1.0)) return fail(MD_EINVAL, "Yp must be in [0, 1]");
+    if (!(rho > 0.0)) return fail(MD_EINVAL, "rho must be > 0");
+    if (!(T >= 0.0)) return fail(MD_EINVAL, "T must be >= 0");
+    if (!(p.dt > 0.0) || !(p.r_nuc > 0.0) || !(p.skin > 0.0) || !(p.lambda_s > 0.0))
+        return fail(MD_EINVAL, "dt, r_nuc, skin and lambda_s must be > 0");
+    if (p.precision != MD_PREC_SPLIT && p.precision != MD_PREC_FP64) return fail(MD_EINVAL, "bad precision");
+    if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
+    const double L0 = std::cbrt((double)N / rho);
+    double rC = p.r_C > 0.0 ? p.r_C : std::min(40.0, 0.5 * L0);
+    // (relative slack of 1e-12 absorbs the rounding of cbrt)
+    if (rC > 0.5 * L0 * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_C exceeds L0/2");
+    if (p.r_nuc > 0.5 * L0 * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_nuc exceeds L0/2");
+    if (!sys.empty() && p.precision != precision) return fail(MD_EINVAL, "mixed precision in one engine");
+    precision = p.precision;
+
+    auto* h = new SysHost();
+    SysHost& s = *h;
+    s.N = N;
+    s.Np = (int64_t)std::floor(Yp * (double)N + 0.5);
+    s.Tp = (int)((s.Np + kTile - 1) / kTile);
+    s.T = s.Tp + (int)((N - s.Np + kTile - 1) / kTile);
+    s.Tpad = (s.T + kTilesPerBlock - 1) / kTilesPerBlock * kTilesPerBlock;
+    s.nbits = p.sort_bits ? p.sort_bits : auto_bits(N);
+    s.nbins = 1ll << (3 * s.nbits);
+    s.L0 = L0;
+    s.rho = rho;
+    s.Yp = Yp;
+    s.T0 = T;
+    s.seed = seed;
+    s.prm = p;
+    s.prm.r_C = rC;
+    s.prm.T = T;
+    s.xi = 0.0;
+
+    SysConst& c = s.c;
+    c.N = (int)N;
+    c.Np = (int)s.Np;
+    c.T = s.T;
+    c.Tp = s.Tp;
+    c.nbits = s.nbits;
+    c.nbins = s.nbins;
+    c.list_cap = (long long)s.T * s.T;
+    int rc = MD_OK;
+    auto A = [&](auto** ptr, size_t count) {
+        if (rc == MD_OK) rc = dalloc(s, ptr, count);
+    };
+    for (int b = 0; b < 2; ++b) {
+        A(&c.x[b], 3 * (size_t)N);
+        A(&c.v[b], 3 * (size_t)N);
+        A(&c.id[b], (size_t)N);
+        A(&c.f32[b], 3 * (size_t)N);
+        A(&c.f64[b], 3 * (size_t)N);
+    }
+    A(&c.disp, 3 * (size_t)N);
+    A(&c.key, (size_t)N);
+    A(&c.slot, (size_t)N);
+    A(&c.tpos, (size_t)s.T * kTile);
+    A(&c.torg, 3 * (size_t)s.T);
+    A(&c.torgf, 4 * (size_t)s.T);
+    A(&c.thalf, 3 * (size_t)s.T);
+    A(&c.lcount, (size_t)s.T);
+    A(&c.lstart, (size_t)s.T + 1);
+    A(&c.list, (size_t)c.list_cap);
+    A(&c.tile_e, 8 * (size_t)s.T);
+    A(&c.blk, 4 * (size_t)(s.Tpad / kTilesPerBlock));
+    A(&s.d_st, 1);
+    A(&s.d_cl, 1);
+    A(&s.d_stage, 9 * (size_t)N);
+    A(&s.d_stage_t, (size_t)N);
+    A(&s.d_stage_lab, (size_t)N);
+    if (rc != MD_OK) {
+        for (void* q : s.allocs) cudaFree(q);
+        delete h;
+        return rc;
+    }
+    c.st = s.d_st;
+    c.cl = s.d_cl;
+    c.dt = p.dt;
+    c.M = 939.0;
+    c.T_target = T;
+    c.skin = p.skin;
+    c.a = 110.0;
+    c.b = -26.0;
+    c.c = 24.0;
+    c.Lambda = 1.25;
+    c.lambda_s = p.lambda_s;
+    c.alpha = 197.3269804 / 137.035999084;
+    c.r_nuc = p.r_nuc;
+    c.r_C = rC;
+    c.r_pp = p.r_pp;
+    c.r_np = p.r_np;
+    c.relax_gamma = p.relax_gamma;
+    c.relax_dmax = p.relax_dmax;
+    c.thermostat_every = (int)p.thermostat_every;
+    c.rebuild_every = (int)std::max<int64_t>(1, p.rebuild_every);
+    c.coulomb = p.coulomb ? 1 : 0;
+    c.energy_every = (int)p.energy_every;
+
+    SysState st{};
+    st.L = st.L_base = st.L_F = st.L_build = L0;
+    st.vscale = 1.0;
+    st.force_rebuild = 1;
+    CK(cudaMemcpy(s.d_st, &st, sizeof(st), cudaMemcpyHostToDevice));
+    sys.push_back(h);
+    return MD_OK;
+}
+
+void Engine::remove_system(int idx) {
+    cudaStreamSynchronize(stream_);
+    SysHost* h = sys[idx];
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->cl_ready) {
+        void* cp[] = {h->hcl.parent, h->hcl.minid, h->hcl.zc, h->hcl.ac, h->hcl.label, h->hcl.hist_A,
+                      h->hcl.hist_Z, h->hcl.stats, h->hcl.count, h->hcl.start, h->hcl.list, h->hcl.total};
+        for (void* p : cp)
+            if (p) cudaFree(p);
+    }
+    delete h;
+    sys.erase(sys.begin() + idx);
+}
+
+int Engine::build_tables() {
+    cudaStreamSynchronize(stream_);
+    drop_graphs();
+    free_tables();
+    const int n = (int)sys.size();
+    int tiles = 0;
+    long long bins = 0;
+    for (SysHost* h : sys) {
+        h->c.tile_base = tiles;
+        h->c.bin_base = bins;
+        tiles += h->Tpad;
+        bins += 2 * h->nbins;
+    }
+    if (tiles == 0) tiles = kTilesPerBlock;
+    if (bins == 0) bins = 1;
+    std::vector<int> ts(tiles, -1);
+    for (int s = 0; s < n; ++s)
+        for (int t = 0; t < sys[s]->Tpad; ++t) ts[sys[s]->c.tile_base + t] = s;
+    const int nscan = (int)((bins + 8191) / 8192);
+    auto A = [&](auto** p, size_t bytes) -> int {
+        cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MD_ENOMEM, "engine table allocation failed");
+        }
+        cudaMemset(*p, 0, std::max<size_t>(bytes, 16));
+        table_bytes_ += bytes;
+        return MD_OK;
+    };
+    int rc = MD_OK;
+    if ((rc = A(&d_sys_, sizeof(SysConst) * std::max(n, 1)))) return rc;
+    if ((rc = A(&d_tile_sys_, sizeof(int) * tiles))) return rc;
+    if ((rc = A(&d_hist_, sizeof(unsigned) * bins))) return rc;
+    if ((rc = A(&d_binstart_, sizeof(unsigned) * bins))) return rc;
+    if ((rc = A(&d_cursor_, sizeof(unsigned) * bins))) return rc;
+    if ((rc = A(&d_blocksum_, sizeof(unsigned) * (nscan + 1)))) return rc;
+    if ((rc = A(&d_any_, sizeof(int)))) return rc;
+    if ((rc = A(&d_out_, sizeof(double) * 16))) return rc;
+    if ((rc = A(&d_clock_, sizeof(double) * 8))) return rc;
+    if ((rc = A(&d_seeds_, sizeof(unsigned long long) * std::max(n, 1)))) return rc;
+    std::vector<SysConst> hs(n);
+    for (int s = 0; s < n; ++s) hs[s] = sys[s]->c;
+    if (n) CK(cudaMemcpy(d_sys_, hs.data(), sizeof(SysConst) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_tile_sys_, ts.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice));
+    EngineDev& E = H_.dev;
+    E.sys = d_sys_;
+    E.tile_sys = d_tile_sys_;
+    E.nsys = n;
+    E.ntiles = tiles;
+    E.nbins_total = bins;
+    E.hist = d_hist_;
+    E.binstart = d_binstart_;
+    E.cursor = d_cursor_;
+    E.blocksum = d_blocksum_;
+    E.any_rebuild = d_any_;
+    H_.precision = precision;
+    return MD_OK;
+}
+
+int Engine::initialise() {
+    std::vector<unsigned long long> seeds;
+    for (SysHost* h : sys) seeds.push_back(h->seed);
+    CK(cudaMemcpyAsync(d_seeds_, seeds.data(), sizeof(unsigned long long) * seeds.size(), cudaMemcpyHostToDevice,
+                       stream_));
+    launch_init(H_, stream_, d_seeds_);
+    CK(cudaGetLastError());
+    int rc = refresh(-1);
+    if (rc) return rc;
+    int64_t iters = 0;
+    for (SysHost* h : sys) iters = std::max(iters, h->prm.relax_iters);
+    if (iters > 0) {
+        if (!g_relax_.exec && (rc = capture(g_relax_, 1, false))) return rc;
+        for (int64_t k = 0; k < iters; ++k)
+            if ((rc = run_graph(g_relax_))) return rc;
+    }
+    return check_errors();
+}
+
+// ------------------------------------------------------------------ graphs
+int Engine::capture(GraphRec& g, int kind, bool energy) {
+    g = GraphRec();
+    capturing_ = true;
+    capture_nodes_ = 0;
+    cur_rec_ = &g;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        if (kind == 0) {
+            launch_kick_drift(H_, stream_);
+            launch_rebuild(H_, stream_, 0, -1);
+            launch_force(H_, stream_, energy, -1, 0);
+            launch_kick_finalize(H_, stream_, energy);
+        } else {
+            launch_sd_update(H_, stream_);
+            launch_rebuild(H_, stream_, 0, -1);
+            launch_force(H_, stream_, false, -1, 0);
+        }
+        if (timing_) {
+            cudaEvent_t ev;
+            cudaEventCreate(&ev);
+            cudaEventRecordWithFlags(ev, stream_, cudaEventRecordExternal);
+            g.events.push_back(ev);
+        }
+        e = cudaStreamEndCapture(stream_, &graph);
+    }
+    capturing_ = false;
+    cur_rec_ = nullptr;
+    if (e != cudaSuccess) return fail(MD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(MD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    g.nodes = capture_nodes_;
+    return MD_OK;
+}
+
+int Engine::run_graph(GraphRec& g) {
+    CK(cudaGraphLaunch(g.exec, stream_));
+    launches += g.nodes;
+    if (timing_ && g.events.size() > 1) {
+        CK(cudaStreamSynchronize(stream_));
+        for (size_t i = 0; i + 1 < g.events.size(); ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, g.events[i], g.events[i + 1]);
+            auto it = ktimes_.find(g.names[i]);
+            if (it == ktimes_.end()) {
+                korder_.push_back(g.names[i]);
+                it = ktimes_.emplace(g.names[i], std::make_pair((int64_t)0, 0.0)).first;
+            }
+            it->second.first += 1;
+            it->second.second += ms;
+        }
+    }
+    return MD_OK;
+}
+
+// ------------------------------------------------------------------ ops
+int Engine::refresh(int only) {
+    launch_rebuild(H_, stream_, 1, only);
+    launch_force(H_, stream_, false, only, 0);
+    CK(cudaGetLastError());
+    for (size_t s = 0; s < sys.size(); ++s)
+        if (only < 0 || (int)s == only) sys[s]->dirty = false;
+    return MD_OK;
+}
+
+int Engine::check_errors() {
+    const int n = (int)sys.size();
+    std::vector<int> errs(n, 0);
+    for (int s = 0; s < n; ++s)
+        CK(cudaMemcpyAsync(&errs[s], &sys[s]->d_st->error, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    for (int s = 0; s < n; ++s)
+        if (errs[s]) return fail(MD_ENUMERIC, "non-finite force in system " + std::to_string(s));
+    return MD_OK;
+}
+
+int Engine::step(int64_t n, const std::vector<double>* xi) {
+    int rc = step_async(n, xi, nullptr);
+    if (rc) return rc;
+    return check_errors();
+}
+
+size_t Engine::estimate_bytes(int64_t N, double Yp, const md_params& p) {
+    const int64_t Np = (int64_t)std::floor(Yp * (double)N + 0.5);
+    const int64_t T = (Np + kTile - 1) / kTile + (N - Np + kTile - 1) / kTile;
+    const int64_t Tpad = (T + kTilesPerBlock - 1) / kTilesPerBlock * kTilesPerBlock;
+    const int nbits = p.sort_bits ? p.sort_bits : auto_bits(N);
+    const int64_t nb = 2ll << (3 * nbits);
+    size_t b = 0;
+    b += 2 * (size_t)N * (8 * 3 + 8 * 3 + 4 + 4 * 3 + 8 * 3);   // x, v, id, f32, f64
+    b += (size_t)N * (4 * 3 + 4 + 4 + 9 * 8 + 1 + 4);           // disp, key, slot, staging
+    b += (size_t)T * (16 * 32 + 8 * 3 + 16 + 12 + 4 + 4 + 32) + 4 * 8 * Tpad;
+    b += (size_t)T * T * 4;                                      // pair list
+    b += (size_t)nb * 12 + 4096;                                 // engine bins
+    return b;
+}
+
+int Engine::step_async(int64_t n, const std::vector<double>* xi, cudaEvent_t* events) {
+    if (n < 0) return fail(MD_EINVAL, "n must be >= 0");
+    int rc;
+    bool any_dirty = false;
+    for (SysHost* h : sys) any_dirty |= h->dirty;
+    if (any_dirty) {
+        for (size_t s = 0; s < sys.size(); ++s) {
+            if (!sys[s]->dirty) continue;
+            int one = 1;
+            CK(cudaMemcpyAsync(&sys[s]->d_st->force_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, stream_));
+            if ((rc = refresh((int)s))) return rc;
+        }
+    }
+    if (xi) {
+        for (size_t s = 0; s < sys.size(); ++s) {
+            const double x = (*xi)[s];
+            if (x != sys[s]->xi) {
+                launch_set_rate(H_, stream_, (int)s, x);
+                sys[s]->xi = x;
+            }
+        }
+    }
+    const int64_t ee = sys.empty() ? 0 : sys[0]->prm.energy_every;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t next = sys.empty() ? 0 : sys[0]->host_step + 1;
+        const int e = (ee > 0 && next % ee == 0) ? 1 : 0;
+        if (!g_step_[e].exec && (rc = capture(g_step_[e], 0, e == 1))) return rc;
+        if (events) CK(cudaEventRecord(events[k], stream_));
+        if ((rc = run_graph(g_step_[e]))) return rc;
+        for (SysHost* h : sys) h->host_step += 1;
+    }
+    if (events) CK(cudaEventRecord(events[n], stream_));
+    CK(cudaGetLastError());
+    return MD_OK;
+}
+
+int Engine::forces(int idx, double* f_out) {
+    SysHost& h = *sys[idx];
+    int rc;
+    if (h.dirty && (rc = refresh(idx))) return rc;
+    double* d_f = h.d_stage + 6 * h.N;
+    launch_gather(H_, stream_, idx, nullptr, nullptr, d_f, nullptr);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(f_out, d_f, sizeof(double) * 3 * h.N, cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    return MD_OK;
+}
+
+int Engine::energy(int idx, md_energy_t* e) {
+    SysHost& h = *sys[idx];
+    int rc;
+    if (h.dirty && (rc = refresh(idx))) return rc;
+    launch_energy_now(H_, stream_, idx, d_out_);
+    CK(cudaGetLastError());
+    double o[9];
+    CK(cudaMemcpyAsync(o, d_out_, sizeof(o), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    e->KE = o[0];
+    e->PE_nuc = o[1];
+    e->PE_coul = o[2];
+    e->virial = o[3];
+    e->L = o[4];
+    e->t = o[5];
+    e->step = (int64_t)o[6];
+    e->pairs_nuc = (int64_t)o[7];
+    e->pairs_coul = (int64_t)o[8];
+    return check_errors();
+}
+
+int Engine::step_energy(int idx, md_energy_t* e) {
+    SysState st;
+    CK(cudaMemcpyAsync(&st, sys[idx]->d_st, sizeof(st), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    if (!st.have_energy) return fail(MD_EAGAIN, "no energies recorded (energy_every = 0?)");
+    e->KE = st.KE;
+    e->PE_nuc = st.PE_nuc;
+    e->PE_coul = st.PE_coul;
+    e->virial = st.virial;
+    e->L = st.e_L;
+    e->t = st.e_t;
+    e->step = st.e_step;
+    e->pairs_nuc = st.e_pairs_nuc;
+    e->pairs_coul = st.e_pairs_coul;
+    return MD_OK;
+}
+
+int Engine::ensure_cluster_bufs(SysHost& h, long long need) {
+    ClusterBufs& B = h.hcl;
+    int rc = MD_OK;
+    if (!h.cl_ready) {
+        std::memset(&B, 0, sizeof(B));
+        auto A = [&](auto** p, size_t count) {
+            if (rc == MD_OK) rc = dalloc(h, p, count);
+        };
+        A(&B.parent, (size_t)h.Np);
+        A(&B.minid, (size_t)h.Np);
+        A(&B.zc, (size_t)h.Np);
+        A(&B.ac, (size_t)h.Np);
+        A(&B.label, (size_t)h.N);
+        A(&B.hist_A, (size_t)h.N + 1);
+        A(&B.hist_Z, (size_t)h.Np + 1);
+        A(&B.stats, 8);
+        A(&B.count, (size_t)h.T);
+        A(&B.start, (size_t)h.T + 1);
+        A(&B.total, 1);
+        if (rc) return rc;
+        h.cl_ready = true;
+    }
+    if (need > B.cap) {
+        long long cap = std::max<long long>(need + need / 4, 1024);
+        int* nl = nullptr;
+        if ((rc = dalloc(h, &nl, (size_t)cap))) return rc;
+        B.list = nl;   // the previous list stays allocated until the system is freed
+        B.cap = cap;
+    }
+    CK(cudaMemcpyAsync(h.d_cl, &B, sizeof(B), cudaMemcpyHostToDevice, stream_));
+    return MD_OK;
+}
+
+int Engine::clusters(int idx, int32_t* labels, int64_t* hA, int64_t* hZ, md_cluster_stats* out) {
+    SysHost& h = *sys[idx];
+    int rc;
+    if (h.dirty && (rc = refresh(idx))) return rc;
+    if ((rc = ensure_cluster_bufs(h, 0))) return rc;
+    launch_cluster_lists(H_, stream_, 0, idx);
+    long long total = 0;
+    CK(cudaMemcpyAsync(&total, h.hcl.total, sizeof(total), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    if ((rc = ensure_cluster_bufs(h, total))) return rc;
+    launch_cluster_lists(H_, stream_, 1, idx);
+    launch_clusters(H_, stream_, idx, (int)h.Np, (int)h.N, h.Tp, h.T, h.d_stage_lab);
+    CK(cudaGetLastError());
+    long long st[8];
+    if (labels)
+        CK(cudaMemcpyAsync(labels, h.d_stage_lab, sizeof(int32_t) * h.N, cudaMemcpyDeviceToHost, stream_));
+    if (hA) CK(cudaMemcpyAsync(hA, h.hcl.hist_A, sizeof(int64_t) * (h.N + 1), cudaMemcpyDeviceToHost, stream_));
+    if (hZ) CK(cudaMemcpyAsync(hZ, h.hcl.hist_Z, sizeof(int64_t) * (h.Np + 1), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(st, h.hcl.stats, sizeof(st), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    if (out) {
+        out->n_clusters = st[0];
+        out->n_free = st[1];
+        out->n_big = st[2];
+        out->m_free_n = (double)st[1] / (double)h.N;
+        out->A_mean = st[2] ? (double)st[3] / (double)st[2] : 0.0;
+        out->Z_mean = st[2] ? (double)st[4] / (double)st[2] : 0.0;
+    }
+    return MD_OK;
+}
+
+int Engine::get_state(int idx, md_state_view* v) {
+    SysHost& h = *sys[idx];
+    double* dx = h.d_stage;
+    double* dv = h.d_stage + 3 * h.N;
+    launch_gather(H_, stream_, idx, v->x ? dx : nullptr, v->v ? dv : nullptr, nullptr,
+                  v->type ? h.d_stage_t : nullptr);
+    CK(cudaGetLastError());
+    if (v->x) CK(cudaMemcpyAsync(v->x, dx, sizeof(double) * 3 * h.N, cudaMemcpyDeviceToHost, stream_));
+    if (v->v) CK(cudaMemcpyAsync(v->v, dv, sizeof(double) * 3 * h.N, cudaMemcpyDeviceToHost, stream_));
+    if (v->type) CK(cudaMemcpyAsync(v->type, h.d_stage_t, h.N, cudaMemcpyDeviceToHost, stream_));
+    SysState st;
+    CK(cudaMemcpyAsync(&st, h.d_st, sizeof(st), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    v->N = h.N;
+    v->Np = h.Np;
+    v->L = st.L;
+    v->L_base = st.L_base;
+    v->t = st.t;
+    v->t_base = st.t_base;
+    v->xi_dot = st.xi_dot;
+    v->L_F = st.L_F;
+    v->step = st.step;
+    return MD_OK;
+}
+
+int Engine::set_state(int idx, const md_state_view* v) {
+    SysHost& h = *sys[idx];
+    if (v->N != h.N || v->Np != h.Np) return fail(MD_EINVAL, "N / Np do not match the system");
+    if (!v->x || !v->v) return fail(MD_EINVAL, "x and v are required");
+    if (!(v->L > 0.0)) return fail(MD_EINVAL, "L must be > 0");
+    if (h.prm.r_C > 0.5 * v->L * (1.0 + 1e-12) || h.prm.r_nuc > 0.5 * v->L * (1.0 + 1e-12))
+        return fail(MD_EINVAL, "cutoff exceeds L/2");
+    if (v->type) {
+        for (int64_t i = 0; i < h.N; ++i)
+            if (v->type[i] != (i < h.Np ? 1 : 0)) return fail(MD_EINVAL, "type must list protons first");
+    }
+    double clock[8] = {v->L, v->L_base > 0 ? v->L_base : v->L, v->t, v->t_base, v->xi_dot, (double)v->step,
+                       v->L, 0.0};
+    CK(cudaMemcpyAsync(h.d_stage, v->x, sizeof(double) * 3 * h.N, cudaMemcpyHostToDevice, stream_));
+    CK(cudaMemcpyAsync(h.d_stage + 3 * h.N, v->v, sizeof(double) * 3 * h.N, cudaMemcpyHostToDevice, stream_));
+    CK(cudaMemcpyAsync(d_clock_, clock, sizeof(clock), cudaMemcpyHostToDevice, stream_));
+    launch_set_clock(H_, stream_, idx, d_clock_);
+    launch_scatter_state(H_, stream_, idx, h.d_stage, h.d_stage + 3 * h.N);
+    int rc = refresh(idx);
+    if (rc) return rc;
+    h.host_step = v->step;
+    h.xi = v->xi_dot;
+    return check_errors();
+}
+
+int Engine::set_params(int idx, const md_params& p) {
+    SysHost& h = *sys[idx];
+    const double rC = p.r_C > 0.0 ? p.r_C : std::min(40.0, 0.5 * h.L0);
+    if (rC > 0.5 * h.L0 * (1.0 + 1e-12) || p.r_nuc > 0.5 * h.L0 * (1.0 + 1e-12))
+        return fail(MD_EINVAL, "cutoff exceeds L0/2");
+    if (!(p.dt > 0.0) || !(p.r_nuc > 0.0) || !(p.skin > 0.0) || !(p.lambda_s > 0.0))
+        return fail(MD_EINVAL, "dt, r_nuc, skin and lambda_s must be > 0");
+    if (p.precision != MD_PREC_SPLIT && p.precision != MD_PREC_FP64) return fail(MD_EINVAL, "bad precision");
+    if (p.precision != precision) {
+        if (sys.size() > 1) return fail(MD_EINVAL, "precision is shared by all systems of a batch");
+        precision = p.precision;
+        H_.precision = precision;
+        cudaStreamSynchronize(stream_);
+        drop_graphs();
+    }
+    h.prm = p;
+    h.prm.r_C = rC;
+    SysConst& c = h.c;
+    c.dt = p.dt;
+    c.T_target = p.T;
+    c.skin = p.skin;
+    c.lambda_s = p.lambda_s;
+    c.r_nuc = p.r_nuc;
+    c.r_C = rC;
+    c.r_pp = p.r_pp;
+    c.r_np = p.r_np;
+    c.relax_gamma = p.relax_gamma;
+    c.relax_dmax = p.relax_dmax;
+    c.thermostat_every = (int)p.thermostat_every;
+    c.rebuild_every = (int)std::max<int64_t>(1, p.rebuild_every);
+    c.coulomb = p.coulomb ? 1 : 0;
+    c.energy_every = (int)p.energy_every;
+    CK(cudaMemcpyAsync(d_sys_ + idx, &c, sizeof(SysConst), cudaMemcpyHostToDevice, stream_));
+    int one = 1;
+    CK(cudaMemcpyAsync(&h.d_st->force_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, stream_));
+    h.dirty = true;
+    CK(cudaStreamSynchronize(stream_));
+    return MD_OK;
+}
+
+int Engine::info(int idx, md_info_t* out) {
+    SysHost& h = *sys[idx];
+    SysState st;
+    CK(cudaMemcpyAsync(&st, h.d_st, sizeof(st), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    out->N = h.N;
+    out->Np = h.Np;
+    out->tiles = h.T;
+    out->rebuilds = st.n_rebuilds;
+    out->list_entries = st.list_total;
+    out->launches = launches;
+    out->device_bytes = (int64_t)(h.bytes + (sys.size() == 1 ? table_bytes_ : 0));
+    out->need_wrap = st.need_wrap;
+    out->sort_bits = h.nbits;
+    return MD_OK;
+}
+
+}  // namespace pasta

@@ -1,0 +1,504 @@
+// Pair-list rebuild (the cell-list build of Sec. II.B.2, re-designed for the
+// GPU): a counting sort of the particles over a Morton-ordered grid of
+// 2^(3 nbits) bins per species, a deterministic in-bin order, 32-particle
+// tiles with FP64 origins and bounding boxes, and per-tile lists of the
+// tiles whose bounding boxes come within the interaction range plus skin.
+//
+// Rebuild rule (the neighbour-list rule of Sec. II.B.1 applied to tiles):
+// rebuild when any particle has moved more than skin/2 since the last
+// rebuild, or every `rebuild_every` steps.  Then every pair closer than the
+// cutoff now was closer than cutoff + skin at the rebuild, so its tiles'
+// boxes were within cutoff + skin.  Growth of the box (Eq. 3) only moves
+// periodic images apart, so it never brings a new pair into range.
+#include "kernels.h"
+
+namespace pasta {
+
+namespace {
+
+__device__ inline unsigned spread3(unsigned v, int nbits) {
+    unsigned r = 0;
+    for (int b = 0; b < nbits; ++b) r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+__device__ inline unsigned morton_key(const SysConst& S, double x, double y, double z, double L) {
+    const int n = 1 << S.nbits;
+    const double sc = (double)n / L;
+    int qx = min(max((int)(x * sc), 0), n - 1);
+    int qy = min(max((int)(y * sc), 0), n - 1);
+    int qz = min(max((int)(z * sc), 0), n - 1);
+    return spread3((unsigned)qx, S.nbits) | (spread3((unsigned)qy, S.nbits) << 1) |
+           (spread3((unsigned)qz, S.nbits) << 2);
+}
+
+// Inclusive scan over a block of 1024 threads; returns the exclusive prefix
+// of v and writes the block total to *total.
+__device__ inline unsigned block_exscan(unsigned v, unsigned* sm /*32*/, unsigned* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) sm[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        unsigned s = lane < nw ? sm[lane] : 0u;
+        unsigned si = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += y;
+        }
+        if (lane < nw) sm[lane] = si - s;
+        if (lane == 31) sm[32] = si;
+    }
+    __syncthreads();
+    unsigned r = sm[w] + inc - v;
+    if (total) *total = sm[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ inline bool sys_rebuilds(const SysConst& S) { return S.st->rebuild != 0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- decision
+// One thread per system.  forced_only: rebuild only systems that asked.
+__global__ void k_decide(EngineDev E, int forced_only, int only) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < E.nsys; s += blockDim.x) {
+        const SysConst& S = E.sys[s];
+        SysState* st = S.st;
+        int need = st->force_rebuild;
+        if (!forced_only) {
+            const float md2 = __uint_as_float(st->maxdisp2);
+            const float h = 0.5f * (float)S.skin;
+            need |= (st->step - st->last_build >= S.rebuild_every) || (md2 > h * h);
+        }
+        if (only >= 0 && s != only) need = 0;
+        st->maxdisp2 = 0u;
+        st->rebuild = need;
+        st->cur_next = need ? (st->cur ^ 1) : st->cur;
+        if (need) {
+            st->force_rebuild = 0;
+            st->hmax = 0u;
+            atomicOr(&any, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *E.any_rebuild = any;
+}
+
+// ---------------------------------------------------------------- histogram
+__global__ void k_hist(EngineDev E) {
+    if (!*E.any_rebuild) return;
+    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    if (g >= E.ntiles) return;
+    const int s = E.tile_sys[g];
+    if (s < 0) return;
+    const SysConst& S = E.sys[s];
+    if (!sys_rebuilds(S)) return;
+    const int t = g - S.tile_base;
+    if (t >= S.T) return;
+    const int p = tile_slot0(S, t) + (threadIdx.x & 31);
+    if (p >= tile_end(S, t)) return;
+    const SysState* st = S.st;
+    const double* x = S.x[st->cur];
+    const unsigned k = morton_key(S, x[p], x[S.N + p], x[2 * S.N + p], st->L) +
+                       (p < S.Np ? 0u : (unsigned)S.nbins);
+    S.key[p] = k;
+    atomicAdd(&E.hist[S.bin_base + k], 1u);
+}
+
+// ---------------------------------------------------------------- bin scan
+// Three-pass exclusive scan of hist over all systems' bins (8192 per block).
+constexpr int kScanPer = 8;
+constexpr int kScanChunk = 1024 * kScanPer;
+
+__global__ void k_scan_reduce(EngineDev E) {
+    if (!*E.any_rebuild) return;
+    __shared__ unsigned sm[33];
+    const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    unsigned s = 0;
+    for (int k = 0; k < kScanPer; ++k)
+        if (base + k < E.nbins_total) s += E.hist[base + k];
+    unsigned tot;
+    block_exscan(s, sm, &tot);
+    if (threadIdx.x == 0) E.blocksum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(EngineDev E, int nblk) {
+    if (!*E.any_rebuild) return;
+    __shared__ unsigned sm[33];
+    const int per = (nblk + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per;
+    unsigned s = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nblk) s += E.blocksum[b0 + k];
+    unsigned run = block_exscan(s, sm, nullptr);
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nblk) {
+            unsigned v = E.blocksum[b0 + k];
+            E.blocksum[b0 + k] = run;
+            run += v;
+        }
+}
+
+__global__ void k_scan_down(EngineDev E) {
+    if (!*E.any_rebuild) return;
+    __shared__ unsigned sm[33];
+    const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    unsigned v[kScanPer];
+    unsigned s = 0;
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = (base + k < E.nbins_total) ? E.hist[base + k] : 0u;
+        s += v[k];
+    }
+    unsigned run = block_exscan(s, sm, nullptr) + E.blocksum[blockIdx.x];
+    for (int k = 0; k < kScanPer; ++k)
+        if (base + k < E.nbins_total) {
+            E.binstart[base + k] = run;
+            E.cursor[base + k] = run;
+            run += v[k];
+        }
+}
+
+// ---------------------------------------------------------------- scatter
+// Places each slot index in its bin (order inside a bin decided by atomics,
+// fixed up deterministically by k_move).
+__global__ void k_scatter(EngineDev E) {
+    if (!*E.any_rebuild) return;
+    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    if (g >= E.ntiles) return;
+    const int s = E.tile_sys[g];
+    if (s < 0) return;
+    const SysConst& S = E.sys[s];
+    if (!sys_rebuilds(S)) return;
+    const int t = g - S.tile_base;
+    if (t >= S.T) return;
+    const int p = tile_slot0(S, t) + (threadIdx.x & 31);
+    if (p >= tile_end(S, t)) return;
+    const unsigned base = E.binstart[S.bin_base];
+    const unsigned pos = atomicAdd(&E.cursor[S.bin_base + S.key[p]], 1u) - base;
+    S.slot[pos] = p;
+}
+
+// Destination of slot q's particle: its bin start plus the number of
+// particles of the same bin with a smaller previous slot index (stable,
+// deterministic).  Moves x, v, id (and the cached force if keep_forces).
+__global__ void k_move(EngineDev E) {
+    if (!*E.any_rebuild) return;
+    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    if (g >= E.ntiles) return;
+    const int s = E.tile_sys[g];
+    if (s < 0) return;
+    const SysConst& S = E.sys[s];
+    if (!sys_rebuilds(S)) return;
+    const int t = g - S.tile_base;
+    if (t >= S.T) return;
+    const int q = tile_slot0(S, t) + (threadIdx.x & 31);
+    if (q >= tile_end(S, t)) return;
+    const SysState* st = S.st;
+    const int c = st->cur, cn = st->cur_next;
+    const int j = S.slot[q];
+    const unsigned gb = (unsigned)S.key[j];
+    const unsigned base = E.binstart[S.bin_base];
+    const int s0 = (int)(E.binstart[S.bin_base + gb] - base);
+    const int n = (int)E.hist[S.bin_base + gb];
+    int rank = 0;
+    for (int k = 0; k < n; ++k) rank += (S.slot[s0 + k] < j);
+    const int d = s0 + rank;
+    const int N = S.N;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        S.x[cn][a * N + d] = S.x[c][a * N + j];
+        S.v[cn][a * N + d] = S.v[c][a * N + j];
+    }
+    S.id[cn][d] = S.id[c][j];
+    if (st->keep_forces) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            S.f32[cn][a * N + d] = S.f32[c][a * N + j];
+            S.f64[cn][a * N + d] = S.f64[c][a * N + j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- tiles
+// Warp per tile: bounding box, FP64 origin (box centre), FP32 local
+// coordinates, displacement reset.  Also clears the system's histogram for
+// the next rebuild and records the rebuild.
+__global__ void k_tiles(EngineDev E) {
+    if (!*E.any_rebuild) return;
+    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= E.ntiles) return;
+    const int s = E.tile_sys[g];
+    if (s < 0) return;
+    const SysConst& S = E.sys[s];
+    if (!sys_rebuilds(S)) return;
+    const int t = g - S.tile_base;
+    SysState* st = S.st;
+    // clear this system's bins (grid-stride over the system's threads)
+    {
+        const long long nb = 2 * S.nbins;
+        const long long tid = (long long)(g - S.tile_base) * kTile + lane;
+        const long long nthr = (long long)((S.T + kTilesPerBlock - 1) / kTilesPerBlock) * kBlock;
+        for (long long b = tid; b < nb; b += nthr) E.hist[S.bin_base + b] = 0u;
+    }
+    if (t >= S.T) return;
+    const int p0 = tile_slot0(S, t), p1 = tile_end(S, t);
+    const int p = p0 + lane;
+    const bool valid = p < p1;
+    const int cn = st->cur_next;
+    const int N = S.N;
+    const double* x = S.x[cn];
+    double c[3], h[3];
+    double xv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xv[a] = valid ? x[a * N + p] : 0.0;
+        const double lo = warp_min(valid ? xv[a] : 1e300);
+        const double hi = warp_max(valid ? xv[a] : -1e300);
+        c[a] = 0.5 * (lo + hi);
+        h[a] = 0.5 * (hi - lo);
+    }
+    const double L = st->L;
+    float4 l;
+    l.x = valid ? (float)(xv[0] - c[0]) : kPad;
+    l.y = valid ? (float)(xv[1] - c[1]) : kPad;
+    l.z = valid ? (float)(xv[2] - c[2]) : kPad;
+    l.w = 0.0f;
+    S.tpos[t * kTile + lane] = l;
+    if (valid) {
+        S.disp[p] = 0.0f;
+        S.disp[N + p] = 0.0f;
+        S.disp[2 * N + p] = 0.0f;
+    }
+    if (lane == 0) {
+        const float hm = (float)fmax(h[0], fmax(h[1], h[2]));
+        for (int a = 0; a < 3; ++a) {
+            S.torg[3 * t + a] = c[a];
+            // round the FP32 box up so the FP32 range test stays conservative
+            S.thalf[3 * t + a] = (float)h[a] * (1.0f + 1e-6f) + 1e-6f;
+            S.torgf[4 * t + a] = (float)c[a];
+        }
+        S.torgf[4 * t + 3] = hm;
+        atomic_max_pos(&st->hmax, hm);
+        if (t == 0) {
+            st->last_build = st->step;
+            st->n_rebuilds += 1;
+            st->L_build = L;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- lists
+// FP32 test "bounding boxes of I and J (nearest image) closer than R".
+// Rounding of the FP32 origins (< 1e-4 fm for L < 2000 fm) is covered by
+// the margin kMargin, so the test can only include extra tiles.
+constexpr float kMargin = 2e-3f;
+
+struct ListTest {
+    float Lf, iLf;
+    float R2same, R2cross;     // squared ranges: same-species / cross-species
+    float R2nuc;               // squared nuclear range (flag for p-p entries)
+    int cluster;               // 1: cluster lists (J only proton tiles)
+};
+
+__device__ inline ListTest make_test(const SysConst& S, int mode, float L) {
+    ListTest T;
+    T.Lf = L;
+    T.iLf = 1.0f / L;
+    if (mode == 0) {
+        const float rn = (float)(S.r_nuc + S.skin) + kMargin;
+        const float rc = (float)((S.coulomb ? fmax(S.r_C, S.r_nuc) : S.r_nuc) + S.skin) + kMargin;
+        T.R2same = rc * rc;      // used for proton-proton only, see below
+        T.R2cross = rn * rn;
+        T.R2nuc = rn * rn;
+        T.cluster = 0;
+    } else {
+        // boxes are those of the last rebuild: every particle has drifted
+        // by at most skin/2 since then
+        const float rpp = (float)(S.r_pp + S.skin) + kMargin, rnp = (float)(S.r_np + S.skin) + kMargin;
+        T.R2same = rpp * rpp;
+        T.R2cross = rnp * rnp;
+        T.R2nuc = 0.0f;
+        T.cluster = 1;
+    }
+    return T;
+}
+
+// Squared distance between the FP32 boxes of tiles I and J (nearest image).
+__device__ inline float box_d2(const SysConst& S, const float4& oI, const float* hI, int J,
+                               const ListTest& T) {
+    const float4 oJ = *reinterpret_cast<const float4*>(&S.torgf[4 * J]);
+    float d2 = 0.0f;
+    float dd[3] = {oI.x - oJ.x, oI.y - oJ.y, oI.z - oJ.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float d = dd[a];
+        d -= T.Lf * rintf(d * T.iLf);
+        float gap = fabsf(d) - hI[a] - S.thalf[3 * J + a];
+        gap = fmaxf(gap, 0.0f);
+        d2 = fmaf(gap, gap, d2);
+    }
+    return d2;
+}
+
+// Entry for J from I, or -1 if out of range.
+__device__ inline int list_entry(const SysConst& S, int I, int J, const float4& oI,
+                                 const float* hI, const ListTest& T) {
+    const bool Ip = I < S.Tp, Jp = J < S.Tp;
+    if (T.cluster) {
+        if (!Jp) return -1;
+        const float d2 = box_d2(S, oI, hI, J, T);
+        return d2 < (Ip ? T.R2same : T.R2cross) ? J : -1;
+    }
+    const float d2 = box_d2(S, oI, hI, J, T);
+    if (Ip && Jp) {
+        if (!(d2 < T.R2same)) return -1;
+        return J | (d2 < T.R2nuc ? kNucBit : 0);
+    }
+    return d2 < T.R2cross ? (J | kNucBit) : -1;
+}
+
+__global__ void k_lcount(EngineDev E, int mode, int only) {
+    if (mode == 0 && !*E.any_rebuild) return;
+    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= E.ntiles) return;
+    const int s = E.tile_sys[g];
+    if (s < 0 || (only >= 0 && s != only)) return;
+    const SysConst& S = E.sys[s];
+    SysState* st = S.st;
+    if (mode == 0 && !sys_rebuilds(S)) return;
+    const int I = g - S.tile_base;
+    if (I == 0 && lane == 0 && mode == 0) st->cur = st->cur_next;
+    if (I >= S.T) return;
+    const ListTest T = make_test(S, mode, (float)st->L);
+    const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
+    const float hI[3] = {S.thalf[3 * I], S.thalf[3 * I + 1], S.thalf[3 * I + 2]};
+    int cnt = 0;
+    const int Jend = T.cluster ? S.Tp : S.T;
+    for (int J0 = 0; J0 < Jend; J0 += 32) {
+        const int J = J0 + lane;
+        const bool hit = J < Jend && list_entry(S, I, J, oI, hI, T) >= 0;
+        cnt += __popc(__ballot_sync(0xffffffffu, hit));
+    }
+    if (lane == 0) (mode ? S.cl->count : S.lcount)[I] = cnt;
+}
+
+// One block per system: exclusive scan of the tile counts.
+__global__ void k_lscan(EngineDev E, int mode, int only) {
+    if (mode == 0 && !*E.any_rebuild) return;
+    const int s = blockIdx.x;
+    if (only >= 0 && s != only) return;
+    const SysConst& S = E.sys[s];
+    SysState* st = S.st;
+    if (mode == 0 && !sys_rebuilds(S)) return;
+    __shared__ unsigned sm[33];
+    const int* cnt = mode ? S.cl->count : S.lcount;
+    int* start = mode ? S.cl->start : S.lstart;
+    const int per = (S.T + blockDim.x - 1) / blockDim.x;
+    const int t0 = threadIdx.x * per;
+    unsigned sum = 0;
+    for (int k = 0; k < per; ++k)
+        if (t0 + k < S.T) sum += (unsigned)cnt[t0 + k];
+    unsigned tot;
+    unsigned run = block_exscan(sum, sm, &tot);
+    for (int k = 0; k < per; ++k)
+        if (t0 + k < S.T) {
+            start[t0 + k] = (int)run;
+            run += (unsigned)cnt[t0 + k];
+        }
+    if (threadIdx.x == 0) {
+        start[S.T] = (int)tot;
+        if (mode) *S.cl->total = tot;
+        else st->list_total = tot;
+    }
+}
+
+__global__ void k_lwrite(EngineDev E, int mode, int only) {
+    if (mode == 0 && !*E.any_rebuild) return;
+    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= E.ntiles) return;
+    const int s = E.tile_sys[g];
+    if (s < 0 || (only >= 0 && s != only)) return;
+    const SysConst& S = E.sys[s];
+    SysState* st = S.st;
+    if (mode == 0 && !sys_rebuilds(S)) return;
+    const int I = g - S.tile_base;
+    if (I >= S.T) return;
+    const ListTest T = make_test(S, mode, (float)st->L);
+    const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
+    const float hI[3] = {S.thalf[3 * I], S.thalf[3 * I + 1], S.thalf[3 * I + 2]};
+    int* lst = mode ? S.cl->list : S.list;
+    int out = (mode ? S.cl->start : S.lstart)[I];
+    const int Jend = T.cluster ? S.Tp : S.T;
+    for (int J0 = 0; J0 < Jend; J0 += 32) {
+        const int J = J0 + lane;
+        const int e = J < Jend ? list_entry(S, I, J, oI, hI, T) : -1;
+        const unsigned m = __ballot_sync(0xffffffffu, e >= 0);
+        if (e >= 0) lst[out + __popc(m & ((1u << lane) - 1u))] = e;
+        out += __popc(m);
+    }
+    // small boxes: tiles are too large for one image per tile pair
+    if (I == 0 && lane == 0 && mode == 0) {
+        const float hm = __uint_as_float(st->hmax);
+        const double rmax = (S.coulomb ? fmax(S.r_C, S.r_nuc) : S.r_nuc);
+        st->need_wrap = (rmax + S.skin + 2.0 * (double)hm + 1e-3 >= 0.5 * st->L) ? 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int only) {
+    const EngineDev& E = H.dev;
+    const int nb = (E.ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
+    const int nscan = (int)((E.nbins_total + kScanChunk - 1) / kScanChunk);
+    H.rec("decide", s);
+    k_decide<<<1, 1024, 0, s>>>(E, forced_only, only);
+    H.rec("hist", s);
+    k_hist<<<nb, kBlock, 0, s>>>(E);
+    H.rec("scan", s);
+    k_scan_reduce<<<nscan, 1024, 0, s>>>(E);
+    k_scan_top<<<1, 1024, 0, s>>>(E, nscan);
+    k_scan_down<<<nscan, 1024, 0, s>>>(E);
+    H.rec("scatter", s);
+    k_scatter<<<nb, kBlock, 0, s>>>(E);
+    H.rec("move", s);
+    k_move<<<nb, kBlock, 0, s>>>(E);
+    H.rec("tiles", s);
+    k_tiles<<<nb, kBlock, 0, s>>>(E);
+    H.rec("lcount", s);
+    k_lcount<<<nb, kBlock, 0, s>>>(E, 0, -1);
+    H.rec("lscan", s);
+    k_lscan<<<E.nsys, 1024, 0, s>>>(E, 0, -1);
+    H.rec("lwrite", s);
+    k_lwrite<<<nb, kBlock, 0, s>>>(E, 0, -1);
+    H.count(11);
+}
+
+// phase 0: count and scan (host then checks capacity); phase 1: write.
+void launch_cluster_lists(const EngineHost& H, cudaStream_t s, int phase, int only) {
+    const EngineDev& E = H.dev;
+    const int nb = (E.ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
+    if (phase == 0) {
+        H.rec("cl_lcount", s);
+        k_lcount<<<nb, kBlock, 0, s>>>(E, 1, only);
+        k_lscan<<<E.nsys, 1024, 0, s>>>(E, 1, only);
+        H.count(2);
+    } else {
+        H.rec("cl_lwrite", s);
+        k_lwrite<<<nb, kBlock, 0, s>>>(E, 1, only);
+        H.count(1);
+    }
+}
+
+}  // namespace pasta

@@ -1,0 +1,230 @@
+// Cluster algorithm of Sec. II.C on the GPU.
+//
+// Protons closer than r_pp (nearest image) are linked; the connected
+// components are the clusters (lock-free union-find with hooking of the
+// larger root onto the smaller one).  Each cluster is labelled by its
+// smallest original proton index.  A neutron joins the cluster of its
+// nearest proton closer than r_np (equal distances: smaller proton index),
+// otherwise it is free.  Candidate pairs come from the current tiles: their
+// boxes (taken at the last pair-list rebuild) are tested against r + skin,
+// which covers every particle's drift since then.  The link and assignment
+// decisions use FP64 squared distances evaluated as
+//   dx = x_i - x_j; nearest image by comparison with L/2;
+//   d2 = (dx*dx + dy*dy) + dz*dz        (no fused multiply-add)
+// so they are exact and identical to a serial FP64 evaluation.
+#include "kernels.h"
+
+namespace pasta {
+
+namespace {
+
+__device__ __forceinline__ double d2_exact(double xi, double yi, double zi, double xj, double yj, double zj,
+                                           double L, double hL) {
+    double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj), dz = __dsub_rn(zi, zj);
+    if (dx > hL) dx = __dsub_rn(dx, L); else if (dx < -hL) dx = __dadd_rn(dx, L);
+    if (dy > hL) dy = __dsub_rn(dy, L); else if (dy < -hL) dy = __dadd_rn(dy, L);
+    if (dz > hL) dz = __dsub_rn(dz, L); else if (dz < -hL) dz = __dadd_rn(dz, L);
+    double s = __dmul_rn(dx, dx);
+    s = __dadd_rn(s, __dmul_rn(dy, dy));
+    s = __dadd_rn(s, __dmul_rn(dz, dz));
+    return s;
+}
+
+// Roots only ever hook onto smaller roots and path halving only shortens
+// paths, so the chain is acyclic; the bound is a safety net.
+__device__ inline int uf_find(int* parent, int a) {
+    int p = ((volatile int*)parent)[a];
+    for (int it = 0; p != a && it < (1 << 26); ++it) {
+        const int gp = ((volatile int*)parent)[p];
+        if (gp != p) atomicCAS(&parent[a], p, gp);   // path halving
+        a = p;
+        p = gp;
+    }
+    return a;
+}
+
+__device__ inline void uf_union(int* parent, int a, int b) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        a = uf_find(parent, a);
+        b = uf_find(parent, b);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(&parent[a], a, b) == a) return;
+    }
+}
+
+constexpr int kCW = 4;   // warps per block
+
+}  // namespace
+
+// Proton slots [0, Np): parent = self; minid/zc/ac cleared; outputs cleared.
+__global__ void k_cl_init(EngineDev E, int only) {
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < S.Np) {
+        B.parent[i] = i;
+        B.minid[i] = 0x7fffffff;
+        B.zc[i] = 0;
+        B.ac[i] = 0;
+    }
+    if (i <= S.N) B.hist_A[i] = 0;
+    if (i <= S.Np) B.hist_Z[i] = 0;
+    if (i < 8) B.stats[i] = 0;
+}
+
+// Warp per proton tile: link proton pairs closer than r_pp.
+__global__ void k_cl_link(EngineDev E, int only) {
+    __shared__ double sb[kCW][3][kTile];
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int I = blockIdx.x * kCW + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (I >= S.Tp) return;
+    const SysState* st = S.st;
+    const double L = st->L, hL = 0.5 * L, r2c = S.r_pp * S.r_pp;
+    const int N = S.N;
+    const double* x = S.x[st->cur];
+    const int p = I * kTile + lane;
+    const bool valid = p < S.Np;
+    const double xi = valid ? x[p] : 0, yi = valid ? x[N + p] : 0, zi = valid ? x[2 * N + p] : 0;
+    for (int e = B.start[I]; e < B.start[I + 1]; ++e) {
+        const int J = B.list[e];
+        const int q = J * kTile + lane;
+        const bool qv = q < S.Np;
+        __syncwarp();
+        sb[w][0][lane] = qv ? x[q] : 0;
+        sb[w][1][lane] = qv ? x[N + q] : 0;
+        sb[w][2][lane] = qv ? x[2 * N + q] : 0;
+        __syncwarp();
+        if (!valid) continue;
+        const int nq = min(kTile, S.Np - J * kTile);
+        for (int k = 0; k < nq; ++k) {
+            const int qq = J * kTile + k;
+            if (qq <= p) continue;
+            if (d2_exact(xi, yi, zi, sb[w][0][k], sb[w][1][k], sb[w][2][k], L, hL) < r2c)
+                uf_union(B.parent, p, qq);
+        }
+    }
+}
+
+// Smallest original index per component.
+__global__ void k_cl_minid(EngineDev E, int only) {
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= S.Np) return;
+    const int r = uf_find(B.parent, q);
+    atomicMin(&B.minid[r], S.id[S.st->cur][q]);
+}
+
+// Proton labels; neutron assignment (warp per neutron tile).
+__global__ void k_cl_assign(EngineDev E, int only) {
+    __shared__ double sb[kCW][3][kTile];
+    __shared__ int sid[kCW][kTile];
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int I = blockIdx.x * kCW + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (I >= S.T) return;
+    const SysState* st = S.st;
+    const int c = st->cur, N = S.N;
+    const double* x = S.x[c];
+    const int p = tile_slot0(S, I) + lane;
+    const bool valid = p < tile_end(S, I);
+    if (I < S.Tp) {
+        if (valid) B.label[p] = B.minid[uf_find(B.parent, p)];
+        return;
+    }
+    const double L = st->L, hL = 0.5 * L, r2c = S.r_np * S.r_np;
+    const double xi = valid ? x[p] : 0, yi = valid ? x[N + p] : 0, zi = valid ? x[2 * N + p] : 0;
+    double best_d2 = 0.0;
+    int best_id = -1, best_slot = -1;
+    for (int e = B.start[I]; e < B.start[I + 1]; ++e) {
+        const int J = B.list[e];
+        const int q = J * kTile + lane;
+        const bool qv = q < S.Np;
+        __syncwarp();
+        sb[w][0][lane] = qv ? x[q] : 0;
+        sb[w][1][lane] = qv ? x[N + q] : 0;
+        sb[w][2][lane] = qv ? x[2 * N + q] : 0;
+        sid[w][lane] = qv ? S.id[c][q] : 0;
+        __syncwarp();
+        if (!valid) continue;
+        const int nq = min(kTile, S.Np - J * kTile);
+        for (int k = 0; k < nq; ++k) {
+            const double d2 = d2_exact(xi, yi, zi, sb[w][0][k], sb[w][1][k], sb[w][2][k], L, hL);
+            if (d2 < r2c) {
+                const int oid = sid[w][k];
+                if (best_id < 0 || d2 < best_d2 || (d2 == best_d2 && oid < best_id)) {
+                    best_d2 = d2;
+                    best_id = oid;
+                    best_slot = J * kTile + k;
+                }
+            }
+        }
+    }
+    if (valid) B.label[p] = best_slot < 0 ? -1 : B.minid[uf_find(B.parent, best_slot)];
+}
+
+// Per-cluster counts (labels are original proton indices < Np).
+__global__ void k_cl_count(EngineDev E, int only) {
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.N) return;
+    const int lab = B.label[p];
+    if (lab < 0) {
+        atomicAdd((unsigned long long*)&B.stats[1], 1ull);
+        return;
+    }
+    atomicAdd(&B.ac[lab], 1);
+    if (p < S.Np) atomicAdd(&B.zc[lab], 1);
+}
+
+// Histograms over clusters; labels written in original order.
+__global__ void k_cl_hist(EngineDev E, int only, int32_t* labels_out) {
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.N) return;
+    const int i = S.id[S.st->cur][p];
+    const int lab = B.label[p];
+    if (labels_out) labels_out[i] = lab;
+    if (p < S.Np && lab == i) {
+        const int A = B.ac[i], Z = B.zc[i];
+        atomicAdd((unsigned long long*)&B.hist_A[A], 1ull);
+        atomicAdd((unsigned long long*)&B.hist_Z[Z], 1ull);
+        atomicAdd((unsigned long long*)&B.stats[0], 1ull);
+        if (A >= 12) {
+            atomicAdd((unsigned long long*)&B.stats[2], 1ull);
+            atomicAdd((unsigned long long*)&B.stats[3], (unsigned long long)A);
+            atomicAdd((unsigned long long*)&B.stats[4], (unsigned long long)Z);
+        }
+    }
+}
+
+void launch_clusters(const EngineHost& H, cudaStream_t s, int only, int Np, int N, int Tp, int T,
+                     int32_t* d_labels_out) {
+    const EngineDev& E = H.dev;
+    const int n1 = (N + 1 + 255) / 256;
+    H.rec("cl_init", s);
+    k_cl_init<<<n1, 256, 0, s>>>(E, only);
+    H.rec("cl_link", s);
+    if (Tp > 0) k_cl_link<<<(Tp + kCW - 1) / kCW, kCW * 32, 0, s>>>(E, only);
+    H.rec("cl_minid", s);
+    if (Np > 0) k_cl_minid<<<(Np + 255) / 256, 256, 0, s>>>(E, only);
+    H.rec("cl_assign", s);
+    k_cl_assign<<<(T + kCW - 1) / kCW, kCW * 32, 0, s>>>(E, only);
+    H.rec("cl_count", s);
+    k_cl_count<<<(N + 255) / 256, 256, 0, s>>>(E, only);
+    H.rec("cl_hist", s);
+    k_cl_hist<<<(N + 255) / 256, 256, 0, s>>>(E, only, d_labels_out);
+    H.count(6);
+}
+
+}  // namespace pasta

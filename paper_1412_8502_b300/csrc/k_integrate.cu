@@ -1,0 +1,514 @@
+// Integrator and reductions (Sec. II.A): velocity Verlet, box growth of
+// Eq. (3) without rescaling positions, isothermal velocity rescale every
+// `thermostat_every` steps, FP64 kinetic/potential energy reductions in a
+// fixed order, the seeded initial state and steepest-descent relaxation.
+//
+// Step order (velocity Verlet, then the box grows):
+//   k_kick_drift  v += dt/(2M) F;  x += dt v;  wrap into [0, L_n);
+//                 displacement and FP32 tile-local coordinates refreshed
+//   [rebuild chain if needed]  ->  forces at (x, L_n)
+//   k_kick        v += dt/(2M) F;  per-block sum v^2
+//   k_finalize    t += dt; step += 1; L = L_base (1 + xi (t - t_base));
+//                 thermostat factor when step % thermostat_every == 0
+//   k_rescale     v *= factor (when one is pending)
+#include "kernels.h"
+
+namespace pasta {
+
+namespace {
+
+struct Slot {
+    int s, t, p;
+    bool valid;
+};
+
+__device__ inline bool slot_of(const EngineDev& E, int only, Slot& o) {
+    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    if (g >= E.ntiles) return false;
+    const int s = E.tile_sys[g];
+    if (s < 0 || (only >= 0 && s != only)) return false;
+    const SysConst& S = E.sys[s];
+    const int t = g - S.tile_base;
+    o.s = s;
+    o.t = t;
+    o.p = (t < S.T) ? tile_slot0(S, t) + (threadIdx.x & 31) : 0;
+    o.valid = (t < S.T) && o.p < tile_end(S, t);
+    return true;
+}
+
+// Block index of this block within its system (blocks never span systems).
+__device__ inline int sys_block(const SysConst& S) {
+    return blockIdx.x - S.tile_base / kTilesPerBlock;
+}
+__device__ inline int sys_nblocks(const SysConst& S) {
+    return (S.T + kTilesPerBlock - 1) / kTilesPerBlock;
+}
+
+// Fixed-order block sum of up to 4 doubles into S.blk[blockIdx * 4 + k].
+__device__ inline void block_sum4(const SysConst& S, double a, double b, double c, double d) {
+    __shared__ double sm[kTilesPerBlock][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    d = warp_sum(d);
+    if (lane == 0) {
+        sm[w][0] = a;
+        sm[w][1] = b;
+        sm[w][2] = c;
+        sm[w][3] = d;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double r = 0.0;
+        for (int k = 0; k < kTilesPerBlock; ++k) r += sm[k][threadIdx.x];
+        S.blk[4 * sys_block(S) + threadIdx.x] = r;
+    }
+}
+
+__device__ inline uint64_t splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ inline double u01(uint64_t seed, uint64_t k) {
+    return __dmul_rn((double)(splitmix64(seed, k) >> 11), 0x1.0p-53);
+}
+
+template <typename FT>
+__device__ inline const FT* cur_force(const SysConst& S, int cur);
+template <>
+__device__ inline const float* cur_force<float>(const SysConst& S, int cur) { return S.f32[cur]; }
+template <>
+__device__ inline const double* cur_force<double>(const SysConst& S, int cur) { return S.f64[cur]; }
+
+// Refresh the FP32 local coordinates of slot p in tile t.
+__device__ inline void write_local(const SysConst& S, int t, int lane, const double* xs, double L) {
+    const double hL = 0.5 * L;
+    float4 l;
+    l.x = (float)min_image(xs[0] - S.torg[3 * t], L, hL);
+    l.y = (float)min_image(xs[1] - S.torg[3 * t + 1], L, hL);
+    l.z = (float)min_image(xs[2] - S.torg[3 * t + 2], L, hL);
+    l.w = 0.0f;
+    S.tpos[t * kTile + lane] = l;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- init
+// Slot p = particle p (identity order).  Reading of Sec. III.B: uniform
+// positions U(3p+a) L; Box-Muller Gaussians from draws 3N + 2m, 3N + 2m + 1.
+__global__ void k_init_rng(EngineDev E, const unsigned long long* seeds) {
+    Slot o;
+    if (!slot_of(E, -1, o) || !o.valid) return;
+    const SysConst& S = E.sys[o.s];
+    const int N = S.N, p = o.p;
+    const uint64_t seed = seeds[o.s];
+    const double L = S.st->L;
+    const double sigma = sqrt(S.T_target / S.M);
+    const double two_pi = 6.283185307179586;
+    for (int a = 0; a < 3; ++a) {
+        const uint64_t k = 3ull * p + a;
+        S.x[0][a * N + p] = __dmul_rn(u01(seed, k), L);
+        const uint64_t m = k / 2;
+        const double u1 = u01(seed, 3ull * N + 2 * m);
+        const double u2 = u01(seed, 3ull * N + 2 * m + 1);
+        const double rad = sqrt(-2.0 * log(1.0 - u1));
+        const double ang = __dmul_rn(two_pi, u2);
+        const double gz = (k % 2 == 0) ? rad * cos(ang) : rad * sin(ang);
+        S.v[0][a * N + p] = __dmul_rn(sigma, gz);
+    }
+    S.id[0][p] = p;
+}
+
+// Per-block sums: mode 0 -> sum v (3 comps), mode 1 -> sum v^2.
+__global__ void k_vsum(EngineDev E, int mode, int only) {
+    Slot o;
+    if (!slot_of(E, only, o)) return;
+    const SysConst& S = E.sys[o.s];
+    const int c = S.st->cur, N = S.N, p = o.p;
+    double a = 0, b = 0, d = 0;
+    if (o.valid) {
+        const double vx = S.v[c][p], vy = S.v[c][N + p], vz = S.v[c][2 * N + p];
+        if (mode == 0) {
+            a = vx; b = vy; d = vz;
+        } else {
+            a = vx * vx + vy * vy + vz * vz;
+        }
+    }
+    block_sum4(S, a, b, d, 0.0);
+}
+
+// One warp per system: fixed-order sum of the system's block partials.
+__device__ inline double sys_sum(const SysConst& S, int k, int lane) {
+    double r = 0.0;
+    const int nb = sys_nblocks(S);
+    for (int b = lane; b < nb; b += 32) r += S.blk[4 * b + k];
+    return warp_sum(r);
+}
+
+// Remove the centre-of-mass velocity (mode 0) or set the rescale factor
+// to reach KE = 3/2 N T (mode 1).
+__global__ void k_init_fix(EngineDev E, int mode) {
+    const int s = blockIdx.x;
+    const SysConst& S = E.sys[s];
+    SysState* st = S.st;
+    const int lane = threadIdx.x;
+    if (mode == 0) {
+        const double sx = sys_sum(S, 0, lane), sy = sys_sum(S, 1, lane), sz = sys_sum(S, 2, lane);
+        if (lane == 0) {
+            st->scratch[0] = sx / S.N;
+            st->scratch[1] = sy / S.N;
+            st->scratch[2] = sz / S.N;
+        }
+    } else {
+        const double v2 = sys_sum(S, 0, lane);
+        if (lane == 0) {
+            const double ke = 0.5 * S.M * v2;
+            st->vscale = ke > 0.0 ? sqrt(1.5 * (double)S.N * S.T_target / ke) : 0.0;
+            st->KE = ke * st->vscale * st->vscale;
+        }
+    }
+}
+
+__global__ void k_sub_com(EngineDev E) {
+    Slot o;
+    if (!slot_of(E, -1, o) || !o.valid) return;
+    const SysConst& S = E.sys[o.s];
+    const SysState* st = S.st;
+    const int N = S.N, p = o.p;
+    S.v[0][p] -= st->scratch[0];
+    S.v[0][N + p] -= st->scratch[1];
+    S.v[0][2 * N + p] -= st->scratch[2];
+}
+
+__global__ void k_rescale(EngineDev E, int only) {
+    Slot o;
+    if (!slot_of(E, only, o) || !o.valid) return;
+    const SysConst& S = E.sys[o.s];
+    const SysState* st = S.st;
+    const double f = st->vscale;
+    if (f == 1.0) return;
+    const int c = st->cur, N = S.N, p = o.p;
+    S.v[c][p] *= f;
+    S.v[c][N + p] *= f;
+    S.v[c][2 * N + p] *= f;
+}
+
+// ---------------------------------------------------------------- relax
+// Steepest descent (reading of the paper's equilibration from random
+// positions): x += gamma F, |dx| clamped to dmax, wrapped.
+template <typename FT>
+__global__ void k_sd_update(EngineDev E) {
+    Slot o;
+    if (!slot_of(E, -1, o)) return;
+    const SysConst& S = E.sys[o.s];
+    SysState* st = S.st;
+    const int lane = threadIdx.x & 31;
+    float d2 = 0.0f;
+    if (o.valid) {
+        const int c = st->cur, N = S.N, p = o.p;
+        const FT* F = cur_force<FT>(S, c);
+        double d[3];
+        for (int a = 0; a < 3; ++a) d[a] = S.relax_gamma * (double)F[a * N + p];
+        const double m = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (m > S.relax_dmax) {
+            const double sc = S.relax_dmax / m;
+            for (int a = 0; a < 3; ++a) d[a] *= sc;
+        }
+        const double L = st->L;
+        double xs[3];
+        for (int a = 0; a < 3; ++a) {
+            xs[a] = wrap_box(S.x[c][a * N + p] + d[a], L);
+            S.x[c][a * N + p] = xs[a];
+            const float dd = S.disp[a * N + p] + (float)d[a];
+            S.disp[a * N + p] = dd;
+            d2 = fmaf(dd, dd, d2);
+        }
+        write_local(S, o.t, lane, xs, L);
+    }
+    d2 = warp_max(d2);
+    if (lane == 0 && d2 > 0.0f) atomic_max_pos(&st->maxdisp2, d2);
+}
+
+// ---------------------------------------------------------------- Verlet
+template <typename FT>
+__global__ void k_kick_drift(EngineDev E) {
+    Slot o;
+    if (!slot_of(E, -1, o)) return;
+    const SysConst& S = E.sys[o.s];
+    SysState* st = S.st;
+    const int lane = threadIdx.x & 31;
+    float d2 = 0.0f;
+    if (o.valid) {
+        const int c = st->cur, N = S.N, p = o.p;
+        const FT* F = cur_force<FT>(S, c);
+        const double h = 0.5 * S.dt / S.M, dt = S.dt, L = st->L;
+        double xs[3];
+        for (int a = 0; a < 3; ++a) {
+            const double v = S.v[c][a * N + p] + h * (double)F[a * N + p];
+            S.v[c][a * N + p] = v;
+            xs[a] = wrap_box(S.x[c][a * N + p] + dt * v, L);
+            S.x[c][a * N + p] = xs[a];
+            const float dd = S.disp[a * N + p] + (float)(dt * v);
+            S.disp[a * N + p] = dd;
+            d2 = fmaf(dd, dd, d2);
+        }
+        write_local(S, o.t, lane, xs, L);
+    }
+    d2 = warp_max(d2);
+    if (lane == 0 && d2 > 0.0f) atomic_max_pos(&st->maxdisp2, d2);
+}
+
+template <typename FT>
+__global__ void k_kick(EngineDev E) {
+    Slot o;
+    if (!slot_of(E, -1, o)) return;
+    const SysConst& S = E.sys[o.s];
+    const SysState* st = S.st;
+    double v2 = 0.0;
+    if (o.valid) {
+        const int c = st->cur, N = S.N, p = o.p;
+        const FT* F = cur_force<FT>(S, c);
+        const double h = 0.5 * S.dt / S.M;
+        for (int a = 0; a < 3; ++a) {
+            const double v = S.v[c][a * N + p] + h * (double)F[a * N + p];
+            S.v[c][a * N + p] = v;
+            v2 += v * v;
+        }
+    }
+    block_sum4(S, v2, 0.0, 0.0, 0.0);
+}
+
+// One warp per system.  energy: also sum the per-tile PE partials.
+__global__ void k_finalize(EngineDev E, int energy) {
+    const int s = blockIdx.x;
+    const SysConst& S = E.sys[s];
+    SysState* st = S.st;
+    const int lane = threadIdx.x;
+    const double v2 = sys_sum(S, 0, lane);
+    double pn = 0, pc = 0, w = 0, cn = 0, cc = 0;
+    if (energy) {
+        for (int t = lane; t < S.T; t += 32) {
+            pn += S.tile_e[8 * t];
+            pc += S.tile_e[8 * t + 1];
+            w += S.tile_e[8 * t + 2];
+            cn += S.tile_e[8 * t + 3];
+            cc += S.tile_e[8 * t + 4];
+        }
+        pn = warp_sum(pn);
+        pc = warp_sum(pc);
+        w = warp_sum(w);
+        cn = warp_sum(cn);
+        cc = warp_sum(cc);
+    }
+    if (lane != 0) return;
+    const double Lf = st->L;
+    st->L_F = Lf;
+    st->t = __dadd_rn(st->t, S.dt);
+    st->step += 1;
+    st->L = __dmul_rn(st->L_base, __dadd_rn(1.0, __dmul_rn(st->xi_dot, __dsub_rn(st->t, st->t_base))));
+    double ke = 0.5 * S.M * v2;
+    double f = 1.0;
+    if (S.thermostat_every > 0 && (st->step % S.thermostat_every) == 0 && ke > 0.0) {
+        f = sqrt(1.5 * (double)S.N * S.T_target / ke);
+        ke *= f * f;
+    }
+    st->vscale = f;
+    if (energy) {
+        st->KE = ke;
+        st->PE_nuc = pn;
+        st->PE_coul = pc;
+        st->virial = w;
+        st->e_L = Lf;
+        st->e_t = st->t;
+        st->e_step = st->step;
+        st->e_pairs_nuc = (int64_t)cn;
+        st->e_pairs_coul = (int64_t)cc;
+        st->have_energy = 1;
+    }
+}
+
+// Energies at the current state (md_energy): KE from the block partials of
+// k_vsum(mode 1), PE from the tile partials of an energy force pass.
+__global__ void k_energy_now(EngineDev E, int only, double* out) {
+    const int s = blockIdx.x;
+    if (only >= 0 && s != only) return;
+    const SysConst& S = E.sys[s];
+    const SysState* st = S.st;
+    const int lane = threadIdx.x;
+    const double v2 = sys_sum(S, 0, lane);
+    double pn = 0, pc = 0, w = 0, cn = 0, cc = 0;
+    for (int t = lane; t < S.T; t += 32) {
+        pn += S.tile_e[8 * t];
+        pc += S.tile_e[8 * t + 1];
+        w += S.tile_e[8 * t + 2];
+        cn += S.tile_e[8 * t + 3];
+        cc += S.tile_e[8 * t + 4];
+    }
+    pn = warp_sum(pn);
+    pc = warp_sum(pc);
+    w = warp_sum(w);
+    cn = warp_sum(cn);
+    cc = warp_sum(cc);
+    if (lane == 0) {
+        out[0] = 0.5 * S.M * v2;
+        out[1] = pn;
+        out[2] = pc;
+        out[3] = w;
+        out[4] = st->L;
+        out[5] = st->t;
+        out[6] = (double)st->step;
+        out[7] = cn;
+        out[8] = cc;
+    }
+}
+
+// ---------------------------------------------------------------- exchange
+// Gather current state to original particle order (AoS [N][3]).
+template <typename FT>
+__global__ void k_gather(EngineDev E, int only, double* ox, double* ov, double* of, int8_t* otype) {
+    Slot o;
+    if (!slot_of(E, only, o) || !o.valid) return;
+    const SysConst& S = E.sys[o.s];
+    const SysState* st = S.st;
+    const int c = st->cur, N = S.N, p = o.p;
+    const int i = S.id[c][p];
+    const FT* F = cur_force<FT>(S, c);
+    for (int a = 0; a < 3; ++a) {
+        if (ox) ox[3 * i + a] = S.x[c][a * N + p];
+        if (ov) ov[3 * i + a] = S.v[c][a * N + p];
+        if (of) of[3 * i + a] = (double)F[a * N + p];
+    }
+    if (otype) otype[i] = (int8_t)(i < S.Np ? 1 : 0);
+}
+
+// Load a caller state (AoS, original order) into slot order = identity.
+__global__ void k_scatter_state(EngineDev E, int only, const double* ix, const double* iv) {
+    Slot o;
+    if (!slot_of(E, only, o) || !o.valid) return;
+    const SysConst& S = E.sys[o.s];
+    const SysState* st = S.st;
+    const int N = S.N, p = o.p;
+    const double L = st->L;
+    for (int a = 0; a < 3; ++a) {
+        S.x[0][a * N + p] = wrap_box(ix[3 * p + a], L);
+        S.v[0][a * N + p] = iv[3 * p + a];
+        S.disp[a * N + p] = 0.0f;
+    }
+    S.id[0][p] = p;
+}
+
+// Clock and bookkeeping of a loaded state: d_clock = {L, L_base, t, t_base,
+// xi_dot, step, L_F}.  Slot order becomes the identity; forces are stale.
+__global__ void k_set_clock(EngineDev E, int only, const double* c) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= E.nsys || (only >= 0 && s != only)) return;
+    SysState* st = E.sys[s].st;
+    st->L = c[0];
+    st->L_base = c[1];
+    st->t = c[2];
+    st->t_base = c[3];
+    st->xi_dot = c[4];
+    st->step = (int64_t)c[5];
+    st->L_F = c[6];
+    st->cur = 0;
+    st->cur_next = 0;
+    st->force_rebuild = 1;
+    st->maxdisp2 = 0u;
+    st->vscale = 1.0;
+    st->have_energy = 0;
+    st->last_build = st->step;
+}
+
+// Re-base Eq. (3) at the current time when the expansion rate changes.
+__global__ void k_set_rate(EngineDev E, int only, double xi) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= E.nsys || (only >= 0 && s != only)) return;
+    SysState* st = E.sys[s].st;
+    if (st->xi_dot != xi) {
+        st->L_base = st->L;
+        st->t_base = st->t;
+        st->xi_dot = xi;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+static inline int nblk(const EngineDev& E) { return (E.ntiles + kTilesPerBlock - 1) / kTilesPerBlock; }
+
+void launch_init(const EngineHost& H, cudaStream_t s, const unsigned long long* d_seeds) {
+    const EngineDev& E = H.dev;
+    k_init_rng<<<nblk(E), kBlock, 0, s>>>(E, d_seeds);
+    k_vsum<<<nblk(E), kBlock, 0, s>>>(E, 0, -1);
+    k_init_fix<<<E.nsys, 32, 0, s>>>(E, 0);
+    k_sub_com<<<nblk(E), kBlock, 0, s>>>(E);
+    k_vsum<<<nblk(E), kBlock, 0, s>>>(E, 1, -1);
+    k_init_fix<<<E.nsys, 32, 0, s>>>(E, 1);
+    k_rescale<<<nblk(E), kBlock, 0, s>>>(E, -1);
+    H.count(7);
+}
+
+void launch_sd_update(const EngineHost& H, cudaStream_t s) {
+    const EngineDev& E = H.dev;
+    H.rec("sd_update", s);
+    if (H.precision == 1) k_sd_update<double><<<nblk(E), kBlock, 0, s>>>(E);
+    else k_sd_update<float><<<nblk(E), kBlock, 0, s>>>(E);
+    H.count(1);
+}
+
+void launch_kick_drift(const EngineHost& H, cudaStream_t s) {
+    const EngineDev& E = H.dev;
+    H.rec("kick_drift", s);
+    if (H.precision == 1) k_kick_drift<double><<<nblk(E), kBlock, 0, s>>>(E);
+    else k_kick_drift<float><<<nblk(E), kBlock, 0, s>>>(E);
+    H.count(1);
+}
+
+void launch_kick_finalize(const EngineHost& H, cudaStream_t s, bool energy) {
+    const EngineDev& E = H.dev;
+    H.rec("kick", s);
+    if (H.precision == 1) k_kick<double><<<nblk(E), kBlock, 0, s>>>(E);
+    else k_kick<float><<<nblk(E), kBlock, 0, s>>>(E);
+    H.rec("finalize", s);
+    k_finalize<<<E.nsys, 32, 0, s>>>(E, energy ? 1 : 0);
+    H.rec("rescale", s);
+    k_rescale<<<nblk(E), kBlock, 0, s>>>(E, -1);
+    H.count(3);
+}
+
+void launch_energy_now(const EngineHost& H, cudaStream_t s, int only, double* d_out) {
+    const EngineDev& E = H.dev;
+    k_vsum<<<nblk(E), kBlock, 0, s>>>(E, 1, only);
+    launch_force(H, s, true, only, 1);
+    k_energy_now<<<E.nsys, 32, 0, s>>>(E, only, d_out);
+    H.count(2);
+}
+
+void launch_gather(const EngineHost& H, cudaStream_t s, int only, double* ox, double* ov, double* of,
+                   int8_t* otype) {
+    const EngineDev& E = H.dev;
+    if (H.precision == 1) k_gather<double><<<nblk(E), kBlock, 0, s>>>(E, only, ox, ov, of, otype);
+    else k_gather<float><<<nblk(E), kBlock, 0, s>>>(E, only, ox, ov, of, otype);
+    H.count(1);
+}
+
+void launch_set_clock(const EngineHost& H, cudaStream_t s, int only, const double* d_clock) {
+    const EngineDev& E = H.dev;
+    k_set_clock<<<(E.nsys + 127) / 128, 128, 0, s>>>(E, only, d_clock);
+    H.count(1);
+}
+
+void launch_set_rate(const EngineHost& H, cudaStream_t s, int only, double xi_dot) {
+    const EngineDev& E = H.dev;
+    k_set_rate<<<(E.nsys + 127) / 128, 128, 0, s>>>(E, only, xi_dot);
+    H.count(1);
+}
+
+void launch_scatter_state(const EngineHost& H, cudaStream_t s, int only, const double* ix, const double* iv) {
+    const EngineDev& E = H.dev;
+    k_scatter_state<<<nblk(E), kBlock, 0, s>>>(E, only, ix, iv);
+    H.count(1);
+}
+
+}  // namespace pasta

@@ -1,0 +1,59 @@
+// Launchers of the device kernels and the host view of an engine.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "md_device.cuh"
+
+namespace pasta {
+
+// Buffers of the on-demand cluster analysis (allocated on first use).
+struct ClusterBufs {
+    int* parent;             // [Np] union-find over sorted proton slots
+    int* minid;              // [Np] smallest original index per root
+    int* zc;                 // [Np] protons per cluster label
+    int* ac;                 // [Np] nucleons per cluster label
+    int* label;              // [N] label per sorted slot
+    long long* hist_A;       // [N+1]
+    long long* hist_Z;       // [Np+1]
+    long long* stats;        // [8]: clusters, free, big, sumA, sumZ
+    int* count;              // [T] candidate tiles per tile
+    int* start;              // [T+1]
+    int* list;               // [cap]
+    long long cap;
+    long long* total;        // [1] entries needed
+};
+
+// Host-side view passed to the launchers: device tables plus instrumentation
+// (event records for per-kernel timing and a launch counter).
+struct EngineHost {
+    EngineDev dev;
+    int precision = 0;
+    void* owner = nullptr;   // Engine*, for rec/count callbacks
+    void (*rec_fn)(void*, const char*, cudaStream_t) = nullptr;
+    void (*count_fn)(void*, int) = nullptr;
+    void rec(const char* name, cudaStream_t s) const {
+        if (rec_fn) rec_fn(owner, name, s);
+    }
+    void count(int n) const {
+        if (count_fn) count_fn(owner, n);
+    }
+};
+
+void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int only);
+void launch_cluster_lists(const EngineHost& H, cudaStream_t s, int phase, int only);
+void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt);
+void launch_init(const EngineHost& H, cudaStream_t s, const unsigned long long* d_seeds);
+void launch_sd_update(const EngineHost& H, cudaStream_t s);
+void launch_kick_drift(const EngineHost& H, cudaStream_t s);
+void launch_kick_finalize(const EngineHost& H, cudaStream_t s, bool energy);
+void launch_energy_now(const EngineHost& H, cudaStream_t s, int only, double* d_out);
+void launch_gather(const EngineHost& H, cudaStream_t s, int only, double* ox, double* ov, double* of,
+                   int8_t* otype);
+void launch_scatter_state(const EngineHost& H, cudaStream_t s, int only, const double* ix, const double* iv);
+void launch_set_clock(const EngineHost& H, cudaStream_t s, int only, const double* d_clock);
+void launch_set_rate(const EngineHost& H, cudaStream_t s, int only, double xi_dot);
+void launch_clusters(const EngineHost& H, cudaStream_t s, int only, int Np, int N, int Tp, int T,
+                     int32_t* d_labels_out);
+
+}  // namespace pasta

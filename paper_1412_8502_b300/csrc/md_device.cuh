@@ -1,0 +1,155 @@
+// Device-side data layout shared by the kernels of the nucleon MD library.
+//
+// One "engine" advances one or more independent systems.  Every per-system
+// quantity lives in device memory behind a SysConst descriptor; all kernels
+// take the descriptor table and work over a global space of 32-particle
+// tiles (each system's tiles start at a multiple of kTilesPerBlock, so a
+// 256-thread block never spans two systems).
+//
+// Particle storage is structure-of-arrays in the current spatially sorted
+// order: protons occupy sorted slots [0, Np), neutrons [Np, N).  Proton tile
+// t covers slots [32 t, 32 t + 32) ∩ [0, Np); neutron tile Tp + u covers
+// [Np + 32 u, ...) ∩ [Np, N).  Positions and velocities are FP64 (x[a*N + p]
+// is axis a of sorted slot p).  The force kernel reads FP32 tile-local
+// coordinates tpos[32 t + lane] = x - O_t (O_t: FP64 tile origin fixed at the
+// last pair-list rebuild), refreshed every step.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pasta {
+
+struct ClusterBufs;
+
+constexpr int kTile = 32;
+constexpr int kTilesPerBlock = 8;
+constexpr int kBlock = kTile * kTilesPerBlock;
+constexpr float kPad = 1.0e9f;          // local coordinate of an empty slot
+constexpr int kNucBit = 1 << 30;        // list entry flag: nuclear term reachable
+
+// Mutable per-system scalars (device memory).
+struct SysState {
+    double L, L_base, t, t_base, xi_dot;
+    double L_F;              // box side of the cached forces
+    double L_build;          // box side at the last rebuild
+    double KE, PE_nuc, PE_coul, virial;     // last recorded energies
+    double e_L, e_t;         // box side / time of the recorded energies
+    int64_t e_pairs_nuc, e_pairs_coul;   // in-range ordered pairs of that pass
+    double vscale;           // pending thermostat factor (1 = none)
+    int64_t step, last_build, n_rebuilds, e_step;
+    int64_t list_total;
+    double scratch[3];       // initialisation scratch (centre-of-mass velocity)
+    int cur;                 // which x/v/id/f buffer is current
+    int cur_next;            // buffer the running rebuild writes
+    int rebuild;             // this step rebuilds (set by the decision kernel)
+    int force_rebuild;       // rebuild at the next decision regardless
+    int keep_forces;         // permute cached forces during the rebuild
+    int need_wrap;           // per-pair minimum image needed in FP32
+    int have_energy;         // energies recorded by a step
+    int error;               // bit 0: non-finite force
+    unsigned maxdisp2;       // float bits of max |disp|^2 since the rebuild
+    unsigned hmax;           // float bits of max tile half-extent at rebuild
+    int pad0;
+};
+
+// Per-system constants and device pointers.
+struct SysConst {
+    int N, Np, T, Tp;        // particles, protons, tiles, proton tiles
+    int tile_base;           // first global tile (multiple of kTilesPerBlock)
+    int nbits;               // spatial-sort bits per axis
+    long long bin_base;      // first global bin (2 species x 2^(3 nbits) bins)
+    long long nbins;         // bins per species
+    long long list_cap;      // entries available in `list`
+    // physics
+    double dt, M, T_target, skin;
+    double a, b, c, Lambda, lambda_s, alpha, r_nuc, r_C;
+    double r_pp, r_np, relax_gamma, relax_dmax;
+    int thermostat_every, rebuild_every, coulomb, energy_every;
+    // state arrays (index [cur] is current)
+    double* x[2];
+    double* v[2];
+    int* id[2];
+    float* f32[2];
+    double* f64[2];
+    float* disp;             // [3N] displacement since the last rebuild
+    unsigned* key;           // [N] bin of each slot (rebuild scratch)
+    int* slot;               // [N] scatter scratch
+    float4* tpos;            // [T*32] tile-local FP32 coordinates
+    double* torg;            // [T*3] FP64 tile origins
+    float* torgf;            // [T*4] FP32 origin (x,y,z) and max half-extent
+    float* thalf;            // [T*3] tile half-extents at rebuild
+    int* lcount;             // [T]
+    int* lstart;             // [T+1]
+    int* list;               // [list_cap] tile-pair entries: J | kNucBit
+    double* tile_e;          // [T*8] per-tile PE_nuc, PE_coul, virial, pair counts
+    double* blk;             // [T/8 * 4] per-block KE partials
+    ClusterBufs* cl;         // cluster-analysis buffers (device struct)
+    SysState* st;
+};
+
+// Global tables of an engine.
+struct EngineDev {
+    const SysConst* sys;     // [nsys]
+    const int* tile_sys;     // [ntiles] global tile -> system (-1: padding)
+    int nsys;
+    int ntiles;              // global tiles (multiple of kTilesPerBlock)
+    long long nbins_total;   // global bins
+    unsigned* hist;          // [nbins_total]
+    unsigned* binstart;      // [nbins_total] exclusive scan of hist
+    unsigned* cursor;        // [nbins_total] scatter cursors
+    unsigned* blocksum;      // [scan blocks]
+    int* any_rebuild;        // set when any system rebuilds this step
+};
+
+__host__ __device__ inline int tile_slot0(const SysConst& s, int t) {
+    return t < s.Tp ? t * kTile : s.Np + (t - s.Tp) * kTile;
+}
+__host__ __device__ inline int tile_end(const SysConst& s, int t) {
+    return t < s.Tp ? min(s.Np, (t + 1) * kTile) : min(s.N, s.Np + (t - s.Tp + 1) * kTile);
+}
+
+// Wrap into [0, L): one period at most (displacements per step << L).
+__device__ inline double wrap_box(double x, double L) {
+    if (x >= L) {
+        x -= L;
+    } else if (x < 0.0) {
+        x += L;
+        if (x >= L) x = 0.0;
+    }
+    return x;
+}
+
+// Nearest image of a difference with |d| < 1.5 L, comparison form.
+__device__ inline double min_image(double d, double L, double hL) {
+    if (d > hL) d -= L;
+    else if (d < -hL) d += L;
+    return d;
+}
+
+__device__ inline float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline double warp_min(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ inline double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ inline float warp_max(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// atomicMax on the bit pattern of a non-negative float.
+__device__ inline void atomic_max_pos(unsigned* addr, float v) {
+    atomicMax(addr, __float_as_uint(fmaxf(v, 0.0f)));
+}
+
+}  // namespace pasta

@@ -1,0 +1,254 @@
+// Serving: continuous batching of MD jobs on one GPU.
+//
+// A worker thread owns all device work.  Submitted jobs wait in a FIFO; a
+// job is admitted as soon as its device footprint fits in the HBM budget
+// next to the jobs already resident.  Each admitted job keeps its state in
+// device memory on its own stream; every tick the worker enqueues a slice of
+// steps for every active job back to back, so the jobs' kernels overlap on
+// the device, then waits for the slices, records per-step latencies from
+// events on each job's stream, retires finished jobs (freeing their memory)
+// and admits waiting ones.  A job's trajectory does not depend on the other
+// jobs: each runs the same deterministic kernels as it would alone.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "engine.h"
+
+using pasta::Engine;
+using pasta::fail;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+    int64_t id;
+    md_job job;
+    size_t bytes;
+    Clock::time_point t_submit, t_admit;
+    Engine* eng = nullptr;
+    int64_t done_steps = 0;
+    std::vector<double> lat_ms;
+    std::vector<cudaEvent_t> ev;
+    int64_t slice = 0;
+};
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+double pct(std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const size_t k = (size_t)std::min<double>(v.size() - 1, std::max(0.0, q * (v.size() - 1) + 0.5));
+    return v[k];
+}
+
+}  // namespace
+
+struct md_server {
+    size_t budget;
+    md_params prm;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Job*> pending;
+    std::vector<Job*> active;
+    std::deque<md_result> done;
+    int64_t next_id = 0, submitted = 0, finished = 0;
+    size_t used = 0;
+    bool stop = false;
+    std::thread worker;
+    int64_t slice_steps = 20;
+
+    void run();
+    void admit();
+    void retire(Job* j, int status);
+};
+
+void md_server::retire(Job* j, int status) {
+    md_result r{};
+    r.id = j->id;
+    r.status = status;
+    r.N = j->job.N;
+    r.steps = j->done_steps;
+    if (j->eng && status == MD_OK) {
+        md_energy_t e{};
+        int rc = j->eng->energy(0, &e);
+        if (rc) r.status = rc;
+        r.energy = e;
+    }
+    const auto now = Clock::now();
+    r.wait_ms = ms_between(j->t_submit, j->t_admit);
+    r.run_ms = ms_between(j->t_admit, now);
+    r.step_p50_ms = pct(j->lat_ms, 0.50);
+    r.step_p99_ms = pct(j->lat_ms, 0.99);
+    for (cudaEvent_t e : j->ev) cudaEventDestroy(e);
+    delete j->eng;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        used -= j->bytes;
+        done.push_back(r);
+        finished += 1;
+    }
+    cv.notify_all();
+    delete j;
+}
+
+void md_server::admit() {
+    for (;;) {
+        Job* j = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (pending.empty()) return;
+            Job* f = pending.front();
+            if (f->bytes > budget) {
+                pending.pop_front();
+                j = f;
+                j->t_admit = Clock::now();
+            } else if (used + f->bytes <= budget) {
+                pending.pop_front();
+                used += f->bytes;
+                j = f;
+            } else {
+                return;   // FIFO: wait for memory to free up
+            }
+        }
+        if (j->bytes > budget) {
+            retire(j, MD_ENOMEM);
+            continue;
+        }
+        j->t_admit = Clock::now();
+        Engine* e = new Engine();
+        int rc = e->add_system(j->job.N, j->job.Yp, j->job.rho, j->job.T, j->job.seed, prm);
+        if (!rc) rc = e->build_tables();
+        if (!rc) rc = e->initialise();
+        j->eng = e;
+        if (rc) {
+            retire(j, rc);
+            continue;
+        }
+        j->ev.resize(slice_steps + 1);
+        for (auto& ev : j->ev) cudaEventCreate(&ev);
+        active.push_back(j);
+    }
+}
+
+void md_server::run() {
+    cudaSetDevice(device);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [&] { return stop || !pending.empty() || !active.empty(); });
+            if (stop && active.empty()) break;
+        }
+        admit();
+        if (active.empty()) continue;
+        // enqueue one slice per job; the jobs' streams run concurrently
+        for (Job* j : active) {
+            const int64_t left = j->job.steps - j->done_steps;
+            j->slice = std::min(slice_steps, left);
+            std::vector<double> xi(1, j->job.xi_dot);
+            int rc = j->slice > 0 ? j->eng->step_async(j->slice, &xi, j->ev.data()) : MD_OK;
+            if (rc) j->slice = -rc;   // error marker
+        }
+        std::vector<Job*> keep;
+        for (Job* j : active) {
+            int rc = j->slice < 0 ? (int)-j->slice : j->eng->check_errors();
+            if (rc == MD_OK) {
+                for (int64_t k = 0; k < j->slice; ++k) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, j->ev[k], j->ev[k + 1]);
+                    j->lat_ms.push_back(ms);
+                }
+                j->done_steps += j->slice;
+            }
+            if (rc != MD_OK) retire(j, rc);
+            else if (j->done_steps >= j->job.steps) retire(j, MD_OK);
+            else keep.push_back(j);
+        }
+        active.swap(keep);
+        if (stop) {
+            for (Job* j : active) retire(j, MD_ETIMEOUT);
+            active.clear();
+        }
+    }
+}
+
+extern "C" {
+
+int md_server_create(size_t hbm_budget_bytes, const md_params* p, md_server** out) {
+    if (!out) return fail(MD_EINVAL, "out is null");
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(MD_ENODEV, "no CUDA device available");
+    }
+    if (hbm_budget_bytes == 0) return fail(MD_EINVAL, "budget must be > 0");
+    md_server* sv = new md_server();
+    sv->budget = hbm_budget_bytes;
+    if (p) sv->prm = *p;
+    else md_params_default(&sv->prm);
+    cudaGetDevice(&sv->device);
+    sv->worker = std::thread([sv] { sv->run(); });
+    *out = sv;
+    return MD_OK;
+}
+
+int md_server_submit(md_server* sv, const md_job* job, int64_t* id) {
+    if (!sv || !job) return fail(MD_EINVAL, "null argument");
+    if (job->N < 2 || job->steps < 0 || !(job->rho > 0) || !(job->Yp >= 0 && job->Yp <= 1) || !(job->T >= 0))
+        return fail(MD_EINVAL, "invalid job");
+    Job* j = new Job();
+    j->job = *job;
+    j->bytes = Engine::estimate_bytes(job->N, job->Yp, sv->prm);
+    j->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        j->id = sv->next_id++;
+        sv->pending.push_back(j);
+        sv->submitted += 1;
+    }
+    sv->cv.notify_all();
+    if (id) *id = j->id;
+    return MD_OK;
+}
+
+int md_server_poll(md_server* sv, md_result* out) {
+    if (!sv || !out) return fail(MD_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->done.empty()) return MD_EAGAIN;
+    *out = sv->done.front();
+    sv->done.pop_front();
+    return MD_OK;
+}
+
+int md_server_drain(md_server* sv, double timeout_s) {
+    if (!sv) return fail(MD_EINVAL, "null server");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    const bool ok = sv->cv.wait_for(lk, std::chrono::duration<double>(timeout_s),
+                                    [&] { return sv->finished == sv->submitted; });
+    return ok ? MD_OK : fail(MD_ETIMEOUT, "jobs still running after the timeout");
+}
+
+int md_server_destroy(md_server* sv) {
+    if (!sv) return MD_OK;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        for (Job* j : sv->pending) delete j;
+        sv->pending.clear();
+    }
+    sv->cv.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    delete sv;
+    return MD_OK;
+}
+
+}  // extern "C"
