@@ -152,7 +152,7 @@ def run_gpu(args):
     launches0 = sys_.info()["launches"]
     K = args.steps
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K + 1)]
-    pairs_nuc = pairs_coul = 0
+    pairs_nuc = pairs_coul = cand = 0
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -166,6 +166,7 @@ def run_gpu(args):
             e = sys_.step_energy()
             pairs_nuc += e["pairs_nuc"]
             pairs_coul += e["pairs_coul"]
+            cand += e["candidates"]
         with torch.cuda.stream(stream):
             flush.zero_()
             evs[K][0].record(stream)
@@ -179,7 +180,8 @@ def run_gpu(args):
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    launches = sys_.info()["launches"] - launches0 + 6   # + the cluster kernels
+    info = sys_.info()
+    launches = info["launches"] - launches0 + 6   # + the cluster kernels
     kt = sys_.kernel_times()
     sys_.set_timing(False)
 
@@ -239,7 +241,12 @@ def run_gpu(args):
                                   "MEASURED_PEAKS has no FP32 figure)",
                      "algorithmic": {"pairs_nuc_per_step": pairs_nuc / K, "pairs_coul_per_step": pairs_coul / K,
                                      "flop_per_pair": {"nuclear": FLOP_NUC, "coulomb": FLOP_COUL},
-                                     "force_ms_per_launch": force_ms / max(force_n, 1)}},
+                                     "force_ms_per_launch": force_ms / max(force_n, 1),
+                                     "candidate_pairs_per_step": cand / K,
+                                     "candidate_efficiency": (pairs_nuc + pairs_coul) / max(cand, 1)}},
+        "tiles": {"count": info["tiles"], "list_entries": info["list_entries"], "rebuilds": info["rebuilds"],
+                  "halfext_mean_fm": info["tile_halfext_mean"], "halfext_max_fm": info["tile_halfext_max"],
+                  "need_wrap": info["need_wrap"]},
         "kernel_ms_per_step": {k: v[1] / max(K, 1) for k, v in kt.items()},
         "step_ms_p50": sorted(step_ms)[len(step_ms) // 2],
         "step_ms_p99": sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)],

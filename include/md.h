@@ -88,6 +88,7 @@ typedef struct {
     int64_t step;    /* steps taken since md_create */
     int64_t pairs_nuc;   /* ordered pairs inside r_nuc in that force pass */
     int64_t pairs_coul;  /* ordered proton pairs inside r_C in that pass */
+    int64_t candidates;  /* pairs evaluated in that pass (md_step_energy only) */
 } md_energy_t;
 
 /* State exchange (md_get_state / md_set_state).  The caller owns x, v
@@ -122,6 +123,8 @@ typedef struct {
     int64_t device_bytes;    /* device memory owned by this handle */
     int32_t need_wrap;       /* 1 if the box is too small for tile images */
     int32_t sort_bits;
+    double tile_halfext_mean;  /* mean / max tile half-extent at the last rebuild, fm */
+    double tile_halfext_max;
 } md_info_t;
 
 /* Fill the defaults listed above. */

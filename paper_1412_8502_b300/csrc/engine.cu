@@ -35,6 +35,12 @@ int dalloc(SysHost& h, T** p, size_t count) {
     return MD_OK;
 }
 
+float __uint_as_float_host(unsigned u) {
+    float f;
+    std::memcpy(&f, &u, sizeof(f));
+    return f;
+}
+
 int auto_bits(int64_t N) {
     int b = (int)std::ceil(std::log2(std::cbrt(2.0 * (double)N)));
     return std::min(7, std::max(2, b));
@@ -151,7 +157,6 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     double rC = p.r_C > 0.0 ? p.r_C : std::min(40.0, 0.5 * L0);
     // (relative slack of 1e-12 absorbs the rounding of cbrt)
     if (rC > 0.5 * L0 * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_C exceeds L0/2");
-    if (p.r_nuc > 0.5 * L0 * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_nuc exceeds L0/2");
     if (!sys.empty() && p.precision != precision) return fail(MD_EINVAL, "mixed precision in one engine");
     precision = p.precision;
 
@@ -196,7 +201,8 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     A(&c.disp, 3 * (size_t)N);
     A(&c.key, (size_t)N);
     A(&c.slot, (size_t)N);
-    A(&c.tpos, (size_t)s.T * kTile);
+    A(&c.xhi, (size_t)s.T * kTile);
+    A(&c.xlo, (size_t)s.T * kTile);
     A(&c.torg, 3 * (size_t)s.T);
     A(&c.torgf, 4 * (size_t)s.T);
     A(&c.thalf, 3 * (size_t)s.T);
@@ -432,7 +438,7 @@ size_t Engine::estimate_bytes(int64_t N, double Yp, const md_params& p) {
     size_t b = 0;
     b += 2 * (size_t)N * (8 * 3 + 8 * 3 + 4 + 4 * 3 + 8 * 3);   // x, v, id, f32, f64
     b += (size_t)N * (4 * 3 + 4 + 4 + 9 * 8 + 1 + 4);           // disp, key, slot, staging
-    b += (size_t)T * (16 * 32 + 8 * 3 + 16 + 12 + 4 + 4 + 32) + 4 * 8 * Tpad;
+    b += (size_t)T * (32 * 32 + 8 * 3 + 16 + 12 + 4 + 4 + 64) + 4 * 8 * Tpad;
     b += (size_t)T * T * 4;                                      // pair list
     b += (size_t)nb * 12 + 4096;                                 // engine bins
     return b;
@@ -521,6 +527,7 @@ int Engine::step_energy(int idx, md_energy_t* e) {
     e->step = st.e_step;
     e->pairs_nuc = st.e_pairs_nuc;
     e->pairs_coul = st.e_pairs_coul;
+    e->candidates = st.e_cand;
     return MD_OK;
 }
 
@@ -618,8 +625,7 @@ int Engine::set_state(int idx, const md_state_view* v) {
     if (v->N != h.N || v->Np != h.Np) return fail(MD_EINVAL, "N / Np do not match the system");
     if (!v->x || !v->v) return fail(MD_EINVAL, "x and v are required");
     if (!(v->L > 0.0)) return fail(MD_EINVAL, "L must be > 0");
-    if (h.prm.r_C > 0.5 * v->L * (1.0 + 1e-12) || h.prm.r_nuc > 0.5 * v->L * (1.0 + 1e-12))
-        return fail(MD_EINVAL, "cutoff exceeds L/2");
+    if (h.prm.r_C > 0.5 * v->L * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_C exceeds L/2");
     if (v->type) {
         for (int64_t i = 0; i < h.N; ++i)
             if (v->type[i] != (i < h.Np ? 1 : 0)) return fail(MD_EINVAL, "type must list protons first");
@@ -641,8 +647,7 @@ int Engine::set_state(int idx, const md_state_view* v) {
 int Engine::set_params(int idx, const md_params& p) {
     SysHost& h = *sys[idx];
     const double rC = p.r_C > 0.0 ? p.r_C : std::min(40.0, 0.5 * h.L0);
-    if (rC > 0.5 * h.L0 * (1.0 + 1e-12) || p.r_nuc > 0.5 * h.L0 * (1.0 + 1e-12))
-        return fail(MD_EINVAL, "cutoff exceeds L0/2");
+    if (rC > 0.5 * h.L0 * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_C exceeds L0/2");
     if (!(p.dt > 0.0) || !(p.r_nuc > 0.0) || !(p.skin > 0.0) || !(p.lambda_s > 0.0))
         return fail(MD_EINVAL, "dt, r_nuc, skin and lambda_s must be > 0");
     if (p.precision != MD_PREC_SPLIT && p.precision != MD_PREC_FP64) return fail(MD_EINVAL, "bad precision");
@@ -692,6 +697,8 @@ int Engine::info(int idx, md_info_t* out) {
     out->device_bytes = (int64_t)(h.bytes + (sys.size() == 1 ? table_bytes_ : 0));
     out->need_wrap = st.need_wrap;
     out->sort_bits = h.nbits;
+    out->tile_halfext_mean = h.T ? (double)st.hsum / h.T : 0.0;
+    out->tile_halfext_max = (double)__uint_as_float_host(st.hmax);
     return MD_OK;
 }
 

@@ -1,35 +1,66 @@
 // Pair-list rebuild (the cell-list build of Sec. II.B.2, re-designed for the
-// GPU): a counting sort of the particles over a Morton-ordered grid of
+// GPU): a counting sort of the particles over a Hilbert-ordered grid of
 // 2^(3 nbits) bins per species, a deterministic in-bin order, 32-particle
 // tiles with FP64 origins and bounding boxes, and per-tile lists of the
 // tiles whose bounding boxes come within the interaction range plus skin.
 //
 // Rebuild rule (the neighbour-list rule of Sec. II.B.1 applied to tiles):
-// rebuild when any particle has moved more than skin/2 since the last
-// rebuild, or every `rebuild_every` steps.  Then every pair closer than the
-// cutoff now was closer than cutoff + skin at the rebuild, so its tiles'
-// boxes were within cutoff + skin.  Growth of the box (Eq. 3) only moves
-// periodic images apart, so it never brings a new pair into range.
+// rebuild when any particle has moved more than skin/2 - (L - L_build)
+// since the last rebuild, or every `rebuild_every` steps.  A particle that
+// crossed a face after the rebuild re-enters shifted by the box growth
+// since its crossing (Eq. 3 grows L, positions are not rescaled), so in its
+// tile's frame it has moved by at most its displacement plus L - L_build.
+// Every pair closer than the cutoff now was then closer than cutoff + skin
+// at the rebuild, so its tiles' boxes were within cutoff + skin.
 #include "kernels.h"
 
 namespace pasta {
 
 namespace {
 
-__device__ inline unsigned spread3(unsigned v, int nbits) {
-    unsigned r = 0;
-    for (int b = 0; b < nbits; ++b) r |= ((v >> b) & 1u) << (3 * b);
-    return r;
+// Hilbert index of the bin (qx, qy, qz) of a 2^nbits grid: Skilling's
+// transpose method ("Programming the Hilbert curve", AIP Conf. Proc. 707,
+// 2004) -- undo the excess work of the Gray-code inverse level by level,
+// Gray-encode, then interleave the bits with axis x most significant.
+// Consecutive indices are face-adjacent bins, so a run of 32 particles in
+// this order occupies a compact region.
+__device__ inline unsigned hilbert_key(unsigned qx, unsigned qy, unsigned qz, int nbits) {
+    unsigned X[3] = {qx, qy, qz};
+    const unsigned M = 1u << (nbits - 1);
+    for (unsigned Q = M; Q > 1; Q >>= 1) {
+        const unsigned P = Q - 1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                const unsigned t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    unsigned t = 0;
+    for (unsigned Q = M; Q > 1; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1;
+    X[0] ^= t;
+    X[1] ^= t;
+    X[2] ^= t;
+    unsigned h = 0;
+    for (int k = nbits - 1; k >= 0; --k)
+        h = (h << 3) | (((X[0] >> k) & 1u) << 2) | (((X[1] >> k) & 1u) << 1) | ((X[2] >> k) & 1u);
+    return h;
 }
 
-__device__ inline unsigned morton_key(const SysConst& S, double x, double y, double z, double L) {
+__device__ inline unsigned sort_key(const SysConst& S, double x, double y, double z, double L) {
     const int n = 1 << S.nbits;
     const double sc = (double)n / L;
-    int qx = min(max((int)(x * sc), 0), n - 1);
-    int qy = min(max((int)(y * sc), 0), n - 1);
-    int qz = min(max((int)(z * sc), 0), n - 1);
-    return spread3((unsigned)qx, S.nbits) | (spread3((unsigned)qy, S.nbits) << 1) |
-           (spread3((unsigned)qz, S.nbits) << 2);
+    const int qx = min(max((int)(x * sc), 0), n - 1);
+    const int qy = min(max((int)(y * sc), 0), n - 1);
+    const int qz = min(max((int)(z * sc), 0), n - 1);
+    return hilbert_key((unsigned)qx, (unsigned)qy, (unsigned)qz, S.nbits);
 }
 
 // Inclusive scan over a block of 1024 threads; returns the exclusive prefix
@@ -77,8 +108,8 @@ __global__ void k_decide(EngineDev E, int forced_only, int only) {
         int need = st->force_rebuild;
         if (!forced_only) {
             const float md2 = __uint_as_float(st->maxdisp2);
-            const float h = 0.5f * (float)S.skin;
-            need |= (st->step - st->last_build >= S.rebuild_every) || (md2 > h * h);
+            const float h = (float)(0.5 * S.skin - (st->L - st->L_build));
+            need |= (st->step - st->last_build >= S.rebuild_every) || (h <= 0.0f) || (md2 > h * h);
         }
         if (only >= 0 && s != only) need = 0;
         st->maxdisp2 = 0u;
@@ -87,6 +118,7 @@ __global__ void k_decide(EngineDev E, int forced_only, int only) {
         if (need) {
             st->force_rebuild = 0;
             st->hmax = 0u;
+            st->hsum = 0.0f;
             atomicOr(&any, 1);
         }
     }
@@ -109,7 +141,7 @@ __global__ void k_hist(EngineDev E) {
     if (p >= tile_end(S, t)) return;
     const SysState* st = S.st;
     const double* x = S.x[st->cur];
-    const unsigned k = morton_key(S, x[p], x[S.N + p], x[2 * S.N + p], st->L) +
+    const unsigned k = sort_key(S, x[p], x[S.N + p], x[2 * S.N + p], st->L) +
                        (p < S.Np ? 0u : (unsigned)S.nbins);
     S.key[p] = k;
     atomicAdd(&E.hist[S.bin_base + k], 1u);
@@ -269,12 +301,10 @@ __global__ void k_tiles(EngineDev E) {
         h[a] = 0.5 * (hi - lo);
     }
     const double L = st->L;
-    float4 l;
-    l.x = valid ? (float)(xv[0] - c[0]) : kPad;
-    l.y = valid ? (float)(xv[1] - c[1]) : kPad;
-    l.z = valid ? (float)(xv[2] - c[2]) : kPad;
-    l.w = 0.0f;
-    S.tpos[t * kTile + lane] = l;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) S.torg[3 * t + a] = c[a];
+    __syncwarp();
+    write_xt(S, t, lane, xv, L, valid);
     if (valid) {
         S.disp[p] = 0.0f;
         S.disp[N + p] = 0.0f;
@@ -283,13 +313,13 @@ __global__ void k_tiles(EngineDev E) {
     if (lane == 0) {
         const float hm = (float)fmax(h[0], fmax(h[1], h[2]));
         for (int a = 0; a < 3; ++a) {
-            S.torg[3 * t + a] = c[a];
             // round the FP32 box up so the FP32 range test stays conservative
             S.thalf[3 * t + a] = (float)h[a] * (1.0f + 1e-6f) + 1e-6f;
             S.torgf[4 * t + a] = (float)c[a];
         }
         S.torgf[4 * t + 3] = hm;
         atomic_max_pos(&st->hmax, hm);
+        atomicAdd(&st->hsum, (float)((h[0] + h[1] + h[2]) / 3.0));
         if (t == 0) {
             st->last_build = st->step;
             st->n_rebuilds += 1;

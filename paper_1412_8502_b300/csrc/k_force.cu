@@ -3,19 +3,24 @@
 // image, no Newton's-third-law sharing (each target sums over all its
 // sources, as the paper's GPU kernel also does, Sec. II.B.1).
 //
-// Work unit: one warp per 32-particle target tile; the warp walks the tile's
-// pair list (tiles whose boxes come within range + skin).  For each source
-// tile the 32 source coordinates are staged in shared memory and broadcast
-// to all lanes (one LDS.128 per pair step); each lane accumulates the force
-// on its own target in registers.  The list is species-sorted by tile, so
-// the pair class (pp with/without the nuclear term, like-species nuclear,
-// unlike-species nuclear) is warp-uniform per source tile.
+// Work unit: one warp per 32-particle target tile I.  The warp walks I's
+// tile-pair list; for each source tile J every lane loads one source,
+// moves it to the periodic image next to I, and tests it against I's box
+// (cutoff + skin/2 covers the drift since the rebuild).  Sources that pass
+// are compacted (ballot + popc) into shared-memory queues, one per pair
+// class: proton-proton with the nuclear term (PPN), proton-proton Coulomb
+// only (PPC), unlike species (nuclear, b - c) and like species (nuclear,
+// b + c).  Whenever a queue holds 32 sources they are broadcast to all
+// lanes (LDS.128) and each lane adds the 32 pair forces on its own target
+// in registers; block partials are summed with Kahan compensation.
 //
-// Split precision: the FP64 difference of tile origins (computed per list
-// entry, one entry per lane) plus FP32 tile-local coordinates give each
-// pair separation with an absolute error of a few 1e-7 fm independent of
-// the box size; pair arithmetic and per-target accumulation are FP32;
-// per-tile energy partials are combined in FP64.
+// Precision (split mode): positions are exact FP32 pairs hi + lo of the
+// image nearest the tile origin; periodic shifts of sources use an
+// error-free two-sum, so every separation dx = (hi_i - hi_j) + (lo_i - lo_j)
+// carries only the rounding of its final sum, whatever the box size.  Pair
+// arithmetic is FP32; far Coulomb-only pairs (beyond r_nuc + skin/2 of the
+// target box) use the hi part only, an error below 1e-4 fm at r > 12 fm.
+// Energies are combined in FP64.
 //
 // Single-exponential nuclear term: with g = exp(-r^2/(2 Lambda)),
 // exp(-r^2/Lambda) = g^2, so one ex2 serves both Gaussians of Eq. (1).
@@ -36,7 +41,7 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return y;
 }
 
-enum PairClass { kPPNuc = 0, kPPCoul = 1, kNucSame = 2, kNucCross = 3 };
+enum PairClass { kPPNuc = 0, kPPCoul = 1, kNucCross = 2, kNucSame = 3 };
 
 struct PairConsts {
     float rn2, rc2;          // squared cutoffs
@@ -48,7 +53,7 @@ struct PairConsts {
     float kc;                // -1/(lambda ln 2)
     float l2a;               // log2(alpha)
     float il;                // 1/lambda
-    float Lf, iLf;           // box side for the per-pair image (small boxes)
+    float Lhi, Llo, iLf;     // box side as an exact FP32 pair, 1/L
 };
 
 struct Acc {
@@ -57,19 +62,40 @@ struct Acc {
     int nn, nc;              // in-range pairs (energy pass only)
 };
 
-template <int kClass, bool kSelf, bool kWrap, bool kEnergy>
-__device__ __forceinline__ void pair_block(const float4* __restrict__ sj, float tx, float ty, float tz,
-                                           const PairConsts& C, Acc& acc) {
+struct Kahan {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+// n <= 32 queued sources against this lane's target.  kLo: use the low
+// parts.  (No padding entries: in small boxes the per-pair image would fold
+// a far-away pad back into the box.)
+template <int kClass, bool kLo, bool kWrap, bool kEnergy>
+__device__ __forceinline__ void pair_block(const float4* __restrict__ qh, const float4* __restrict__ ql, int n,
+                                           const float4& hi, const float4& lo, const PairConsts& C, Acc& acc) {
     const float S = (kClass == kNucCross) ? C.Scross : C.Ssame;
     const float bS = (kClass == kNucCross) ? C.bcross : C.bsame;
+    const bool self_possible = (kClass == kPPNuc) || (kClass == kNucSame);
 #pragma unroll 8
-    for (int k = 0; k < kTile; ++k) {
-        const float4 q = sj[k];
-        float dx = tx - q.x, dy = ty - q.y, dz = tz - q.z;
+    for (int k = 0; k < n; ++k) {
+        const float4 q = qh[k];
+        float dx = hi.x - q.x, dy = hi.y - q.y, dz = hi.z - q.z;
+        if (kLo) {
+            const float4 u = ql[k];
+            dx += lo.x - u.x;
+            dy += lo.y - u.y;
+            dz += lo.z - u.z;
+        }
         if (kWrap) {
-            dx = fmaf(-C.Lf, rintf(dx * C.iLf), dx);
-            dy = fmaf(-C.Lf, rintf(dy * C.iLf), dy);
-            dz = fmaf(-C.Lf, rintf(dz * C.iLf), dz);
+            const float kx = rintf(dx * C.iLf), ky = rintf(dy * C.iLf), kz = rintf(dz * C.iLf);
+            dx = fmaf(-C.Llo, kx, fmaf(-C.Lhi, kx, dx));
+            dy = fmaf(-C.Llo, ky, fmaf(-C.Lhi, ky, dy));
+            dz = fmaf(-C.Llo, kz, fmaf(-C.Lhi, kz, dz));
         }
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         float fr = 0.0f;
@@ -77,7 +103,7 @@ __device__ __forceinline__ void pair_block(const float4* __restrict__ sj, float 
             const float gq = ex2_approx(r2 * C.kq);
             const float fn = gq * fmaf(C.A2, gq, S);
             bool in = r2 < C.rn2;
-            if (kSelf) in = in && (r2 > 0.0f);
+            if (self_possible) in = in && (r2 > 0.0f);
             fr = in ? fn : 0.0f;
             if (kEnergy) {
                 acc.en += in ? gq * fmaf(C.a, gq, bS) : 0.0f;
@@ -90,7 +116,7 @@ __device__ __forceinline__ void pair_block(const float4* __restrict__ sj, float 
             const float ea = ex2_approx(fmaf(r, C.kc, C.l2a));     // alpha e^{-r/lambda}
             const float fc = ea * (ri * ri) * (ri + C.il);
             bool in = r2 < C.rc2;
-            if (kSelf) in = in && (r2 > 0.0f);
+            if (self_possible) in = in && (r2 > 0.0f);
             fr += in ? fc : 0.0f;
             if (kEnergy) {
                 acc.ec += in ? ea * ri : 0.0f;
@@ -104,45 +130,94 @@ __device__ __forceinline__ void pair_block(const float4* __restrict__ sj, float 
     }
 }
 
-template <bool kWrap, bool kEnergy>
-__device__ __forceinline__ void dispatch(int cls, bool self, const float4* sj, float tx, float ty, float tz,
-                                         const PairConsts& C, Acc& acc) {
-    if (self) {
-        switch (cls) {
-            case kPPNuc: pair_block<kPPNuc, true, kWrap, kEnergy>(sj, tx, ty, tz, C, acc); break;
-            case kPPCoul: pair_block<kPPCoul, true, kWrap, kEnergy>(sj, tx, ty, tz, C, acc); break;
-            case kNucSame: pair_block<kNucSame, true, kWrap, kEnergy>(sj, tx, ty, tz, C, acc); break;
-            default: pair_block<kNucCross, true, kWrap, kEnergy>(sj, tx, ty, tz, C, acc); break;
-        }
-    } else {
-        switch (cls) {
-            case kPPNuc: pair_block<kPPNuc, false, kWrap, kEnergy>(sj, tx, ty, tz, C, acc); break;
-            case kPPCoul: pair_block<kPPCoul, false, kWrap, kEnergy>(sj, tx, ty, tz, C, acc); break;
-            case kNucSame: pair_block<kNucSame, false, kWrap, kEnergy>(sj, tx, ty, tz, C, acc); break;
-            default: pair_block<kNucCross, false, kWrap, kEnergy>(sj, tx, ty, tz, C, acc); break;
-        }
+// error-free a + b = s + e
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+constexpr int kForceWarps = 4;   // warps (target tiles) per block
+constexpr int kQ = 2 * kTile;    // queue capacity
+constexpr int kStages = 4;       // source tiles in flight per warp (cp.async)
+
+struct WarpQueues {
+    float4 h[3][kQ];             // 0: PPN / like species, 1: PPC, 2: unlike species
+    float4 l[3][kQ];             // low parts (queue 1 does not use them)
+    float4 sh[kStages][kTile];   // staged source tiles (high parts)
+    float4 sl[kStages][kTile];   // staged source tiles (low parts)
+    int sJ[kStages];             // staged tile index | shift code << 24 | nuclear flag
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int kN>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(kN) : "memory"); }
+
+struct Totals {
+    Kahan kx, ky, kz, ken, kec, kw;
+    int nn = 0, nc = 0, blocks = 0;
+};
+
+template <int kClass, bool kLo, bool kWrap, bool kEnergy>
+__device__ __forceinline__ void run_block(const float4* qh, const float4* ql, int n, const float4& hi,
+                                          const float4& lo, const PairConsts& C, Totals& T) {
+    Acc a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0};
+    pair_block<kClass, kLo, kWrap, kEnergy>(qh, ql, n, hi, lo, C, a);
+    T.kx.add(a.fx);
+    T.ky.add(a.fy);
+    T.kz.add(a.fz);
+    if (kEnergy) {
+        T.ken.add(a.en);
+        T.kec.add(a.ec);
+        T.kw.add(a.w);
+        T.nn += a.nn;
+        T.nc += a.nc;
+        T.blocks += 1;
     }
 }
 
-struct Kahan {
-    float s = 0.0f, c = 0.0f;
-    __device__ __forceinline__ void add(float v) {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
+// Process the first min(cnt, 32) entries of queue q, shift the rest down.
+template <bool kWrap, bool kEnergy>
+__device__ __forceinline__ void drain(WarpQueues& Q, int q, int cls, int& cnt, int lane, const float4& hi,
+                                      const float4& lo, const PairConsts& C, Totals& T) {
+    __syncwarp();
+    const int n = min(cnt, kTile);
+    switch (cls) {
+        case kPPNuc: run_block<kPPNuc, true, kWrap, kEnergy>(Q.h[q], Q.l[q], n, hi, lo, C, T); break;
+        case kPPCoul: run_block<kPPCoul, false, kWrap, kEnergy>(Q.h[q], Q.l[q], n, hi, lo, C, T); break;
+        case kNucCross: run_block<kNucCross, true, kWrap, kEnergy>(Q.h[q], Q.l[q], n, hi, lo, C, T); break;
+        default: run_block<kNucSame, true, kWrap, kEnergy>(Q.h[q], Q.l[q], n, hi, lo, C, T); break;
     }
-};
+    __syncwarp();
+    const int rest = cnt - n;
+    if (lane < rest) {
+        Q.h[q][lane] = Q.h[q][kTile + lane];
+        Q.l[q][lane] = Q.l[q][kTile + lane];
+    }
+    cnt = rest;
+    __syncwarp();
+}
 
-constexpr int kForceWarps = 4;   // warps (target tiles) per block
+__device__ __forceinline__ void push(WarpQueues& Q, int q, bool pred, int& cnt, int lane, const float4& h,
+                                     const float4& l) {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (pred) {
+        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+        Q.h[q][pos] = h;
+        Q.l[q][pos] = l;
+    }
+    cnt += __popc(m);
+}
 
 template <bool kWrap, bool kEnergy>
-__device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt) {
-    __shared__ float4 sbuf[kForceWarps][kTile];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    float4* sj = sbuf[w];
+__device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt, WarpQueues& Q) {
+    const int lane = threadIdx.x & 31;
     SysState* st = S.st;
-    const double L = st->L, hL = 0.5 * L;
+    const double L = st->L;
 
     PairConsts C;
     C.rn2 = (float)(S.r_nuc * S.r_nuc);
@@ -157,78 +232,122 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
     C.kc = (float)(-1.0 / (S.lambda_s * 0.69314718055994530942));
     C.l2a = (float)log2(S.alpha);
     C.il = (float)(1.0 / S.lambda_s);
-    C.Lf = (float)L;
+    const float Lhi = (float)L, Llo = (float)(L - (double)Lhi);
+    C.Lhi = Lhi;
+    C.Llo = Llo;
     C.iLf = (float)(1.0 / L);
+    // source filter radii around I's box: cutoff + skin/2 (+ FP32 margin)
+    const float half = 0.5f * (float)S.skin + 2e-3f;
+    const float Rn = (float)S.r_nuc + half, Rc = (float)(S.coulomb ? S.r_C : 0.0) + half;
+    const float Rn2 = Rn * Rn, Rc2 = Rc * Rc;
 
-    const float4 me = S.tpos[I * kTile + lane];
-    const double oIx = S.torg[3 * I], oIy = S.torg[3 * I + 1], oIz = S.torg[3 * I + 2];
+    const float4 hi = S.xhi[I * kTile + lane];
+    const float4 lo = S.xlo[I * kTile + lane];
+    const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
+    const float hIx = S.thalf[3 * I], hIy = S.thalf[3 * I + 1], hIz = S.thalf[3 * I + 2];
     const bool Ip = I < S.Tp;
+    const int cls0 = (Ip && S.coulomb) ? kPPNuc : kNucSame;
     const int e0 = S.lstart[I], e1 = S.lstart[I + 1];
 
-    Acc acc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0};
-    Kahan ken, kec, kw;
-    int nn = 0, nc = 0;
+    Totals T;
+    int c0 = 0, c1 = 0, c2 = 0;
 
-    for (int base = e0; base < e1; base += 32) {
-        const int n = min(32, e1 - base);
-        const int ent = lane < n ? S.list[base + lane] : 0;
+    // Stage entry e: tile index, periodic shift toward I and nuclear flag
+    // (lane 0 stores them), then this lane's source coordinates (cp.async;
+    // the low parts only when the nuclear term is reachable).
+    auto stage = [&](int e) {
+        const int slot = (e - e0) % kStages;
+        const int ent = S.list[e];
         const int J = ent & (kNucBit - 1);
-        float ax = 0.f, ay = 0.f, az = 0.f;
-        if (lane < n) {
-            ax = (float)min_image(oIx - S.torg[3 * J], L, hL);
-            ay = (float)min_image(oIy - S.torg[3 * J + 1], L, hL);
-            az = (float)min_image(oIz - S.torg[3 * J + 2], L, hL);
+        if (lane == 0) {
+            const float4 oJ = *reinterpret_cast<const float4*>(&S.torgf[4 * J]);
+            const int sx = (int)rintf((oI.x - oJ.x) * C.iLf);
+            const int sy = (int)rintf((oI.y - oJ.y) * C.iLf);
+            const int sz = (int)rintf((oI.z - oJ.z) * C.iLf);
+            const int code = (sx + 1) | ((sy + 1) << 2) | ((sz + 1) << 4);
+            Q.sJ[slot] = J | (code << 24) | ((ent & kNucBit) ? (1 << 30) : 0);
         }
-        int Jn = __shfl_sync(0xffffffffu, J, 0);
-        float4 qn = S.tpos[Jn * kTile + lane];
-        for (int k = 0; k < n; ++k) {
-            const int Jk = Jn;
-            const int ek = __shfl_sync(0xffffffffu, ent, k);
-            const float dxo = __shfl_sync(0xffffffffu, ax, k);
-            const float dyo = __shfl_sync(0xffffffffu, ay, k);
-            const float dzo = __shfl_sync(0xffffffffu, az, k);
-            __syncwarp();
-            sj[lane] = qn;
-            __syncwarp();
-            if (k + 1 < n) {
-                Jn = __shfl_sync(0xffffffffu, J, k + 1);
-                qn = S.tpos[Jn * kTile + lane];
-            }
-            const float tx = me.x + dxo, ty = me.y + dyo, tz = me.z + dzo;
-            const bool Jp = Jk < S.Tp;
-            int cls;
-            if (Ip && Jp) cls = S.coulomb ? ((ek & kNucBit) ? kPPNuc : kPPCoul) : kNucSame;
-            else cls = (Ip == Jp) ? kNucSame : kNucCross;
-            Acc part{acc.fx, acc.fy, acc.fz, 0.f, 0.f, 0.f, 0, 0};
-            dispatch<kWrap, kEnergy>(cls, Jk == I, sj, tx, ty, tz, C, part);
-            acc.fx = part.fx;
-            acc.fy = part.fy;
-            acc.fz = part.fz;
-            if (kEnergy) {
-                ken.add(part.en);
-                kec.add(part.ec);
-                kw.add(part.w);
-                nn += part.nn;
-                nc += part.nc;
-            }
+        cp_async16(&Q.sh[slot][lane], &S.xhi[J * kTile + lane]);
+        if ((ent & kNucBit) || !(Ip && J < S.Tp && S.coulomb)) cp_async16(&Q.sl[slot][lane], &S.xlo[J * kTile + lane]);
+    };
+    for (int d = 0; d < kStages - 1; ++d) {
+        if (e0 + d < e1) stage(e0 + d);
+        cp_async_commit();
+    }
+    for (int e = e0; e < e1; ++e) {
+        if (e + kStages - 1 < e1) stage(e + kStages - 1);
+        cp_async_commit();
+        cp_async_wait<kStages - 1>();
+        __syncwarp();
+        const int slot = (e - e0) % kStages;
+        const int tag = Q.sJ[slot];
+        const int Jk = tag & 0xFFFFFF;
+        const int shk = (tag >> 24) & 63;
+        const bool nucflag = (tag >> 30) & 1;
+        float4 h = Q.sh[slot][lane];
+        const bool Jp = Jk < S.Tp;
+        const bool farc = Ip && Jp && S.coulomb && !nucflag;      // Coulomb-only entry
+        float4 l = farc ? make_float4(0.f, 0.f, 0.f, 0.f) : Q.sl[slot][lane];
+        __syncwarp();
+        const bool valid = h.x != kPad;
+        if (shk != (1 | (1 << 2) | (1 << 4))) {
+            const float fx = (float)((shk & 3) - 1), fy = (float)(((shk >> 2) & 3) - 1),
+                        fz = (float)(((shk >> 4) & 3) - 1);
+            float er;
+            two_sum(h.x, fx * Lhi, h.x, er);
+            l.x = l.x + fx * Llo + er;
+            two_sum(h.y, fy * Lhi, h.y, er);
+            l.y = l.y + fy * Llo + er;
+            two_sum(h.z, fz * Lhi, h.z, er);
+            l.z = l.z + fz * Llo + er;
+        }
+        // distance of the source to I's box (small boxes: nearest image)
+        float ux = h.x - oI.x, uy = h.y - oI.y, uz = h.z - oI.z;
+        if (kWrap) {
+            ux = fmaf(-Lhi, rintf(ux * C.iLf), ux);
+            uy = fmaf(-Lhi, rintf(uy * C.iLf), uy);
+            uz = fmaf(-Lhi, rintf(uz * C.iLf), uz);
+        }
+        const float gx = fmaxf(fabsf(ux) - hIx, 0.0f);
+        const float gy = fmaxf(fabsf(uy) - hIy, 0.0f);
+        const float gz = fmaxf(fabsf(uz) - hIz, 0.0f);
+        const float d2 = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+        if (Ip && Jp && S.coulomb) {
+            const bool nuc = valid && !farc && d2 < Rn2;
+            push(Q, 0, nuc, c0, lane, h, l);
+            push(Q, 1, valid && !nuc && d2 < Rc2, c1, lane, h, l);
+            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, kPPNuc, c0, lane, hi, lo, C, T);
+            if (c1 >= kTile) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, hi, lo, C, T);
+        } else if (Ip != Jp) {
+            push(Q, 2, valid && d2 < Rn2, c2, lane, h, l);
+            if (c2 >= kTile) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, hi, lo, C, T);
+        } else {
+            push(Q, 0, valid && d2 < Rn2, c0, lane, h, l);
+            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, hi, lo, C, T);
         }
     }
+    cp_async_wait<0>();
+    // flush the partial queues (< 32 entries each)
+    if (c0 > 0) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, hi, lo, C, T);
+    if (c1 > 0) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, hi, lo, C, T);
+    if (c2 > 0) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, hi, lo, C, T);
 
     const int p = tile_slot0(S, I) + lane;
     const bool valid = p < tile_end(S, I);
     const int N = S.N;
     float* F = S.f32[out_alt ? (st->cur ^ 1) : st->cur];
+    const float fx = T.kx.s - T.kx.c, fy = T.ky.s - T.ky.c, fz = T.kz.s - T.kz.c;
     if (valid) {
-        F[p] = acc.fx;
-        F[N + p] = acc.fy;
-        F[2 * N + p] = acc.fz;
-        if (!isfinite(acc.fx) || !isfinite(acc.fy) || !isfinite(acc.fz)) atomicOr(&st->error, 1);
+        F[p] = fx;
+        F[N + p] = fy;
+        F[2 * N + p] = fz;
+        if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&st->error, 1);
     }
     if (kEnergy) {
-        double en = valid ? ((double)ken.s - (double)ken.c) : 0.0;
-        double ec = valid ? ((double)kec.s - (double)kec.c) : 0.0;
-        double wv = valid ? ((double)kw.s - (double)kw.c) : 0.0;
-        double cn = valid ? (double)nn : 0.0, cc = valid ? (double)nc : 0.0;
+        double en = valid ? ((double)T.ken.s - (double)T.ken.c) : 0.0;
+        double ec = valid ? ((double)T.kec.s - (double)T.kec.c) : 0.0;
+        double wv = valid ? ((double)T.kw.s - (double)T.kw.c) : 0.0;
+        double cn = valid ? (double)T.nn : 0.0, cc = valid ? (double)T.nc : 0.0;
         en = warp_sum(en);
         ec = warp_sum(ec);
         wv = warp_sum(wv);
@@ -240,12 +359,14 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
             S.tile_e[8 * I + 2] = 0.5 * wv;
             S.tile_e[8 * I + 3] = cn;
             S.tile_e[8 * I + 4] = cc;
+            S.tile_e[8 * I + 5] = (double)T.blocks * (kTile * kTile);
         }
     }
 }
 
 template <bool kEnergy>
 __global__ void __launch_bounds__(kForceWarps * 32) k_force_split(EngineDev E, int only, int out_alt) {
+    __shared__ WarpQueues qs[kForceWarps];
     const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
     if (g >= E.ntiles) return;
     const int s = E.tile_sys[g];
@@ -253,8 +374,9 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_split(EngineDev E, i
     const SysConst& S = E.sys[s];
     const int I = g - S.tile_base;
     if (I >= S.T) return;
-    if (S.st->need_wrap) force_tile<true, kEnergy>(S, I, out_alt);
-    else force_tile<false, kEnergy>(S, I, out_alt);
+    WarpQueues& Q = qs[threadIdx.x >> 5];
+    if (S.st->need_wrap) force_tile<true, kEnergy>(S, I, out_alt, Q);
+    else force_tile<false, kEnergy>(S, I, out_alt, Q);
 }
 
 // ---------------------------------------------------------------- FP64
@@ -343,6 +465,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fp64(EngineDev E, in
             S.tile_e[8 * I + 2] = 0.5 * wv;
             S.tile_e[8 * I + 3] = cn;
             S.tile_e[8 * I + 4] = cc;
+            S.tile_e[8 * I + 5] = (double)(e1 - e0) * (kTile * kTile);
         }
     }
 }

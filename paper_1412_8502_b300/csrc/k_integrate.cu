@@ -83,17 +83,6 @@ __device__ inline const float* cur_force<float>(const SysConst& S, int cur) { re
 template <>
 __device__ inline const double* cur_force<double>(const SysConst& S, int cur) { return S.f64[cur]; }
 
-// Refresh the FP32 local coordinates of slot p in tile t.
-__device__ inline void write_local(const SysConst& S, int t, int lane, const double* xs, double L) {
-    const double hL = 0.5 * L;
-    float4 l;
-    l.x = (float)min_image(xs[0] - S.torg[3 * t], L, hL);
-    l.y = (float)min_image(xs[1] - S.torg[3 * t + 1], L, hL);
-    l.z = (float)min_image(xs[2] - S.torg[3 * t + 2], L, hL);
-    l.w = 0.0f;
-    S.tpos[t * kTile + lane] = l;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------- init
@@ -226,7 +215,7 @@ __global__ void k_sd_update(EngineDev E) {
             S.disp[a * N + p] = dd;
             d2 = fmaf(dd, dd, d2);
         }
-        write_local(S, o.t, lane, xs, L);
+        write_xt(S, o.t, lane, xs, L, true);
     }
     d2 = warp_max(d2);
     if (lane == 0 && d2 > 0.0f) atomic_max_pos(&st->maxdisp2, d2);
@@ -255,7 +244,7 @@ __global__ void k_kick_drift(EngineDev E) {
             S.disp[a * N + p] = dd;
             d2 = fmaf(dd, dd, d2);
         }
-        write_local(S, o.t, lane, xs, L);
+        write_xt(S, o.t, lane, xs, L, true);
     }
     d2 = warp_max(d2);
     if (lane == 0 && d2 > 0.0f) atomic_max_pos(&st->maxdisp2, d2);
@@ -288,7 +277,7 @@ __global__ void k_finalize(EngineDev E, int energy) {
     SysState* st = S.st;
     const int lane = threadIdx.x;
     const double v2 = sys_sum(S, 0, lane);
-    double pn = 0, pc = 0, w = 0, cn = 0, cc = 0;
+    double pn = 0, pc = 0, w = 0, cn = 0, cc = 0, ca = 0;
     if (energy) {
         for (int t = lane; t < S.T; t += 32) {
             pn += S.tile_e[8 * t];
@@ -296,12 +285,14 @@ __global__ void k_finalize(EngineDev E, int energy) {
             w += S.tile_e[8 * t + 2];
             cn += S.tile_e[8 * t + 3];
             cc += S.tile_e[8 * t + 4];
+            ca += S.tile_e[8 * t + 5];
         }
         pn = warp_sum(pn);
         pc = warp_sum(pc);
         w = warp_sum(w);
         cn = warp_sum(cn);
         cc = warp_sum(cc);
+        ca = warp_sum(ca);
     }
     if (lane != 0) return;
     const double Lf = st->L;
@@ -326,6 +317,7 @@ __global__ void k_finalize(EngineDev E, int energy) {
         st->e_step = st->step;
         st->e_pairs_nuc = (int64_t)cn;
         st->e_pairs_coul = (int64_t)cc;
+        st->e_cand = (int64_t)ca;
         st->have_energy = 1;
     }
 }

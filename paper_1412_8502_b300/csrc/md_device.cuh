@@ -10,9 +10,10 @@
 // order: protons occupy sorted slots [0, Np), neutrons [Np, N).  Proton tile
 // t covers slots [32 t, 32 t + 32) ∩ [0, Np); neutron tile Tp + u covers
 // [Np + 32 u, ...) ∩ [Np, N).  Positions and velocities are FP64 (x[a*N + p]
-// is axis a of sorted slot p).  The force kernel reads FP32 tile-local
-// coordinates tpos[32 t + lane] = x - O_t (O_t: FP64 tile origin fixed at the
-// last pair-list rebuild), refreshed every step.
+// is axis a of sorted slot p).  The force kernel reads each position as an
+// exact pair of FP32 numbers, xhi + xlo, of the periodic image nearest its
+// tile's origin O_t (FP64, fixed at the last pair-list rebuild), refreshed
+// every step: xhi[32 t + lane] = fp32(xt), xlo = fp32(xt - xhi).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -35,6 +36,9 @@ struct SysState {
     double KE, PE_nuc, PE_coul, virial;     // last recorded energies
     double e_L, e_t;         // box side / time of the recorded energies
     int64_t e_pairs_nuc, e_pairs_coul;   // in-range ordered pairs of that pass
+    int64_t e_cand;                      // candidate pairs evaluated in that pass
+    float hsum;              // sum of tile half-extents at the last rebuild
+    int pad1;
     double vscale;           // pending thermostat factor (1 = none)
     int64_t step, last_build, n_rebuilds, e_step;
     int64_t list_total;
@@ -74,7 +78,8 @@ struct SysConst {
     float* disp;             // [3N] displacement since the last rebuild
     unsigned* key;           // [N] bin of each slot (rebuild scratch)
     int* slot;               // [N] scatter scratch
-    float4* tpos;            // [T*32] tile-local FP32 coordinates
+    float4* xhi;             // [T*32] FP32 high part of the tile-frame position
+    float4* xlo;             // [T*32] FP32 low part (xhi + xlo = position)
     double* torg;            // [T*3] FP64 tile origins
     float* torgf;            // [T*4] FP32 origin (x,y,z) and max half-extent
     float* thalf;            // [T*3] tile half-extents at rebuild
@@ -145,6 +150,32 @@ __device__ inline double warp_max(double v) {
 __device__ inline float warp_max(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// Store slot (t, lane)'s position as hi + lo FP32 pair of its image nearest
+// the tile origin (empty slots: far away, zero low part).
+__device__ inline void write_xt(const SysConst& s, int t, int lane, const double* xs, double L, bool valid) {
+    float4 h, l;
+    h.w = l.w = 0.0f;
+    if (valid) {
+        const double hL = 0.5 * L;
+        double xt[3];
+        for (int a = 0; a < 3; ++a) {
+            const double o = s.torg[3 * t + a];
+            xt[a] = o + min_image(xs[a] - o, L, hL);
+        }
+        h.x = (float)xt[0];
+        h.y = (float)xt[1];
+        h.z = (float)xt[2];
+        l.x = (float)(xt[0] - (double)h.x);
+        l.y = (float)(xt[1] - (double)h.y);
+        l.z = (float)(xt[2] - (double)h.z);
+    } else {
+        h.x = h.y = h.z = kPad;
+        l.x = l.y = l.z = 0.0f;
+    }
+    s.xhi[t * kTile + lane] = h;
+    s.xlo[t * kTile + lane] = l;
 }
 
 // atomicMax on the bit pattern of a non-negative float.

@@ -42,7 +42,8 @@ class md_params(ctypes.Structure):
 
 class md_energy_t(ctypes.Structure):
     _fields_ = [("KE", _D), ("PE_nuc", _D), ("PE_coul", _D), ("virial", _D), ("L", _D),
-                ("t", _D), ("step", _I64), ("pairs_nuc", _I64), ("pairs_coul", _I64)]
+                ("t", _D), ("step", _I64), ("pairs_nuc", _I64), ("pairs_coul", _I64),
+                ("candidates", _I64)]
 
 
 class md_state_view(ctypes.Structure):
@@ -59,7 +60,7 @@ class md_cluster_stats(ctypes.Structure):
 class md_info_t(ctypes.Structure):
     _fields_ = [("N", _I64), ("Np", _I64), ("tiles", _I64), ("rebuilds", _I64),
                 ("list_entries", _I64), ("launches", _I64), ("device_bytes", _I64),
-                ("need_wrap", _I32), ("sort_bits", _I32)]
+                ("need_wrap", _I32), ("sort_bits", _I32), ("tile_halfext_mean", _D), ("tile_halfext_max", _D)]
 
 
 class md_job(ctypes.Structure):
