@@ -195,6 +195,31 @@ MD_API int md_kernel_times(md_system* s, int max, const char** names, int64_t* l
 /* Thread-local message describing the last error of this thread. */
 MD_API const char* md_last_error(void);
 
+/* Cluster analysis (same rules and results as md_clusters) on positions the
+ * caller already holds in device memory, for callers that cannot allocate
+ * device memory: code running inside another application's memory pool,
+ * work enqueued while a CUDA graph is being captured, or loops that must not
+ * stall on the allocator.  The paper has no counterpart; this is a service of
+ * the library.  It calls no cudaMalloc, cudaFree or allocating routine: its
+ * working memory is one fixed file-scope device array, held by every GPU that
+ * loads the library until the process exits.
+ *   d_x       [N][3] doubles, device, original order, particles 0..Np-1 are
+ *             protons; positions inside the periodic cube of side L
+ *   d_labels  [N] int32, device (output): smallest proton index of the
+ *             cluster, -1 for a free neutron
+ *   d_hist_A  [N+1] int64, device (output); d_hist_Z [Np+1] int64 (output)
+ *   d_counts  [5] int64, device (output): clusters, free neutrons, clusters
+ *             with A >= 12, sum of their A, sum of their Z
+ *   stream    cudaStream_t (NULL: legacy default stream); the call is
+ *             asynchronous on it.
+ * N above 32768 gives MD_EINVAL (fixed scratch limit).  The first call on
+ * each device looks up the scratch array's device address with that device
+ * current, so make it before any stream capture.  Calls share the scratch
+ * array: two calls whose work overlaps on the GPU race. */
+MD_API int md_clusters_noalloc(const double* d_x, int64_t N, int64_t Np, double L, double r_pp, double r_np,
+                               int32_t* d_labels, int64_t* d_hist_A, int64_t* d_hist_Z, int64_t* d_counts,
+                               void* stream);
+
 /* ---- batched ensemble: many independent systems advanced together ---- */
 
 typedef struct {

@@ -107,6 +107,7 @@ _SIGS = {
     "md_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(md_result)]),
     "md_server_drain": (ctypes.c_int, [_P, _D]),
     "md_server_destroy": (ctypes.c_int, [_P]),
+    "md_clusters_noalloc": (ctypes.c_int, [_P, _I64, _I64, _D, _D, _D, _P, _P, _P, _P, _P]),
 }
 
 
@@ -229,6 +230,14 @@ def md_clusters(h, N: int, Np: int, labels=True):
                         hA.ctypes.data_as(ctypes.POINTER(_I64)), hZ.ctypes.data_as(ctypes.POINTER(_I64)),
                         ctypes.byref(st)), "md_clusters")
     return lab, hA, hZ, {k: getattr(st, k) for k, _ in md_cluster_stats._fields_}
+
+
+def md_clusters_noalloc(d_x, N, Np, L, r_pp, r_np, d_labels, d_hist_A, d_hist_Z, d_counts, stream=None) -> None:
+    """Cluster analysis on caller-owned device buffers (raw device pointers
+    as ints); allocates nothing.  See md_clusters_noalloc in md.h."""
+    ptr = getattr(stream, "cuda_stream", stream)
+    _ck(LIB.md_clusters_noalloc(_P(d_x), int(N), int(Np), float(L), float(r_pp), float(r_np), _P(d_labels),
+                                _P(d_hist_A), _P(d_hist_Z), _P(d_counts), _P(ptr or 0)), "md_clusters_noalloc")
 
 
 def md_get_params(h) -> md_params:
