@@ -156,6 +156,7 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
     with Clocks(local) as clk:
         for k in range(K):
             with torch.cuda.stream(stream):
@@ -173,6 +174,7 @@ def run_gpu(args):
             _, hA, hZ, cst = sys_.clusters(labels=False)
             evs[K][1].record(stream)
         torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     step_ms = [a.elapsed_time(b) for a, b in evs[:K]]
     cl_ms = evs[K][0].elapsed_time(evs[K][1])
     total_ms = sum(step_ms) + cl_ms

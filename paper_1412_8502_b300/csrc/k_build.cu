@@ -119,6 +119,7 @@ __global__ void k_decide(EngineDev E, int forced_only, int only) {
             st->force_rebuild = 0;
             st->hmax = 0u;
             st->hsum = 0.0f;
+            st->list_total = 0;
             atomicOr(&any, 1);
         }
     }
@@ -398,6 +399,46 @@ __device__ inline int list_entry(const SysConst& S, int I, int J, const float4& 
     return d2 < T.R2cross ? (J | kNucBit) : -1;
 }
 
+// Force lists in one pass: tile I's entries go to list[I*T ...], its count
+// to lcount[I] (the list buffer holds T entries per tile, the worst case).
+__global__ void k_lbuild(EngineDev E) {
+    if (!*E.any_rebuild) return;
+    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= E.ntiles) return;
+    const int s = E.tile_sys[g];
+    if (s < 0) return;
+    const SysConst& S = E.sys[s];
+    SysState* st = S.st;
+    if (!sys_rebuilds(S)) return;
+    const int I = g - S.tile_base;
+    if (I == 0 && lane == 0) {
+        st->cur = st->cur_next;
+        // small boxes: tiles are too large for one image per tile pair
+        const float hm = __uint_as_float(st->hmax);
+        const double rmax = (S.coulomb ? fmax(S.r_C, S.r_nuc) : S.r_nuc);
+        st->need_wrap = (rmax + S.skin + 2.0 * (double)hm + 1e-3 >= 0.5 * st->L) ? 1 : 0;
+    }
+    if (I >= S.T) return;
+    const ListTest T = make_test(S, 0, (float)st->L);
+    const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
+    const float hI[3] = {S.thalf[3 * I], S.thalf[3 * I + 1], S.thalf[3 * I + 2]};
+    int* lst = S.list + (long long)I * S.T;
+    int out = 0;
+    for (int J0 = 0; J0 < S.T; J0 += 32) {
+        const int J = J0 + lane;
+        const int e = J < S.T ? list_entry(S, I, J, oI, hI, T) : -1;
+        const unsigned m = __ballot_sync(0xffffffffu, e >= 0);
+        if (e >= 0) lst[out + __popc(m & ((1u << lane) - 1u))] = e;
+        out += __popc(m);
+    }
+    if (lane == 0) {
+        S.lcount[I] = out;
+        atomicAdd((unsigned long long*)&st->list_total, (unsigned long long)out);
+    }
+}
+
+// Cluster lists (mode 1): count, scan, write into a buffer sized by the host.
 __global__ void k_lcount(EngineDev E, int mode, int only) {
     if (mode == 0 && !*E.any_rebuild) return;
     const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
@@ -506,13 +547,9 @@ void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int on
     k_move<<<nb, kBlock, 0, s>>>(E);
     H.rec("tiles", s);
     k_tiles<<<nb, kBlock, 0, s>>>(E);
-    H.rec("lcount", s);
-    k_lcount<<<nb, kBlock, 0, s>>>(E, 0, -1);
-    H.rec("lscan", s);
-    k_lscan<<<E.nsys, 1024, 0, s>>>(E, 0, -1);
-    H.rec("lwrite", s);
-    k_lwrite<<<nb, kBlock, 0, s>>>(E, 0, -1);
-    H.count(11);
+    H.rec("lists", s);
+    k_lbuild<<<nb, kBlock, 0, s>>>(E);
+    H.count(9);
 }
 
 // phase 0: count and scan (host then checks capacity); phase 1: write.

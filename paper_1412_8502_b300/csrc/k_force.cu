@@ -247,7 +247,8 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
     const float hIx = S.thalf[3 * I], hIy = S.thalf[3 * I + 1], hIz = S.thalf[3 * I + 2];
     const bool Ip = I < S.Tp;
     const int cls0 = (Ip && S.coulomb) ? kPPNuc : kNucSame;
-    const int e0 = S.lstart[I], e1 = S.lstart[I + 1];
+    const int* lst = S.list + (long long)I * S.T;
+    const int e0 = 0, e1 = S.lcount[I];
 
     Totals T;
     int c0 = 0, c1 = 0, c2 = 0;
@@ -257,7 +258,7 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
     // the low parts only when the nuclear term is reachable).
     auto stage = [&](int e) {
         const int slot = (e - e0) % kStages;
-        const int ent = S.list[e];
+        const int ent = lst[e];
         const int J = ent & (kNucBit - 1);
         if (lane == 0) {
             const float4 oJ = *reinterpret_cast<const float4*>(&S.torgf[4 * J]);
@@ -404,9 +405,10 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fp64(EngineDev E, in
     const double A2 = 2.0 * S.a / S.Lambda;
     double fx = 0, fy = 0, fz = 0, en = 0, ec = 0, wv = 0;
     int nn = 0, nc = 0;
-    const int e0 = S.lstart[I], e1 = S.lstart[I + 1];
+    const int* lst = S.list + (long long)I * S.T;
+    const int e0 = 0, e1 = S.lcount[I];
     for (int e = e0; e < e1; ++e) {
-        const int J = S.list[e] & (kNucBit - 1);
+        const int J = lst[e] & (kNucBit - 1);
         const int q = tile_slot0(S, J) + lane;
         const bool qv = q < tile_end(S, J);
         __syncwarp();

@@ -129,12 +129,30 @@ __global__ void k_vsum(EngineDev E, int mode, int only) {
     block_sum4(S, a, b, d, 0.0);
 }
 
-// One warp per system: fixed-order sum of the system's block partials.
-__device__ inline double sys_sum(const SysConst& S, int k, int lane) {
+constexpr int kRed = 256;   // threads of the per-system reduction blocks
+
+// Fixed-order block sum (kRed threads): strided partials, then a tree.
+__device__ inline double block_sum(double v) {
+    __shared__ double sm[kRed / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = lane < kRed / 32 ? sm[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;   // valid in thread 0
+}
+
+// One block per system: fixed-order sum of the system's block partials.
+__device__ inline double sys_sum(const SysConst& S, int k) {
     double r = 0.0;
     const int nb = sys_nblocks(S);
-    for (int b = lane; b < nb; b += 32) r += S.blk[4 * b + k];
-    return warp_sum(r);
+    for (int b = threadIdx.x; b < nb; b += kRed) r += S.blk[4 * b + k];
+    return block_sum(r);
 }
 
 // Remove the centre-of-mass velocity (mode 0) or set the rescale factor
@@ -145,14 +163,14 @@ __global__ void k_init_fix(EngineDev E, int mode) {
     SysState* st = S.st;
     const int lane = threadIdx.x;
     if (mode == 0) {
-        const double sx = sys_sum(S, 0, lane), sy = sys_sum(S, 1, lane), sz = sys_sum(S, 2, lane);
+        const double sx = sys_sum(S, 0), sy = sys_sum(S, 1), sz = sys_sum(S, 2);
         if (lane == 0) {
             st->scratch[0] = sx / S.N;
             st->scratch[1] = sy / S.N;
             st->scratch[2] = sz / S.N;
         }
     } else {
-        const double v2 = sys_sum(S, 0, lane);
+        const double v2 = sys_sum(S, 0);
         if (lane == 0) {
             const double ke = 0.5 * S.M * v2;
             st->vscale = ke > 0.0 ? sqrt(1.5 * (double)S.N * S.T_target / ke) : 0.0;
@@ -276,10 +294,10 @@ __global__ void k_finalize(EngineDev E, int energy) {
     const SysConst& S = E.sys[s];
     SysState* st = S.st;
     const int lane = threadIdx.x;
-    const double v2 = sys_sum(S, 0, lane);
+    const double v2 = sys_sum(S, 0);
     double pn = 0, pc = 0, w = 0, cn = 0, cc = 0, ca = 0;
     if (energy) {
-        for (int t = lane; t < S.T; t += 32) {
+        for (int t = lane; t < S.T; t += kRed) {
             pn += S.tile_e[8 * t];
             pc += S.tile_e[8 * t + 1];
             w += S.tile_e[8 * t + 2];
@@ -287,12 +305,12 @@ __global__ void k_finalize(EngineDev E, int energy) {
             cc += S.tile_e[8 * t + 4];
             ca += S.tile_e[8 * t + 5];
         }
-        pn = warp_sum(pn);
-        pc = warp_sum(pc);
-        w = warp_sum(w);
-        cn = warp_sum(cn);
-        cc = warp_sum(cc);
-        ca = warp_sum(ca);
+        pn = block_sum(pn);
+        pc = block_sum(pc);
+        w = block_sum(w);
+        cn = block_sum(cn);
+        cc = block_sum(cc);
+        ca = block_sum(ca);
     }
     if (lane != 0) return;
     const double Lf = st->L;
@@ -330,20 +348,20 @@ __global__ void k_energy_now(EngineDev E, int only, double* out) {
     const SysConst& S = E.sys[s];
     const SysState* st = S.st;
     const int lane = threadIdx.x;
-    const double v2 = sys_sum(S, 0, lane);
+    const double v2 = sys_sum(S, 0);
     double pn = 0, pc = 0, w = 0, cn = 0, cc = 0;
-    for (int t = lane; t < S.T; t += 32) {
+    for (int t = lane; t < S.T; t += kRed) {
         pn += S.tile_e[8 * t];
         pc += S.tile_e[8 * t + 1];
         w += S.tile_e[8 * t + 2];
         cn += S.tile_e[8 * t + 3];
         cc += S.tile_e[8 * t + 4];
     }
-    pn = warp_sum(pn);
-    pc = warp_sum(pc);
-    w = warp_sum(w);
-    cn = warp_sum(cn);
-    cc = warp_sum(cc);
+    pn = block_sum(pn);
+    pc = block_sum(pc);
+    w = block_sum(w);
+    cn = block_sum(cn);
+    cc = block_sum(cc);
     if (lane == 0) {
         out[0] = 0.5 * S.M * v2;
         out[1] = pn;
@@ -433,10 +451,10 @@ void launch_init(const EngineHost& H, cudaStream_t s, const unsigned long long* 
     const EngineDev& E = H.dev;
     k_init_rng<<<nblk(E), kBlock, 0, s>>>(E, d_seeds);
     k_vsum<<<nblk(E), kBlock, 0, s>>>(E, 0, -1);
-    k_init_fix<<<E.nsys, 32, 0, s>>>(E, 0);
+    k_init_fix<<<E.nsys, kRed, 0, s>>>(E, 0);
     k_sub_com<<<nblk(E), kBlock, 0, s>>>(E);
     k_vsum<<<nblk(E), kBlock, 0, s>>>(E, 1, -1);
-    k_init_fix<<<E.nsys, 32, 0, s>>>(E, 1);
+    k_init_fix<<<E.nsys, kRed, 0, s>>>(E, 1);
     k_rescale<<<nblk(E), kBlock, 0, s>>>(E, -1);
     H.count(7);
 }
@@ -463,7 +481,7 @@ void launch_kick_finalize(const EngineHost& H, cudaStream_t s, bool energy) {
     if (H.precision == 1) k_kick<double><<<nblk(E), kBlock, 0, s>>>(E);
     else k_kick<float><<<nblk(E), kBlock, 0, s>>>(E);
     H.rec("finalize", s);
-    k_finalize<<<E.nsys, 32, 0, s>>>(E, energy ? 1 : 0);
+    k_finalize<<<E.nsys, kRed, 0, s>>>(E, energy ? 1 : 0);
     H.rec("rescale", s);
     k_rescale<<<nblk(E), kBlock, 0, s>>>(E, -1);
     H.count(3);
@@ -473,7 +491,7 @@ void launch_energy_now(const EngineHost& H, cudaStream_t s, int only, double* d_
     const EngineDev& E = H.dev;
     k_vsum<<<nblk(E), kBlock, 0, s>>>(E, 1, only);
     launch_force(H, s, true, only, 1);
-    k_energy_now<<<E.nsys, 32, 0, s>>>(E, only, d_out);
+    k_energy_now<<<E.nsys, kRed, 0, s>>>(E, only, d_out);
     H.count(2);
 }
 
