@@ -260,11 +260,123 @@ def run_gpu(args):
     }
     if e2e:
         line["e2e"] = e2e
+    if not args.no_batch and world == 1:
+        line["batch"] = run_batch(args.batch_steps)
+    if not args.no_serve and world == 1:
+        line["serve"] = run_serve(args.serve_jobs, args.serve_steps, args.serve_rate)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(W, args.cpu_seconds)
     if world > 1:
         dist.destroy_process_group()
     return line
+
+
+# ------------------------------------------------------------------ batch / serve
+def batch_jobs(seed=4):
+    """Ensemble of the paper's Yp x T sweep (5 x 3 systems): N drawn from
+    {4,000, 12,800, 25,600, 51,200}, density log-uniform in [0.00125, 0.080]
+    fm^-3, no expansion."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for Yp in (0.05, 0.10, 0.20, 0.30, 0.40):
+        for T in (0.5, 0.75, 1.0):
+            N = int(rng.choice([4000, 12800, 25600, 51200]))
+            rho = float(np.exp(rng.uniform(np.log(0.00125), np.log(0.080))))
+            jobs.append(dict(N=N, Yp=Yp, rho=rho, T=T, seed=int(rng.integers(1 << 30)), xi_dot=0.0))
+    return jobs
+
+
+def run_batch(steps):
+    """One graph launch per step for all 15 systems vs the same systems
+    stepped one after another (each its own graph), device time."""
+    import torch
+    from paper_1412_8502_b300 import md
+    jobs = batch_jobs()
+    p = md.md_params_default()
+    p.energy_every = 1
+    ntot = sum(j["N"] for j in jobs)
+    b = md.Batch(jobs, p)
+    b.step(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    launches = b.systems[0].info()["launches"]
+    b.close()
+    ts = 0.0
+    for j in jobs:
+        s = md.System(j["N"], j["Yp"], j["rho"], j["T"], j["seed"], p)
+        s.step(3, 0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(steps, 0.0)
+        torch.cuda.synchronize()
+        ts += time.perf_counter() - t0
+        s.close()
+    return {"systems": len(jobs), "nucleons": ntot, "steps": steps,
+            "batched": ntot * steps / tb, "serial": ntot * steps / ts, "speedup": ts / tb,
+            "unit": "nucleon-steps/s", "graph_nodes_per_step": 16,
+            "note": "15 systems (Yp x T sweep), N from {4000,12800,25600,51200}, rho log-uniform "
+                    "[0.00125, 0.08]; batched = one graph launch per step for all; serial = one system at a time"}
+
+
+def run_serve(n_jobs, steps, rate, seed=5):
+    """Poisson stream of MD jobs into the server; per-step latency from CUDA
+    events on each job's stream; the same jobs run one at a time after."""
+    import numpy as np
+    import torch
+    from paper_1412_8502_b300 import md
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for _ in range(n_jobs):
+        N = int(round(float(np.exp(rng.uniform(np.log(2000), np.log(args_serve_nmax))))))
+        rho_f = float(rng.uniform(0.005, 0.02))
+        xi = ((0.08 / rho_f) ** (1 / 3) - 1.0) / (2.0 * 2000)
+        jobs.append(dict(N=N, Yp=float(rng.choice([0.05, 0.1, 0.2, 0.3, 0.4])), rho=0.08,
+                         T=float(rng.choice([0.5, 0.75, 1.0])), seed=int(rng.integers(1 << 30)),
+                         xi_dot=xi, steps=steps))
+    gaps = rng.exponential(1.0 / rate, n_jobs)
+    p = md.md_params_default()
+    free, total = torch.cuda.mem_get_info()
+    sv = md.md_server_create(int(0.5 * free), p)
+    t0 = time.perf_counter()
+    for j, g in zip(jobs, gaps):
+        md.md_server_submit(sv, j)
+        time.sleep(float(g))
+    md.md_server_drain(sv, 900.0)
+    wall = time.perf_counter() - t0
+    res = []
+    while True:
+        r = md.md_server_poll(sv)
+        if r is None:
+            break
+        res.append(r)
+    md.md_server_destroy(sv)
+    ok = [r for r in res if r["status"] == 0]
+    work = sum(r["N"] * r["steps"] for r in ok)
+    lat = sorted(x for r in ok for x in (r["step_p50_ms"],))
+    p99 = max(r["step_p99_ms"] for r in ok) if ok else None
+    t1 = time.perf_counter()
+    for j in jobs:
+        s = md.System(j["N"], j["Yp"], j["rho"], j["T"], j["seed"], p)
+        s.step(j["steps"], j["xi_dot"])
+        s.energy()
+        s.close()
+    torch.cuda.synchronize()
+    serial = time.perf_counter() - t1
+    return {"jobs": n_jobs, "completed": len(ok), "steps_per_job": steps, "arrival_rate_per_s": rate,
+            "served": work / wall, "serial": work / serial, "speedup": serial / wall,
+            "unit": "nucleon-steps/s (wall, including job creation and relaxation)",
+            "step_p50_ms": lat[len(lat) // 2] if lat else None, "step_p99_ms": p99,
+            "wait_ms_max": max(r["wait_ms"] for r in ok) if ok else None,
+            "note": "N log-uniform in [2000, %d], Yp/T from the sweep, rho 0.080 -> U[0.005,0.02] over 2000 "
+                    "steps' rate; p50 = median over jobs of each job's median step latency, p99 = max over "
+                    "jobs of each job's 99th percentile" % args_serve_nmax}
+
+
+args_serve_nmax = 409600
 
 
 # ------------------------------------------------------------------ oracle
@@ -325,6 +437,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--serve-jobs", type=int, default=12)
+    ap.add_argument("--serve-steps", type=int, default=400)
+    ap.add_argument("--serve-rate", type=float, default=4.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -1,0 +1,112 @@
+"""Batched ensemble and serving: each system's result is the same alone and
+in the mix (the kernels are deterministic per system, so "the same" is
+bit-identical here, tighter than the stated tolerances), a batch member
+matches the oracle, and the server admits jobs under its HBM budget."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+JOBS = [
+    dict(N=1500, Yp=0.30, rho=0.080, T=1.0, seed=11, xi_dot=0.0),
+    dict(N=4000, Yp=0.05, rho=0.020, T=0.5, seed=12, xi_dot=7.5e-5),
+    dict(N=2700, Yp=0.40, rho=0.005, T=0.75, seed=13, xi_dot=2e-4),
+    dict(N=640, Yp=0.20, rho=0.0125, T=1.0, seed=14, xi_dot=0.0),
+]
+
+
+@pytest.fixture(scope="module")
+def md():
+    from paper_1412_8502_b300 import md as m
+    return m
+
+
+def params(md, relax=40):
+    p = md.md_params_default()
+    p.relax_iters = relax
+    p.thermostat_every = 25
+    return p
+
+
+def alone(md, job, steps, p):
+    s = md.System(job["N"], job["Yp"], job["rho"], job["T"], job["seed"], p)
+    s.step(steps, job["xi_dot"])
+    return s
+
+
+def test_batch_member_equals_alone(md):
+    p = params(md)
+    b = md.Batch(JOBS, p)
+    b.step(60)
+    for j, s in zip(JOBS, b.systems):
+        a = alone(md, j, 60, p)
+        ga, gb = a.state(), s.state()
+        assert np.array_equal(ga["x"], gb["x"]) and np.array_equal(ga["v"], gb["v"]), j
+        assert ga["L"] == gb["L"] and ga["t"] == gb["t"]
+        assert np.array_equal(a.forces(), s.forces())
+        la, _, _, _ = a.clusters()
+        lb, _, _, _ = s.clusters()
+        assert np.array_equal(la, lb)
+        a.close()
+    b.close()
+
+
+def test_batch_member_matches_oracle(md):
+    p = params(md)
+    b = md.Batch(JOBS[:3], p)
+    b.step(10)
+    for s in b.systems:
+        g = s.state()
+        F = s.forces()
+        pr = s.params
+        Fo, _ = oracle.forces(g["x"], g["type"], g["L_F"], oracle.params(pr.r_C))
+        assert np.linalg.norm(F - Fo) / np.linalg.norm(Fo) <= 1e-5
+    b.close()
+
+
+def test_server_results_equal_alone_and_budget(md):
+    p = params(md, relax=30)
+    steps = 40
+    jobs = [dict(j, steps=steps) for j in JOBS]
+    # budget that holds only some of the jobs at once (a few MB each)
+    from paper_1412_8502_b300 import md as m
+    budget = 5 * 1024 * 1024
+    sv = m.md_server_create(budget, p)
+    ids = {}
+    for j in jobs:
+        ids[m.md_server_submit(sv, j)] = j
+        time.sleep(0.01)
+    big = m.md_server_submit(sv, dict(N=400000, Yp=0.4, rho=0.08, T=0.5, seed=1, xi_dot=0.0, steps=1))
+    m.md_server_drain(sv, 600.0)
+    res = {}
+    while True:
+        r = m.md_server_poll(sv)
+        if r is None:
+            break
+        res[r["id"]] = r
+    m.md_server_destroy(sv)
+    assert set(res) == set(ids) | {big}
+    assert res[big]["status"] == m.MD_ENOMEM
+    for jid, j in ids.items():
+        r = res[jid]
+        assert r["status"] == m.MD_OK and r["steps"] == steps
+        a = alone(md, j, steps, p)
+        e = a.energy()
+        for k in ("KE", "PE_nuc", "PE_coul", "virial", "L", "t"):
+            assert r["energy"][k] == e[k], (j, k, r["energy"][k], e[k])
+        assert 0 < r["step_p50_ms"] <= r["step_p99_ms"]
+        a.close()
+
+
+def test_server_poll_empty_and_bad_job(md):
+    from paper_1412_8502_b300 import md as m
+    sv = m.md_server_create(1 << 30)
+    assert m.md_server_poll(sv) is None
+    with pytest.raises(m.MDError):
+        m.md_server_submit(sv, dict(N=1, Yp=0.3, rho=0.08, T=1.0, seed=1, xi_dot=0.0, steps=5))
+    m.md_server_drain(sv, 10.0)
+    m.md_server_destroy(sv)
