@@ -40,6 +40,9 @@ WORKLOADS = {
     "md409600": dict(N=409600, Yp=0.40, T=0.5, rho=0.080, seed=3, xi=7.5e-5,
                      desc="409,600 nucleons, Yp=0.40, T=0.5 MeV, rho 0.080 fm^-3 expanding at 7.5e-5 c/fm "
                           "(to 0.00125 over 20,000 steps), split FP32/FP64, 1 fm skin, rebuild <= 10 steps"),
+    "md204800": dict(N=204800, Yp=0.40, T=0.5, rho=0.080, seed=6, xi=7.5e-5,
+                     desc="204,800 nucleons, Yp=0.40, T=0.5 MeV, rho 0.080 fm^-3 expanding at 7.5e-5 c/fm "
+                          "(profiling size of the 409,600 workload)"),
     "md51200": dict(N=51200, Yp=0.30, T=1.0, rho=0.080, seed=2, xi=7.5e-5,
                     desc="51,200 nucleons, Yp=0.30, T=1.0 MeV, rho 0.080 fm^-3 expanding at 7.5e-5 c/fm"),
     "md2000": dict(N=2000, Yp=0.30, T=1.0, rho=0.080, seed=1, xi=0.0,

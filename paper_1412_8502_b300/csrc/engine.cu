@@ -327,6 +327,12 @@ int Engine::build_tables() {
 }
 
 int Engine::initialise() {
+    int rc = initialise_async();
+    if (rc) return rc;
+    return check_errors();
+}
+
+int Engine::initialise_async() {
     std::vector<unsigned long long> seeds;
     for (SysHost* h : sys) seeds.push_back(h->seed);
     CK(cudaMemcpyAsync(d_seeds_, seeds.data(), sizeof(unsigned long long) * seeds.size(), cudaMemcpyHostToDevice,
@@ -342,7 +348,7 @@ int Engine::initialise() {
         for (int64_t k = 0; k < iters; ++k)
             if ((rc = run_graph(g_relax_))) return rc;
     }
-    return check_errors();
+    return MD_OK;
 }
 
 // ------------------------------------------------------------------ graphs

@@ -54,6 +54,8 @@ public:
     int build_tables();
     // Seed, relax and evaluate forces of all systems (creation path).
     int initialise();
+    // Same, only enqueued on the engine's stream (no synchronisation).
+    int initialise_async();
     // Release a system's device memory and drop it from the engine.
     void remove_system(int idx);
 

@@ -8,10 +8,14 @@
 // otherwise it is free.  Candidate pairs come from the current tiles: their
 // boxes (taken at the last pair-list rebuild) are tested against r + skin,
 // which covers every particle's drift since then.  The link and assignment
-// decisions use FP64 squared distances evaluated as
+// decisions are those of FP64 squared distances evaluated as
 //   dx = x_i - x_j; nearest image by comparison with L/2;
 //   d2 = (dx*dx + dy*dy) + dz*dz        (no fused multiply-add)
-// so they are exact and identical to a serial FP64 evaluation.
+// so they are exact and identical to a serial FP64 evaluation.  A pair is
+// first screened in FP32 from the exact hi + lo tile-frame positions (the
+// separation is exact before rounding, so the FP32 d2 is within a few ulp
+// of the FP64 one); only pairs within kBand of the threshold, and every
+// neutron-proton candidate inside r_np, are evaluated in FP64.
 #include "kernels.h"
 
 namespace pasta {
@@ -58,6 +62,56 @@ __device__ inline void uf_union(int* parent, int a, int b) {
 }
 
 constexpr int kCW = 4;   // warps per block
+constexpr float kBand = 1e-3f;   // fm^2, far above the FP32 screening error
+
+struct Frame {
+    float Lhi, Llo, iL;
+    int wrap;
+};
+
+__device__ inline Frame frame_of(const SysState* st) {
+    Frame f;
+    f.Lhi = (float)st->L;
+    f.Llo = (float)(st->L - (double)f.Lhi);
+    f.iL = (float)(1.0 / st->L);
+    f.wrap = st->need_wrap;
+    return f;
+}
+
+// Stage source tile J (moved to the image next to tile I) for this lane.
+__device__ inline void stage_src(const SysConst& S, int I, int J, int lane, const Frame& F, float4& h, float4& l) {
+    h = S.xhi[J * kTile + lane];
+    l = S.xlo[J * kTile + lane];
+    const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
+    const float4 oJ = *reinterpret_cast<const float4*>(&S.torgf[4 * J]);
+    const float s[3] = {rintf((oI.x - oJ.x) * F.iL), rintf((oI.y - oJ.y) * F.iL), rintf((oI.z - oJ.z) * F.iL)};
+    float* hp = &h.x;
+    float* lp = &l.x;
+    for (int a = 0; a < 3; ++a) {
+        if (s[a] != 0.0f) {
+            const float b = s[a] * F.Lhi;
+            const float t = hp[a] + b;
+            const float bb = t - hp[a];
+            const float e = (hp[a] - (t - bb)) + (b - bb);
+            hp[a] = t;
+            lp[a] = lp[a] + s[a] * F.Llo + e;
+        }
+    }
+}
+
+__device__ inline float d2_screen(const float4& hi, const float4& lo, const float4& q, const float4& u,
+                                  const Frame& F) {
+    float dx = (hi.x - q.x) + (lo.x - u.x);
+    float dy = (hi.y - q.y) + (lo.y - u.y);
+    float dz = (hi.z - q.z) + (lo.z - u.z);
+    if (F.wrap) {
+        const float kx = rintf(dx * F.iL), ky = rintf(dy * F.iL), kz = rintf(dz * F.iL);
+        dx = fmaf(-F.Llo, kx, fmaf(-F.Lhi, kx, dx));
+        dy = fmaf(-F.Llo, ky, fmaf(-F.Lhi, ky, dy));
+        dz = fmaf(-F.Llo, kz, fmaf(-F.Lhi, kz, dz));
+    }
+    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
 
 }  // namespace
 
@@ -79,35 +133,40 @@ __global__ void k_cl_init(EngineDev E, int only) {
 
 // Warp per proton tile: link proton pairs closer than r_pp.
 __global__ void k_cl_link(EngineDev E, int only) {
-    __shared__ double sb[kCW][3][kTile];
+    __shared__ float4 sh[kCW][kTile], sl[kCW][kTile];
     const SysConst& S = E.sys[only];
     const ClusterBufs& B = *S.cl;
     const int I = blockIdx.x * kCW + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (I >= S.Tp) return;
     const SysState* st = S.st;
+    const Frame F = frame_of(st);
     const double L = st->L, hL = 0.5 * L, r2c = S.r_pp * S.r_pp;
+    const float lo2 = (float)r2c - kBand, hi2 = (float)r2c + kBand;
     const int N = S.N;
     const double* x = S.x[st->cur];
     const int p = I * kTile + lane;
     const bool valid = p < S.Np;
-    const double xi = valid ? x[p] : 0, yi = valid ? x[N + p] : 0, zi = valid ? x[2 * N + p] : 0;
+    const float4 hi = S.xhi[I * kTile + lane], lo = S.xlo[I * kTile + lane];
     for (int e = B.start[I]; e < B.start[I + 1]; ++e) {
         const int J = B.list[e];
-        const int q = J * kTile + lane;
-        const bool qv = q < S.Np;
+        float4 h, l;
+        stage_src(S, I, J, lane, F, h, l);
         __syncwarp();
-        sb[w][0][lane] = qv ? x[q] : 0;
-        sb[w][1][lane] = qv ? x[N + q] : 0;
-        sb[w][2][lane] = qv ? x[2 * N + q] : 0;
+        sh[w][lane] = h;
+        sl[w][lane] = l;
         __syncwarp();
         if (!valid) continue;
         const int nq = min(kTile, S.Np - J * kTile);
         for (int k = 0; k < nq; ++k) {
             const int qq = J * kTile + k;
             if (qq <= p) continue;
-            if (d2_exact(xi, yi, zi, sb[w][0][k], sb[w][1][k], sb[w][2][k], L, hL) < r2c)
-                uf_union(B.parent, p, qq);
+            const float d2 = d2_screen(hi, lo, sh[w][k], sl[w][k], F);
+            if (d2 >= hi2) continue;
+            bool link = d2 < lo2;
+            if (!link)
+                link = d2_exact(x[p], x[N + p], x[2 * N + p], x[qq], x[N + qq], x[2 * N + qq], L, hL) < r2c;
+            if (link) uf_union(B.parent, p, qq);
         }
     }
 }
@@ -124,7 +183,7 @@ __global__ void k_cl_minid(EngineDev E, int only) {
 
 // Proton labels; neutron assignment (warp per neutron tile).
 __global__ void k_cl_assign(EngineDev E, int only) {
-    __shared__ double sb[kCW][3][kTile];
+    __shared__ float4 sh[kCW][kTile], sl[kCW][kTile];
     __shared__ int sid[kCW][kTile];
     const SysConst& S = E.sys[only];
     const ClusterBufs& B = *S.cl;
@@ -140,30 +199,35 @@ __global__ void k_cl_assign(EngineDev E, int only) {
         if (valid) B.label[p] = B.minid[uf_find(B.parent, p)];
         return;
     }
+    const Frame F = frame_of(st);
     const double L = st->L, hL = 0.5 * L, r2c = S.r_np * S.r_np;
+    const float hi2 = (float)r2c + kBand;
+    const float4 hi = S.xhi[I * kTile + lane], lo = S.xlo[I * kTile + lane];
     const double xi = valid ? x[p] : 0, yi = valid ? x[N + p] : 0, zi = valid ? x[2 * N + p] : 0;
     double best_d2 = 0.0;
     int best_id = -1, best_slot = -1;
     for (int e = B.start[I]; e < B.start[I + 1]; ++e) {
         const int J = B.list[e];
+        float4 h, l;
+        stage_src(S, I, J, lane, F, h, l);
         const int q = J * kTile + lane;
-        const bool qv = q < S.Np;
         __syncwarp();
-        sb[w][0][lane] = qv ? x[q] : 0;
-        sb[w][1][lane] = qv ? x[N + q] : 0;
-        sb[w][2][lane] = qv ? x[2 * N + q] : 0;
-        sid[w][lane] = qv ? S.id[c][q] : 0;
+        sh[w][lane] = h;
+        sl[w][lane] = l;
+        sid[w][lane] = q < S.Np ? S.id[c][q] : 0;
         __syncwarp();
         if (!valid) continue;
         const int nq = min(kTile, S.Np - J * kTile);
         for (int k = 0; k < nq; ++k) {
-            const double d2 = d2_exact(xi, yi, zi, sb[w][0][k], sb[w][1][k], sb[w][2][k], L, hL);
+            if (d2_screen(hi, lo, sh[w][k], sl[w][k], F) >= hi2) continue;
+            const int qq = J * kTile + k;
+            const double d2 = d2_exact(xi, yi, zi, x[qq], x[N + qq], x[2 * N + qq], L, hL);
             if (d2 < r2c) {
                 const int oid = sid[w][k];
                 if (best_id < 0 || d2 < best_d2 || (d2 == best_d2 && oid < best_id)) {
                     best_d2 = d2;
                     best_id = oid;
-                    best_slot = J * kTile + k;
+                    best_slot = qq;
                 }
             }
         }

@@ -72,61 +72,75 @@ struct Kahan {
     }
 };
 
-// n <= 32 queued sources against this lane's target.  kLo: use the low
-// parts.  (No padding entries: in small boxes the per-pair image would fold
-// a far-away pad back into the box.)
+// One queued source against this lane's target.  kLo: use the low parts.
+// In-range contributions are added under predicates (no selects).
+template <int kClass, bool kLo, bool kWrap, bool kEnergy>
+__device__ __forceinline__ void one_pair(const float4& q, const float4& u, const float4& hi, const float4& lo,
+                                         const PairConsts& C, float S, float bS, Acc& acc) {
+    constexpr bool self_possible = (kClass == kPPNuc) || (kClass == kNucSame);
+    float dx = hi.x - q.x, dy = hi.y - q.y, dz = hi.z - q.z;
+    if (kLo) {
+        dx += lo.x - u.x;
+        dy += lo.y - u.y;
+        dz += lo.z - u.z;
+    }
+    if (kWrap) {
+        const float kx = rintf(dx * C.iLf), ky = rintf(dy * C.iLf), kz = rintf(dz * C.iLf);
+        dx = fmaf(-C.Llo, kx, fmaf(-C.Lhi, kx, dx));
+        dy = fmaf(-C.Llo, ky, fmaf(-C.Lhi, ky, dy));
+        dz = fmaf(-C.Llo, kz, fmaf(-C.Lhi, kz, dz));
+    }
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    float fr = 0.0f;
+    if (kClass == kPPNuc || kClass == kPPCoul) {
+        const float ri = rsqrt_approx(r2);
+        const float r = r2 * ri;
+        const float ea = ex2_approx(fmaf(r, C.kc, C.l2a));     // alpha e^{-r/lambda}
+        const float vc = ea * ri;                             // screened Coulomb V
+        const float fc = vc * ri * (ri + C.il);
+        bool in = r2 < C.rc2;
+        if (self_possible) in = in && (r2 > 0.0f);
+        if (in) {
+            fr = fc;
+            if (kEnergy) {
+                acc.ec += vc;
+                acc.nc += 1;
+            }
+        }
+    }
+    if (kClass != kPPCoul) {
+        const float gq = ex2_approx(r2 * C.kq);
+        bool in = r2 < C.rn2;
+        if (self_possible) in = in && (r2 > 0.0f);
+        if (in) {
+            fr = fmaf(gq, fmaf(C.A2, gq, S), fr);
+            if (kEnergy) {
+                acc.en = fmaf(gq, fmaf(C.a, gq, bS), acc.en);
+                acc.nn += 1;
+            }
+        }
+    }
+    acc.fx = fmaf(fr, dx, acc.fx);
+    acc.fy = fmaf(fr, dy, acc.fy);
+    acc.fz = fmaf(fr, dz, acc.fz);
+    if (kEnergy) acc.w = fmaf(fr, r2, acc.w);
+}
+
+// A full block of 32 queued sources (compile-time trip count) or the final
+// partial block of n < 32 (no padding entries: in small boxes the per-pair
+// image would fold a far-away pad back into the box).
 template <int kClass, bool kLo, bool kWrap, bool kEnergy>
 __device__ __forceinline__ void pair_block(const float4* __restrict__ qh, const float4* __restrict__ ql, int n,
                                            const float4& hi, const float4& lo, const PairConsts& C, Acc& acc) {
     const float S = (kClass == kNucCross) ? C.Scross : C.Ssame;
     const float bS = (kClass == kNucCross) ? C.bcross : C.bsame;
-    const bool self_possible = (kClass == kPPNuc) || (kClass == kNucSame);
+    if (n == kTile) {
 #pragma unroll 8
-    for (int k = 0; k < n; ++k) {
-        const float4 q = qh[k];
-        float dx = hi.x - q.x, dy = hi.y - q.y, dz = hi.z - q.z;
-        if (kLo) {
-            const float4 u = ql[k];
-            dx += lo.x - u.x;
-            dy += lo.y - u.y;
-            dz += lo.z - u.z;
-        }
-        if (kWrap) {
-            const float kx = rintf(dx * C.iLf), ky = rintf(dy * C.iLf), kz = rintf(dz * C.iLf);
-            dx = fmaf(-C.Llo, kx, fmaf(-C.Lhi, kx, dx));
-            dy = fmaf(-C.Llo, ky, fmaf(-C.Lhi, ky, dy));
-            dz = fmaf(-C.Llo, kz, fmaf(-C.Lhi, kz, dz));
-        }
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        float fr = 0.0f;
-        if (kClass != kPPCoul) {
-            const float gq = ex2_approx(r2 * C.kq);
-            const float fn = gq * fmaf(C.A2, gq, S);
-            bool in = r2 < C.rn2;
-            if (self_possible) in = in && (r2 > 0.0f);
-            fr = in ? fn : 0.0f;
-            if (kEnergy) {
-                acc.en += in ? gq * fmaf(C.a, gq, bS) : 0.0f;
-                acc.nn += in ? 1 : 0;
-            }
-        }
-        if (kClass == kPPNuc || kClass == kPPCoul) {
-            const float ri = rsqrt_approx(r2);
-            const float r = r2 * ri;
-            const float ea = ex2_approx(fmaf(r, C.kc, C.l2a));     // alpha e^{-r/lambda}
-            const float fc = ea * (ri * ri) * (ri + C.il);
-            bool in = r2 < C.rc2;
-            if (self_possible) in = in && (r2 > 0.0f);
-            fr += in ? fc : 0.0f;
-            if (kEnergy) {
-                acc.ec += in ? ea * ri : 0.0f;
-                acc.nc += in ? 1 : 0;
-            }
-        }
-        acc.fx = fmaf(fr, dx, acc.fx);
-        acc.fy = fmaf(fr, dy, acc.fy);
-        acc.fz = fmaf(fr, dz, acc.fz);
-        if (kEnergy) acc.w = fmaf(fr, r2, acc.w);
+        for (int k = 0; k < kTile; ++k)
+            one_pair<kClass, kLo, kWrap, kEnergy>(qh[k], kLo ? ql[k] : qh[k], hi, lo, C, S, bS, acc);
+    } else {
+        for (int k = 0; k < n; ++k)
+            one_pair<kClass, kLo, kWrap, kEnergy>(qh[k], kLo ? ql[k] : qh[k], hi, lo, C, S, bS, acc);
     }
 }
 

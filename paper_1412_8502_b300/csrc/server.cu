@@ -3,12 +3,14 @@
 // A worker thread owns all device work.  Submitted jobs wait in a FIFO; a
 // job is admitted as soon as its device footprint fits in the HBM budget
 // next to the jobs already resident.  Each admitted job keeps its state in
-// device memory on its own stream; every tick the worker enqueues a slice of
-// steps for every active job back to back, so the jobs' kernels overlap on
-// the device, then waits for the slices, records per-step latencies from
-// events on each job's stream, retires finished jobs (freeing their memory)
-// and admits waiting ones.  A job's trajectory does not depend on the other
-// jobs: each runs the same deterministic kernels as it would alone.
+// device memory on its own stream.  Its creation (seeding, relaxation) and
+// then slices of steps are enqueued asynchronously; the worker polls each
+// job's completion event and enqueues the job's next slice as soon as the
+// previous one is done, so every job's stream stays busy and the jobs'
+// kernels overlap on the device.  Per-step latencies come from events on the
+// job's stream.  Finished jobs are retired (their memory freed) and waiting
+// ones admitted.  A job's trajectory does not depend on the other jobs: each
+// runs the same deterministic kernels as it would alone.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -26,6 +28,8 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+enum JobState { kInit = 0, kReady = 1, kRunning = 2 };
+
 struct Job {
     int64_t id;
     md_job job;
@@ -35,6 +39,8 @@ struct Job {
     int64_t done_steps = 0;
     std::vector<double> lat_ms;
     std::vector<cudaEvent_t> ev;
+    cudaEvent_t done = nullptr;
+    int state = kInit;
     int64_t slice = 0;
 };
 
@@ -89,6 +95,7 @@ void md_server::retire(Job* j, int status) {
     r.step_p50_ms = pct(j->lat_ms, 0.50);
     r.step_p99_ms = pct(j->lat_ms, 0.99);
     for (cudaEvent_t e : j->ev) cudaEventDestroy(e);
+    if (j->done) cudaEventDestroy(j->done);
     delete j->eng;
     {
         std::lock_guard<std::mutex> lk(mu);
@@ -127,7 +134,7 @@ void md_server::admit() {
         Engine* e = new Engine();
         int rc = e->add_system(j->job.N, j->job.Yp, j->job.rho, j->job.T, j->job.seed, prm);
         if (!rc) rc = e->build_tables();
-        if (!rc) rc = e->initialise();
+        if (!rc) rc = e->initialise_async();
         j->eng = e;
         if (rc) {
             retire(j, rc);
@@ -135,6 +142,9 @@ void md_server::admit() {
         }
         j->ev.resize(slice_steps + 1);
         for (auto& ev : j->ev) cudaEventCreate(&ev);
+        cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming);
+        cudaEventRecord(j->done, e->stream());
+        j->state = kInit;
         active.push_back(j);
     }
 }
@@ -148,35 +158,50 @@ void md_server::run() {
             if (stop && active.empty()) break;
         }
         admit();
-        if (active.empty()) continue;
-        // enqueue one slice per job; the jobs' streams run concurrently
-        for (Job* j : active) {
-            const int64_t left = j->job.steps - j->done_steps;
-            j->slice = std::min(slice_steps, left);
-            std::vector<double> xi(1, j->job.xi_dot);
-            int rc = j->slice > 0 ? j->eng->step_async(j->slice, &xi, j->ev.data()) : MD_OK;
-            if (rc) j->slice = -rc;   // error marker
-        }
+        bool progressed = false;
         std::vector<Job*> keep;
         for (Job* j : active) {
-            int rc = j->slice < 0 ? (int)-j->slice : j->eng->check_errors();
-            if (rc == MD_OK) {
-                for (int64_t k = 0; k < j->slice; ++k) {
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, j->ev[k], j->ev[k + 1]);
-                    j->lat_ms.push_back(ms);
+            if (j->state != kReady) {
+                const cudaError_t q = cudaEventQuery(j->done);
+                if (q == cudaErrorNotReady) {
+                    keep.push_back(j);
+                    continue;
                 }
-                j->done_steps += j->slice;
+                progressed = true;
+                int rc = q == cudaSuccess ? j->eng->check_errors() : MD_ECUDA;
+                if (rc == MD_OK && j->state == kRunning) {
+                    for (int64_t k = 0; k < j->slice; ++k) {
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, j->ev[k], j->ev[k + 1]);
+                        j->lat_ms.push_back(ms);
+                    }
+                    j->done_steps += j->slice;
+                }
+                if (rc != MD_OK) {
+                    retire(j, rc);
+                    continue;
+                }
+                j->state = kReady;
             }
-            if (rc != MD_OK) retire(j, rc);
-            else if (j->done_steps >= j->job.steps) retire(j, MD_OK);
-            else keep.push_back(j);
+            const int64_t left = j->job.steps - j->done_steps;
+            if (left <= 0 || stop) {
+                retire(j, stop && left > 0 ? MD_ETIMEOUT : MD_OK);
+                continue;
+            }
+            j->slice = std::min(slice_steps, left);
+            std::vector<double> xi(1, j->job.xi_dot);
+            int rc = j->eng->step_async(j->slice, &xi, j->ev.data());
+            if (rc == MD_OK && cudaEventRecord(j->done, j->eng->stream()) != cudaSuccess) rc = MD_ECUDA;
+            if (rc != MD_OK) {
+                retire(j, rc);
+                continue;
+            }
+            j->state = kRunning;
+            progressed = true;
+            keep.push_back(j);
         }
         active.swap(keep);
-        if (stop) {
-            for (Job* j : active) retire(j, MD_ETIMEOUT);
-            active.clear();
-        }
+        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
 }
 
