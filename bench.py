@@ -300,6 +300,10 @@ def run_batch(steps):
     p.energy_every = 1
     ntot = sum(j["N"] for j in jobs)
     b = md.Batch(jobs, p)
+    p = b.autotune(10)          # project autotuner: skin x sort resolution, shared by all systems
+    tuned_skin = p.skin
+    p.sort_bits = 0             # serial runs: same skin, sort resolution from each N
+    p.r_C = 0.0                 # and the Coulomb cutoff from each box (min(40, L0/2))
     b.step(3)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -310,7 +314,7 @@ def run_batch(steps):
     b.close()
     ts = 0.0
     for j in jobs:
-        s = md.System(j["N"], j["Yp"], j["rho"], j["T"], j["seed"], p)
+        s = md.System(j["N"], j["Yp"], j["rho"], j["T"], j["seed"], p)   # same tuned settings
         s.step(3, 0.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -318,7 +322,7 @@ def run_batch(steps):
         torch.cuda.synchronize()
         ts += time.perf_counter() - t0
         s.close()
-    return {"systems": len(jobs), "nucleons": ntot, "steps": steps,
+    return {"systems": len(jobs), "nucleons": ntot, "steps": steps, "tuned_skin_fm": tuned_skin,
             "batched": ntot * steps / tb, "serial": ntot * steps / ts, "speedup": ts / tb,
             "unit": "nucleon-steps/s", "graph_nodes_per_step": 16,
             "note": "15 systems (Yp x T sweep), N from {4000,12800,25600,51200}, rho log-uniform "

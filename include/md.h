@@ -192,6 +192,14 @@ MD_API int md_set_timing(md_system* s, int on);
 MD_API int md_kernel_times(md_system* s, int max, const char** names, int64_t* launches,
                     double* ms, int* n);
 
+/* Autotuner: short timed trials (steps each, from the current state, which
+ * is restored afterwards) over pair-list skin {0.5, 1, 1.5, 2} fm x spatial-
+ * sort resolution {auto-1, auto, auto+1} bits; keeps the fastest setting and
+ * returns the resulting parameters in *chosen (may be NULL).  The physics
+ * does not depend on these settings; trajectories differ only by FP32
+ * summation order. */
+MD_API int md_autotune(md_system* s, int64_t steps, md_params* chosen);
+
 /* Thread-local message describing the last error of this thread. */
 MD_API const char* md_last_error(void);
 
@@ -234,6 +242,8 @@ typedef struct {
  * one graph launch per step that covers all of them. */
 MD_API int md_batch_create(int n, const md_job* jobs, const md_params* p, md_batch** out);
 MD_API int md_batch_step(md_batch* b, int64_t n);
+/* md_autotune for all systems of the batch (one setting shared by all). */
+MD_API int md_batch_autotune(md_batch* b, int64_t steps, md_params* chosen);
 /* Borrow system i of the batch (owned by the batch; do not destroy). */
 MD_API int md_batch_system(md_batch* b, int i, md_system** out);
 MD_API int md_batch_destroy(md_batch* b);

@@ -206,6 +206,8 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     A(&c.torg, 3 * (size_t)s.T);
     A(&c.torgf, 4 * (size_t)s.T);
     A(&c.thalf, 3 * (size_t)s.T);
+    A(&c.sorg, (size_t)(s.T + kTile - 1) / kTile);
+    A(&c.shalf, (size_t)(s.T + kTile - 1) / kTile);
     A(&c.lcount, (size_t)s.T);
     A(&c.lstart, (size_t)s.T + 1);
     A(&c.list, (size_t)c.list_cap);
@@ -657,6 +659,8 @@ int Engine::set_params(int idx, const md_params& p) {
     if (!(p.dt > 0.0) || !(p.r_nuc > 0.0) || !(p.skin > 0.0) || !(p.lambda_s > 0.0))
         return fail(MD_EINVAL, "dt, r_nuc, skin and lambda_s must be > 0");
     if (p.precision != MD_PREC_SPLIT && p.precision != MD_PREC_FP64) return fail(MD_EINVAL, "bad precision");
+    if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
+    const int nbits = p.sort_bits ? p.sort_bits : auto_bits(h.N);
     if (p.precision != precision) {
         if (sys.size() > 1) return fail(MD_EINVAL, "precision is shared by all systems of a batch");
         precision = p.precision;
@@ -681,12 +685,86 @@ int Engine::set_params(int idx, const md_params& p) {
     c.rebuild_every = (int)std::max<int64_t>(1, p.rebuild_every);
     c.coulomb = p.coulomb ? 1 : 0;
     c.energy_every = (int)p.energy_every;
-    CK(cudaMemcpyAsync(d_sys_ + idx, &c, sizeof(SysConst), cudaMemcpyHostToDevice, stream_));
+    if (nbits != h.nbits) {
+        // a different sort grid resizes the engine's bin tables
+        h.nbits = nbits;
+        h.nbins = 1ll << (3 * nbits);
+        c.nbits = nbits;
+        c.nbins = h.nbins;
+        int rc = build_tables();
+        if (rc) return rc;
+    } else {
+        CK(cudaMemcpyAsync(d_sys_ + idx, &c, sizeof(SysConst), cudaMemcpyHostToDevice, stream_));
+    }
     int one = 1;
     CK(cudaMemcpyAsync(&h.d_st->force_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, stream_));
     h.dirty = true;
     CK(cudaStreamSynchronize(stream_));
     return MD_OK;
+}
+
+// Short timed trials over pair-list skin x spatial-sort resolution from a
+// saved state; the fastest setting is kept and the state restored.
+int Engine::autotune(int64_t steps, md_params* chosen) {
+    if (steps < 1) return fail(MD_EINVAL, "steps must be >= 1");
+    const int n = (int)sys.size();
+    std::vector<std::vector<double>> xs(n), vs(n);
+    std::vector<md_state_view> saved(n);
+    std::vector<md_params> base(n);
+    int rc;
+    for (int s = 0; s < n; ++s) {
+        xs[s].resize(3 * sys[s]->N);
+        vs[s].resize(3 * sys[s]->N);
+        md_state_view v{};
+        v.x = xs[s].data();
+        v.v = vs[s].data();
+        if ((rc = get_state(s, &v))) return rc;
+        saved[s] = v;
+        base[s] = sys[s]->prm;
+    }
+    const double skins[] = {0.5, 1.0, 1.5, 2.0};
+    const int dbits[] = {-1, 0, 1};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    double best_skin = base[0].skin;
+    int best_d = 0;
+    for (double sk : skins) {
+        for (int d : dbits) {
+            for (int s = 0; s < n; ++s) {
+                md_params p = base[s];
+                p.skin = sk;
+                p.sort_bits = std::min(7, std::max(2, auto_bits(sys[s]->N) + d));
+                if ((rc = set_params(s, p)) || (rc = set_state(s, &saved[s]))) goto done;
+            }
+            if ((rc = step(2, nullptr))) goto done;
+            CK(cudaEventRecord(e0, stream_));
+            if ((rc = step_async(steps, nullptr, nullptr))) goto done;
+            CK(cudaEventRecord(e1, stream_));
+            if ((rc = check_errors())) goto done;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_skin = sk;
+                best_d = d;
+            }
+        }
+    }
+    for (int s = 0; s < n; ++s) {
+        md_params p = base[s];
+        p.skin = best_skin;
+        p.sort_bits = std::min(7, std::max(2, auto_bits(sys[s]->N) + best_d));
+        if ((rc = set_params(s, p)) || (rc = set_state(s, &saved[s]))) goto done;
+        sys[s]->host_step = saved[s].step;
+    }
+    if (chosen) *chosen = sys[0]->prm;
+    rc = MD_OK;
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 int Engine::info(int idx, md_info_t* out) {

@@ -74,6 +74,7 @@ public:
     int set_state(int idx, const md_state_view* v);
     int set_params(int idx, const md_params& p);
     int info(int idx, md_info_t* out);
+    int autotune(int64_t steps, md_params* chosen);
     int check_errors();                     // sync + MD_ENUMERIC
     size_t device_bytes() const;
 

@@ -399,8 +399,37 @@ __device__ inline int list_entry(const SysConst& S, int I, int J, const float4& 
     return d2 < T.R2cross ? (J | kNucBit) : -1;
 }
 
+// Boxes of super-tiles (32 consecutive tiles, compact in Hilbert order):
+// one thread each, union of the member tiles' boxes.
+__global__ void k_super(EngineDev E) {
+    if (!*E.any_rebuild) return;
+    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (g >= E.ntiles) return;
+    const int s = E.tile_sys[g];
+    if (s < 0) return;
+    const SysConst& S = E.sys[s];
+    if (!sys_rebuilds(S)) return;
+    const int I = g - S.tile_base;           // one warp per tile; lane 0 of every 32nd tile works
+    if (I >= S.T || (I % kTile) != 0 || lane != 0) return;
+    const int t1 = min(S.T, I + kTile);
+    float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+    for (int t = I; t < t1; ++t)
+        for (int a = 0; a < 3; ++a) {
+            const float c = S.torgf[4 * t + a], h = S.thalf[3 * t + a];
+            lo[a] = fminf(lo[a], c - h);
+            hi[a] = fmaxf(hi[a], c + h);
+        }
+    // half extents rounded up, as for tiles
+    S.sorg[I / kTile] = make_float4(0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2]), 0.f);
+    S.shalf[I / kTile] = make_float4(0.5f * (hi[0] - lo[0]) * (1.0f + 1e-6f) + 1e-4f,
+                                     0.5f * (hi[1] - lo[1]) * (1.0f + 1e-6f) + 1e-4f,
+                                     0.5f * (hi[2] - lo[2]) * (1.0f + 1e-6f) + 1e-4f, 0.f);
+}
+
 // Force lists in one pass: tile I's entries go to list[I*T ...], its count
 // to lcount[I] (the list buffer holds T entries per tile, the worst case).
+// Super-tiles out of range of I (widest range) are skipped whole.
 __global__ void k_lbuild(EngineDev E) {
     if (!*E.any_rebuild) return;
     const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
@@ -425,12 +454,34 @@ __global__ void k_lbuild(EngineDev E) {
     const float hI[3] = {S.thalf[3 * I], S.thalf[3 * I + 1], S.thalf[3 * I + 2]};
     int* lst = S.list + (long long)I * S.T;
     int out = 0;
-    for (int J0 = 0; J0 < S.T; J0 += 32) {
-        const int J = J0 + lane;
-        const int e = J < S.T ? list_entry(S, I, J, oI, hI, T) : -1;
-        const unsigned m = __ballot_sync(0xffffffffu, e >= 0);
-        if (e >= 0) lst[out + __popc(m & ((1u << lane) - 1u))] = e;
-        out += __popc(m);
+    const int nsup = (S.T + kTile - 1) / kTile;
+    const float R2max = fmaxf(T.R2same, T.R2cross);
+    for (int s0 = 0; s0 < nsup; s0 += 32) {
+        const int sg = s0 + lane;
+        bool pass = false;
+        if (sg < nsup) {
+            const float4 c = S.sorg[sg], h = S.shalf[sg];
+            const float dd[3] = {oI.x - c.x, oI.y - c.y, oI.z - c.z};
+            const float hh[3] = {h.x, h.y, h.z};
+            float d2 = 0.0f;
+            for (int a = 0; a < 3; ++a) {
+                float d = dd[a];
+                d -= T.Lf * rintf(d * T.iLf);
+                const float gap = fmaxf(fabsf(d) - hI[a] - hh[a], 0.0f);
+                d2 = fmaf(gap, gap, d2);
+            }
+            pass = d2 < R2max;
+        }
+        unsigned sm = __ballot_sync(0xffffffffu, pass);
+        while (sm) {
+            const int b = __ffs(sm) - 1;
+            sm &= sm - 1;
+            const int J = (s0 + b) * kTile + lane;
+            const int e = J < S.T ? list_entry(S, I, J, oI, hI, T) : -1;
+            const unsigned m = __ballot_sync(0xffffffffu, e >= 0);
+            if (e >= 0) lst[out + __popc(m & ((1u << lane) - 1u))] = e;
+            out += __popc(m);
+        }
     }
     if (lane == 0) {
         S.lcount[I] = out;
@@ -548,8 +599,9 @@ void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int on
     H.rec("tiles", s);
     k_tiles<<<nb, kBlock, 0, s>>>(E);
     H.rec("lists", s);
+    k_super<<<nb, kBlock, 0, s>>>(E);
     k_lbuild<<<nb, kBlock, 0, s>>>(E);
-    H.count(9);
+    H.count(10);
 }
 
 // phase 0: count and scan (host then checks capacity); phase 1: write.

@@ -179,6 +179,12 @@ int md_kernel_times(md_system* s, int max, const char** names, int64_t* launches
     return s->eng->kernel_times(max, names, launches, ms, n);
 }
 
+int md_autotune(md_system* s, int64_t steps, md_params* chosen) {
+    GUARD(s);
+    if (!s->owner) return fail(MD_EINVAL, "tune a batch through md_batch_autotune");
+    return s->eng->autotune(steps, chosen);
+}
+
 // ------------------------------------------------------------------ batch
 int md_batch_create(int n, const md_job* jobs, const md_params* p, md_batch** out) {
     if (!out || !jobs || n <= 0) return fail(MD_EINVAL, "need n > 0 jobs and an out pointer");
@@ -211,6 +217,11 @@ int md_batch_create(int n, const md_job* jobs, const md_params* p, md_batch** ou
 int md_batch_step(md_batch* b, int64_t n) {
     GUARD(b);
     return b->eng->step(n, &b->xi);
+}
+
+int md_batch_autotune(md_batch* b, int64_t steps, md_params* chosen) {
+    GUARD(b);
+    return b->eng->autotune(steps, chosen);
 }
 
 int md_batch_system(md_batch* b, int i, md_system** out) {

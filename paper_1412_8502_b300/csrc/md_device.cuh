@@ -83,6 +83,8 @@ struct SysConst {
     double* torg;            // [T*3] FP64 tile origins
     float* torgf;            // [T*4] FP32 origin (x,y,z) and max half-extent
     float* thalf;            // [T*3] tile half-extents at rebuild
+    float4* sorg;            // [ceil(T/32)] super-tile (32 tiles) box centre
+    float4* shalf;           // [ceil(T/32)] super-tile box half extents
     int* lcount;             // [T]
     int* lstart;             // [T+1]
     int* list;               // [list_cap] tile-pair entries: J | kNucBit

@@ -107,6 +107,8 @@ _SIGS = {
     "md_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(md_result)]),
     "md_server_drain": (ctypes.c_int, [_P, _D]),
     "md_server_destroy": (ctypes.c_int, [_P]),
+    "md_autotune": (ctypes.c_int, [_P, _I64, ctypes.POINTER(md_params)]),
+    "md_batch_autotune": (ctypes.c_int, [_P, _I64, ctypes.POINTER(md_params)]),
     "md_clusters_noalloc": (ctypes.c_int, [_P, _I64, _I64, _D, _D, _D, _P, _P, _P, _P, _P]),
 }
 
@@ -271,6 +273,18 @@ def md_kernel_times(h) -> dict:
     return {names[i].decode(): (cnt[i], ms[i]) for i in range(k)}
 
 
+def md_autotune(h, steps: int = 10) -> md_params:
+    p = md_params()
+    _ck(LIB.md_autotune(h, int(steps), ctypes.byref(p)), "md_autotune")
+    return p
+
+
+def md_batch_autotune(b, steps: int = 10) -> md_params:
+    p = md_params()
+    _ck(LIB.md_batch_autotune(b, int(steps), ctypes.byref(p)), "md_batch_autotune")
+    return p
+
+
 def _jobs(jobs):
     arr = (md_job * len(jobs))()
     for i, j in enumerate(jobs):
@@ -394,6 +408,9 @@ class System:
     def kernel_times(self):
         return md_kernel_times(self.h)
 
+    def autotune(self, steps=10):
+        return md_autotune(self.h, steps)
+
 
 class Batch:
     """Independent systems advanced by one graph launch per step."""
@@ -405,6 +422,9 @@ class Batch:
 
     def step(self, n):
         md_batch_step(self.b, n)
+
+    def autotune(self, steps=10):
+        return md_batch_autotune(self.b, steps)
 
     def close(self):
         if self.b is not None:

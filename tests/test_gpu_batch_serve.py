@@ -110,3 +110,26 @@ def test_server_poll_empty_and_bad_job(md):
         m.md_server_submit(sv, dict(N=1, Yp=0.3, rho=0.08, T=1.0, seed=1, xi_dot=0.0, steps=5))
     m.md_server_drain(sv, 10.0)
     m.md_server_destroy(sv)
+
+
+def test_autotune_restores_state_and_picks_a_candidate(md):
+    p = params(md)
+    s = md.System(3000, 0.3, 0.04, 1.0, 21, p)
+    s.step(5, 0.0)
+    g0 = s.state()
+    chosen = s.autotune(4)
+    g1 = s.state()
+    assert np.array_equal(g0["x"], g1["x"]) and np.array_equal(g0["v"], g1["v"])
+    assert g0["t"] == g1["t"] and g0["step"] == g1["step"] and g0["L"] == g1["L"]
+    assert chosen.skin in (0.5, 1.0, 1.5, 2.0) and 2 <= chosen.sort_bits <= 7
+    s.step(10, 0.0)
+    F = s.forces()
+    g = s.state()
+    Fo, _ = oracle.forces(g["x"], g["type"], g["L_F"], oracle.params(s.params.r_C))
+    assert np.linalg.norm(F - Fo) / np.linalg.norm(Fo) <= 1e-5
+    b = md.Batch(JOBS[:2], p)
+    cb = b.autotune(3)
+    assert cb.skin in (0.5, 1.0, 1.5, 2.0)
+    b.step(5)
+    b.close()
+    s.close()
