@@ -382,21 +382,30 @@ __device__ inline float box_d2(const SysConst& S, const float4& oI, const float*
     return d2;
 }
 
-// Entry for J from I, or -1 if out of range.
-__device__ inline int list_entry(const SysConst& S, int I, int J, const float4& oI,
-                                 const float* hI, const ListTest& T) {
+// Entry for J from I, or -1 if out of range (see kJMask / kShiftPos /
+// kNucBit).  The shift moves J's frame next to I's: s = rint((O_I - O_J)/L).
+__device__ inline int list_entry(const SysConst& S, int I, int J, const float4& oI, const float* hI,
+                                 const ListTest& T) {
     const bool Ip = I < S.Tp, Jp = J < S.Tp;
-    if (T.cluster) {
-        if (!Jp) return -1;
-        const float d2 = box_d2(S, oI, hI, J, T);
-        return d2 < (Ip ? T.R2same : T.R2cross) ? J : -1;
-    }
+    if (T.cluster && !Jp) return -1;
     const float d2 = box_d2(S, oI, hI, J, T);
+    int e;
+    if (T.cluster) {
+        if (!(d2 < (Ip ? T.R2same : T.R2cross))) return -1;
+        return J;
+    }
     if (Ip && Jp) {
         if (!(d2 < T.R2same)) return -1;
-        return J | (d2 < T.R2nuc ? kNucBit : 0);
+        e = J | (d2 < T.R2nuc ? kNucBit : 0);
+    } else {
+        if (!(d2 < T.R2cross)) return -1;
+        e = J | kNucBit;
     }
-    return d2 < T.R2cross ? (J | kNucBit) : -1;
+    const float4 oJ = *reinterpret_cast<const float4*>(&S.torgf[4 * J]);
+    const int sx = (int)rintf((oI.x - oJ.x) * T.iLf);
+    const int sy = (int)rintf((oI.y - oJ.y) * T.iLf);
+    const int sz = (int)rintf((oI.z - oJ.z) * T.iLf);
+    return e | (((sx + 1) | ((sy + 1) << 2) | ((sz + 1) << 4)) << kShiftPos);
 }
 
 // Boxes of super-tiles (32 consecutive tiles, compact in Hilbert order):

@@ -59,7 +59,7 @@ struct PairConsts {
 struct Acc {
     float fx, fy, fz;
     float en, ec, w;
-    int nn, nc;              // in-range pairs (energy pass only)
+    float nn, nc;            // in-range pairs (energy pass only), exact below 2^24
 };
 
 struct Kahan {
@@ -91,6 +91,7 @@ __device__ __forceinline__ void one_pair(const float4& q, const float4& u, const
         dz = fmaf(-C.Llo, kz, fmaf(-C.Lhi, kz, dz));
     }
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    // in-range masks as 0/1 factors: branch-free predication of the updates
     float fr = 0.0f;
     if (kClass == kPPNuc || kClass == kPPCoul) {
         const float ri = rsqrt_approx(r2);
@@ -99,25 +100,27 @@ __device__ __forceinline__ void one_pair(const float4& q, const float4& u, const
         const float vc = ea * ri;                             // screened Coulomb V
         const float fc = vc * ri * (ri + C.il);
         bool in = r2 < C.rc2;
-        if (self_possible) in = in && (r2 > 0.0f);
-        if (in) {
-            fr = fc;
-            if (kEnergy) {
-                acc.ec += vc;
-                acc.nc += 1;
-            }
+        if (self_possible) {
+            // the target itself (r2 = 0) gives inf: select, never multiply
+            in = in && (r2 > 0.0f);
+            fr = in ? fc : 0.0f;
+            if (kEnergy) acc.ec += in ? vc : 0.0f;
+        } else {
+            const float m = in ? 1.0f : 0.0f;
+            fr = fc * m;
+            if (kEnergy) acc.ec = fmaf(vc, m, acc.ec);
         }
+        if (kEnergy) acc.nc += in ? 1.0f : 0.0f;
     }
     if (kClass != kPPCoul) {
         const float gq = ex2_approx(r2 * C.kq);
         bool in = r2 < C.rn2;
         if (self_possible) in = in && (r2 > 0.0f);
-        if (in) {
-            fr = fmaf(gq, fmaf(C.A2, gq, S), fr);
-            if (kEnergy) {
-                acc.en = fmaf(gq, fmaf(C.a, gq, bS), acc.en);
-                acc.nn += 1;
-            }
+        const float gm = in ? gq : 0.0f;
+        fr = fmaf(gm, fmaf(C.A2, gq, S), fr);
+        if (kEnergy) {
+            acc.en = fmaf(gm, fmaf(C.a, gq, bS), acc.en);
+            acc.nn += in ? 1.0f : 0.0f;
         }
     }
     acc.fx = fmaf(fr, dx, acc.fx);
@@ -179,7 +182,7 @@ struct Totals {
 template <int kClass, bool kLo, bool kWrap, bool kEnergy>
 __device__ __forceinline__ void run_block(const float4* qh, const float4* ql, int n, const float4& hi,
                                           const float4& lo, const PairConsts& C, Totals& T) {
-    Acc a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0};
+    Acc a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     pair_block<kClass, kLo, kWrap, kEnergy>(qh, ql, n, hi, lo, C, a);
     T.kx.add(a.fx);
     T.ky.add(a.fy);
@@ -188,8 +191,8 @@ __device__ __forceinline__ void run_block(const float4* qh, const float4* ql, in
         T.ken.add(a.en);
         T.kec.add(a.ec);
         T.kw.add(a.w);
-        T.nn += a.nn;
-        T.nc += a.nc;
+        T.nn += (int)a.nn;
+        T.nc += (int)a.nc;
         T.blocks += 1;
     }
 }
@@ -273,15 +276,8 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
     auto stage = [&](int e) {
         const int slot = (e - e0) % kStages;
         const int ent = lst[e];
-        const int J = ent & (kNucBit - 1);
-        if (lane == 0) {
-            const float4 oJ = *reinterpret_cast<const float4*>(&S.torgf[4 * J]);
-            const int sx = (int)rintf((oI.x - oJ.x) * C.iLf);
-            const int sy = (int)rintf((oI.y - oJ.y) * C.iLf);
-            const int sz = (int)rintf((oI.z - oJ.z) * C.iLf);
-            const int code = (sx + 1) | ((sy + 1) << 2) | ((sz + 1) << 4);
-            Q.sJ[slot] = J | (code << 24) | ((ent & kNucBit) ? (1 << 30) : 0);
-        }
+        const int J = ent & kJMask;
+        if (lane == 0) Q.sJ[slot] = ent;
         cp_async16(&Q.sh[slot][lane], &S.xhi[J * kTile + lane]);
         if ((ent & kNucBit) || !(Ip && J < S.Tp && S.coulomb)) cp_async16(&Q.sl[slot][lane], &S.xlo[J * kTile + lane]);
     };
@@ -296,9 +292,9 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
         __syncwarp();
         const int slot = (e - e0) % kStages;
         const int tag = Q.sJ[slot];
-        const int Jk = tag & 0xFFFFFF;
-        const int shk = (tag >> 24) & 63;
-        const bool nucflag = (tag >> 30) & 1;
+        const int Jk = tag & kJMask;
+        const int shk = (tag >> kShiftPos) & 63;
+        const bool nucflag = (tag & kNucBit) != 0;
         float4 h = Q.sh[slot][lane];
         const bool Jp = Jk < S.Tp;
         const bool farc = Ip && Jp && S.coulomb && !nucflag;      // Coulomb-only entry
@@ -422,7 +418,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fp64(EngineDev E, in
     const int* lst = S.list + (long long)I * S.T;
     const int e0 = 0, e1 = S.lcount[I];
     for (int e = e0; e < e1; ++e) {
-        const int J = lst[e] & (kNucBit - 1);
+        const int J = lst[e] & kJMask;
         const int q = tile_slot0(S, J) + lane;
         const bool qv = q < tile_end(S, J);
         __syncwarp();

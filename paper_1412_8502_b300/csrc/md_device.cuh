@@ -26,7 +26,12 @@ constexpr int kTile = 32;
 constexpr int kTilesPerBlock = 8;
 constexpr int kBlock = kTile * kTilesPerBlock;
 constexpr float kPad = 1.0e9f;          // local coordinate of an empty slot
-constexpr int kNucBit = 1 << 30;        // list entry flag: nuclear term reachable
+// Pair-list entry: bits 0-23 source tile J, 24-29 periodic shift code
+// (sx+1) | (sy+1) << 2 | (sz+1) << 4 moving J next to the target tile,
+// bit 30 set when the nuclear term is reachable.
+constexpr int kJMask = (1 << 24) - 1;
+constexpr int kShiftPos = 24;
+constexpr int kNucBit = 1 << 30;
 
 // Mutable per-system scalars (device memory).
 struct SysState {
