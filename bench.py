@@ -56,7 +56,8 @@ SMS, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
 
 
 def dist_env():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+    from paper_1412_8502_b300 import replicas
+    return replicas.dist_env()
 
 
 class Clocks:
@@ -130,19 +131,17 @@ def force_traffic():
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
-    import torch.distributed as dist
-    from paper_1412_8502_b300 import md
+    from paper_1412_8502_b300 import md, replicas
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
+    replicas.init("nccl")
     W = WORKLOADS[args.workload]
     N = W["N"]
     p = md.md_params_default()
     p.energy_every = 1
     p.T = W["T"]
-    sys_ = md.System(N, W["Yp"], W["rho"], W["T"], W["seed"] + 1000 * rank, p)
+    sys_ = md.System(N, W["Yp"], W["rho"], W["T"], replicas.replica_seed(W["seed"], rank), p)
     stream = torch.cuda.Stream()
     sys_.set_stream(stream)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -156,8 +155,7 @@ def run_gpu(args):
     K = args.steps
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K + 1)]
     pairs_nuc = pairs_coul = cand = 0
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("timed")
     with Clocks(local) as clk:
@@ -180,11 +178,7 @@ def run_gpu(args):
     torch.cuda.nvtx.range_pop()
     step_ms = [a.elapsed_time(b) for a, b in evs[:K]]
     cl_ms = evs[K][0].elapsed_time(evs[K][1])
-    total_ms = sum(step_ms) + cl_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(sum(step_ms) + cl_ms, device="cuda")
     info = sys_.info()
     launches = info["launches"] - launches0 + 6   # + the cluster kernels
     kt = sys_.kernel_times()
@@ -212,8 +206,7 @@ def run_gpu(args):
                        "md_step_energy"}
 
     if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
+        replicas.finalize()
         return None
 
     force_ms, force_n = kt.get("force", (0, 0.0))[1], kt.get("force", (0, 0.0))[0]
@@ -269,8 +262,7 @@ def run_gpu(args):
         line["serve"] = run_serve(args.serve_jobs, args.serve_steps, args.serve_rate)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(W, args.cpu_seconds)
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finalize()
     return line
 
 

@@ -62,20 +62,27 @@ typedef struct {
     double r_nuc;            /* nuclear cutoff, fm (Sec. II.A: 11.5) */
     double r_C;              /* Coulomb cutoff, fm; <= 0 means min(40, L0/2).
                                 Must not exceed L0/2 (MD_EINVAL). */
-    double lambda_s;         /* Coulomb screening length, fm (Sec. II.A: 10) */
+    double lambda_s;         /* Coulomb screening length, fm (Sec. II.A: 10);
+                                0 = Thomas-Fermi value of Eq. (2) at the initial
+                                proton density (md_lambda_thomas_fermi) */
     double skin;             /* pair-list skin, fm (default 1) */
     int64_t rebuild_every;   /* rebuild pair lists at least every k steps (10) */
     int64_t thermostat_every;/* velocity rescale period in steps (100); 0 = off */
     double T;                /* rescale temperature, MeV (md_create sets it) */
     int32_t precision;       /* MD_PREC_SPLIT (default) or MD_PREC_FP64 */
-    int32_t coulomb;         /* 1 = include the screened Coulomb term (default) */
+    int32_t coulomb;         /* screened Coulomb term of V_pp: 0 = off;
+                                1 = pairs inside r_C (default, pair lists);
+                                2 = every proton pair, nearest image, no cutoff
+                                    (Sec. II.A as printed; O(Np^2) per step) */
     double r_pp, r_np;       /* cluster link radii, fm (Sec. II.C: 4.5, 3) */
     int64_t relax_iters;     /* steepest-descent iterations in md_create (500) */
     double relax_gamma;      /* steepest-descent step, fm^2/MeV (0.002) */
     double relax_dmax;       /* per-iteration displacement clamp, fm (0.1) */
     int64_t energy_every;    /* md_step records energies every k steps; 0 = off */
     int32_t sort_bits;       /* spatial-sort bits per axis, 2..7; 0 = from N */
-    int32_t reserved0;
+    int32_t affine;          /* 1: scale positions by L_{n+1}/L_n after each box
+                                update (an option; the paper does not rescale,
+                                Sec. II.A); 0 = off (default) */
 } md_params;
 
 typedef struct {
@@ -199,6 +206,10 @@ MD_API int md_kernel_times(md_system* s, int max, const char** names, int64_t* l
  * does not depend on these settings; trajectories differ only by FP32
  * summation order. */
 MD_API int md_autotune(md_system* s, int64_t steps, md_params* chosen);
+
+/* Eq. (2): Thomas-Fermi screening length (fm) of a degenerate relativistic
+ * electron gas of density n_e (fm^-3), equal to the proton density. */
+MD_API double md_lambda_thomas_fermi(double n_e);
 
 /* Thread-local message describing the last error of this thread. */
 MD_API const char* md_last_error(void);

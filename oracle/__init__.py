@@ -51,7 +51,7 @@ class RunParams(ctypes.Structure):
     """Mirror of ``orc_run_params`` (integrator, Eq. 3 expansion, thermostat)."""
     _fields_ = [("dt", ctypes.c_double), ("xi_dot", ctypes.c_double),
                 ("L_base", ctypes.c_double), ("t_base", ctypes.c_double),
-                ("T", ctypes.c_double), ("thermostat_every", ctypes.c_int64)]
+                ("T", ctypes.c_double), ("thermostat_every", ctypes.c_int64), ("affine", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -81,6 +81,8 @@ def lib():
         L.orc_wrap.restype = ctypes.c_double
         L.orc_run.argtypes = [ctypes.c_int64, _D, _D, _D, _I8, _P,
                               ctypes.POINTER(RunParams), ctypes.c_int64, _D, _I64, _D]
+        L.orc_lambda_tf.argtypes = [ctypes.c_double]
+        L.orc_lambda_tf.restype = ctypes.c_double
         L.orc_kinetic.argtypes = [ctypes.c_int64, _D, ctypes.c_double]
         L.orc_kinetic.restype = ctypes.c_double
         L.orc_clusters.argtypes = [ctypes.c_int64, _D, _I8, ctypes.c_double,
@@ -154,6 +156,11 @@ def wrap(x: float, L: float) -> float:
     return lib().orc_wrap(x, L)
 
 
+def lambda_tf(n_e: float) -> float:
+    """Eq. (2): Thomas-Fermi screening length (fm) at electron density n_e."""
+    return lib().orc_lambda_tf(float(n_e))
+
+
 def kinetic(v, M: float = 939.0) -> float:
     v = _as(v, np.float64).reshape(-1, 3)
     return lib().orc_kinetic(v.shape[0], _dp(v), M)
@@ -161,7 +168,7 @@ def kinetic(v, M: float = 939.0) -> float:
 
 def run(x, v, typ, L, p: Params, nsteps: int, dt: float = 2.0, xi_dot: float = 0.0,
         T: float = 0.0, thermostat_every: int = 0, t: float = 0.0, step: int = 0,
-        L_base: float | None = None, t_base: float = 0.0, F=None):
+        L_base: float | None = None, t_base: float = 0.0, F=None, affine: bool = False):
     """Velocity Verlet + Eq. (3) box growth + rescale (Sec. II.A).
 
     Returns dict(x, v, F, t, step, L).  When F is None it is computed at the
@@ -173,7 +180,7 @@ def run(x, v, typ, L, p: Params, nsteps: int, dt: float = 2.0, xi_dot: float = 0
     if F is None:
         F, _ = forces(x, typ, L, p)
     F = _as(F, np.float64).reshape(-1, 3).copy()
-    rp = RunParams(dt, xi_dot, L if L_base is None else L_base, t_base, T, thermostat_every)
+    rp = RunParams(dt, xi_dot, L if L_base is None else L_base, t_base, T, thermostat_every, 1 if affine else 0)
     tt = ctypes.c_double(t); ss = ctypes.c_int64(step); LL = ctypes.c_double(L)
     lib().orc_run(N, _dp(x), _dp(v), _dp(F), typ.ctypes.data_as(_I8), ctypes.byref(p),
                   ctypes.byref(rp), int(nsteps), ctypes.byref(tt), ctypes.byref(ss), ctypes.byref(LL))

@@ -227,7 +227,12 @@ void orc_run(int64_t N, double* x, double* v, double* F, const int8_t* type,
         for (int64_t k = 0; k < 3 * N; ++k) v[k] += h * F[k];
         *t += rp->dt;
         *step += 1;
+        const double L_old = *L;
         *L = rp->L_base * (1.0 + rp->xi_dot * (*t - rp->t_base));
+        if (rp->affine) {
+            const double sc = *L / L_old;
+            for (int64_t k = 0; k < 3 * N; ++k) x[k] *= sc;
+        }
         if (rp->thermostat_every > 0 && (*step % rp->thermostat_every) == 0) {
             double ke = orc_kinetic(N, v, p->M);
             if (ke > 0.0) {
@@ -236,6 +241,15 @@ void orc_run(int64_t N, double* x, double* v, double* F, const int8_t* type,
             }
         }
     }
+}
+
+double orc_lambda_tf(double n_e)
+{
+    const double pi = 3.14159265358979323846;
+    const double alpha = 1.0 / 137.035999084;
+    const double me = 0.51099895 / 197.3269804;     /* electron mass, fm^-1 */
+    const double kF = cbrt(3.0 * pi * pi * n_e);
+    return sqrt(pi) / (2.0 * sqrt(alpha)) / sqrt(kF * sqrt(kF * kF + me * me));
 }
 
 static int64_t uf_find(int64_t* parent, int64_t a)

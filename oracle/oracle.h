@@ -91,6 +91,8 @@ typedef struct {
     double L_base, t_base; /* L(t) = L_base * (1 + xi_dot * (t - t_base)) */
     double T;              /* thermostat temperature, MeV */
     int64_t thermostat_every; /* 0 = off; else rescale after every k-th step */
+    int affine;            /* 1: scale positions by L_{n+1}/L_n after the box update
+                              (an option outside the paper, which does not rescale) */
 } orc_run_params;
 
 /* Velocity Verlet with box expansion and isothermal rescale (Sec. II.A,
@@ -104,6 +106,12 @@ typedef struct {
 void orc_run(int64_t N, double* x, double* v, double* F, const int8_t* type,
              const orc_params* p, const orc_run_params* rp, int64_t nsteps,
              double* t, int64_t* step, double* L);
+
+/* Eq. (2): Thomas-Fermi screening length of a degenerate relativistic
+ * electron gas of density n_e (fm^-3): lambda = sqrt(pi)/(2 sqrt(alpha))
+ * (k_F sqrt(k_F^2 + m_e^2))^(-1/2), k_F = (3 pi^2 n_e)^(1/3), with the
+ * fine-structure constant alpha and m_e in fm^-1 (hbar = c = 1). */
+double orc_lambda_tf(double n_e);
 
 /* Kinetic energy 1/2 M sum v^2 (Kahan). */
 double orc_kinetic(int64_t N, const double* v, double M);

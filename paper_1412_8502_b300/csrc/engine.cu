@@ -47,6 +47,18 @@ int auto_bits(int64_t N) {
 }
 }  // namespace
 
+// Eq. (2): lambda = sqrt(pi)/(2 sqrt(alpha)) (k_F sqrt(k_F^2 + m_e^2))^(-1/2)
+// with k_F = (3 pi^2 n_e)^(1/3); hbar = c = 1, lengths in fm, so the electron
+// mass enters as m_e c^2 / (hbar c) in fm^-1 and alpha is the fine-structure
+// constant.
+double lambda_thomas_fermi(double n_e) {
+    const double pi = 3.14159265358979323846;
+    const double fine = 1.0 / 137.035999084;
+    const double m_e = 0.51099895 / 197.3269804;
+    const double k_F = std::cbrt(3.0 * pi * pi * n_e);
+    return std::sqrt(pi) / (2.0 * std::sqrt(fine)) / std::sqrt(k_F * std::sqrt(k_F * k_F + m_e * m_e));
+}
+
 void set_error(const std::string& msg) { g_err = msg; }
 int fail(int code, const std::string& msg) {
     g_err = msg;
@@ -149,14 +161,16 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     if (!(Yp >= 0.0 && Yp <= 1.0)) return fail(MD_EINVAL, "Yp must be in [0, 1]");
     if (!(rho > 0.0)) return fail(MD_EINVAL, "rho must be > 0");
     if (!(T >= 0.0)) return fail(MD_EINVAL, "T must be >= 0");
-    if (!(p.dt > 0.0) || !(p.r_nuc > 0.0) || !(p.skin > 0.0) || !(p.lambda_s > 0.0))
-        return fail(MD_EINVAL, "dt, r_nuc, skin and lambda_s must be > 0");
+    if (!(p.dt > 0.0) || !(p.r_nuc > 0.0) || !(p.skin > 0.0) || !(p.lambda_s >= 0.0))
+        return fail(MD_EINVAL, "dt, r_nuc, skin must be > 0 and lambda_s >= 0");
     if (p.precision != MD_PREC_SPLIT && p.precision != MD_PREC_FP64) return fail(MD_EINVAL, "bad precision");
     if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
+    if (p.coulomb < 0 || p.coulomb > 2) return fail(MD_EINVAL, "coulomb must be 0, 1 or 2");
+    if (p.affine != 0 && p.affine != 1) return fail(MD_EINVAL, "affine must be 0 or 1");
     const double L0 = std::cbrt((double)N / rho);
     double rC = p.r_C > 0.0 ? p.r_C : std::min(40.0, 0.5 * L0);
     // (relative slack of 1e-12 absorbs the rounding of cbrt)
-    if (rC > 0.5 * L0 * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_C exceeds L0/2");
+    if (p.coulomb == 1 && rC > 0.5 * L0 * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_C exceeds L0/2");
     if (!sys.empty() && p.precision != precision) return fail(MD_EINVAL, "mixed precision in one engine");
     precision = p.precision;
 
@@ -177,6 +191,7 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     s.prm = p;
     s.prm.r_C = rC;
     s.prm.T = T;
+    if (p.lambda_s == 0.0) s.prm.lambda_s = lambda_thomas_fermi((double)s.Np / (L0 * L0 * L0));
     s.xi = 0.0;
 
     SysConst& c = s.c;
@@ -233,7 +248,8 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     c.b = -26.0;
     c.c = 24.0;
     c.Lambda = 1.25;
-    c.lambda_s = p.lambda_s;
+    c.lambda_s = s.prm.lambda_s;
+    c.affine = p.affine;
     c.alpha = 197.3269804 / 137.035999084;
     c.r_nuc = p.r_nuc;
     c.r_C = rC;
@@ -243,12 +259,13 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     c.relax_dmax = p.relax_dmax;
     c.thermostat_every = (int)p.thermostat_every;
     c.rebuild_every = (int)std::max<int64_t>(1, p.rebuild_every);
-    c.coulomb = p.coulomb ? 1 : 0;
+    c.coulomb = p.coulomb;
     c.energy_every = (int)p.energy_every;
 
     SysState st{};
     st.L = st.L_base = st.L_F = st.L_build = L0;
     st.vscale = 1.0;
+    st.xscale = 1.0;
     st.force_rebuild = 1;
     CK(cudaMemcpy(s.d_st, &st, sizeof(st), cudaMemcpyHostToDevice));
     sys.push_back(h);
@@ -325,6 +342,8 @@ int Engine::build_tables() {
     E.blocksum = d_blocksum_;
     E.any_rebuild = d_any_;
     H_.precision = precision;
+    H_.any_pp = false;
+    for (SysHost* h : sys) H_.any_pp |= (h->c.coulomb == 2);
     return MD_OK;
 }
 
@@ -633,7 +652,7 @@ int Engine::set_state(int idx, const md_state_view* v) {
     if (v->N != h.N || v->Np != h.Np) return fail(MD_EINVAL, "N / Np do not match the system");
     if (!v->x || !v->v) return fail(MD_EINVAL, "x and v are required");
     if (!(v->L > 0.0)) return fail(MD_EINVAL, "L must be > 0");
-    if (h.prm.r_C > 0.5 * v->L * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_C exceeds L/2");
+    if (h.c.coulomb == 1 && h.prm.r_C > 0.5 * v->L * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_C exceeds L/2");
     if (v->type) {
         for (int64_t i = 0; i < h.N; ++i)
             if (v->type[i] != (i < h.Np ? 1 : 0)) return fail(MD_EINVAL, "type must list protons first");
@@ -655,9 +674,11 @@ int Engine::set_state(int idx, const md_state_view* v) {
 int Engine::set_params(int idx, const md_params& p) {
     SysHost& h = *sys[idx];
     const double rC = p.r_C > 0.0 ? p.r_C : std::min(40.0, 0.5 * h.L0);
-    if (rC > 0.5 * h.L0 * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_C exceeds L0/2");
-    if (!(p.dt > 0.0) || !(p.r_nuc > 0.0) || !(p.skin > 0.0) || !(p.lambda_s > 0.0))
-        return fail(MD_EINVAL, "dt, r_nuc, skin and lambda_s must be > 0");
+    if (p.coulomb < 0 || p.coulomb > 2) return fail(MD_EINVAL, "coulomb must be 0, 1 or 2");
+    if (p.coulomb == 1 && rC > 0.5 * h.L0 * (1.0 + 1e-12)) return fail(MD_EINVAL, "r_C exceeds L0/2");
+    if (!(p.dt > 0.0) || !(p.r_nuc > 0.0) || !(p.skin > 0.0) || !(p.lambda_s >= 0.0))
+        return fail(MD_EINVAL, "dt, r_nuc, skin must be > 0 and lambda_s >= 0");
+    if (p.affine != 0 && p.affine != 1) return fail(MD_EINVAL, "affine must be 0 or 1");
     if (p.precision != MD_PREC_SPLIT && p.precision != MD_PREC_FP64) return fail(MD_EINVAL, "bad precision");
     if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
     const int nbits = p.sort_bits ? p.sort_bits : auto_bits(h.N);
@@ -670,11 +691,13 @@ int Engine::set_params(int idx, const md_params& p) {
     }
     h.prm = p;
     h.prm.r_C = rC;
+    if (p.lambda_s == 0.0) h.prm.lambda_s = lambda_thomas_fermi((double)h.Np / (h.L0 * h.L0 * h.L0));
     SysConst& c = h.c;
     c.dt = p.dt;
     c.T_target = p.T;
     c.skin = p.skin;
-    c.lambda_s = p.lambda_s;
+    c.lambda_s = h.prm.lambda_s;
+    c.affine = p.affine;
     c.r_nuc = p.r_nuc;
     c.r_C = rC;
     c.r_pp = p.r_pp;
@@ -683,8 +706,15 @@ int Engine::set_params(int idx, const md_params& p) {
     c.relax_dmax = p.relax_dmax;
     c.thermostat_every = (int)p.thermostat_every;
     c.rebuild_every = (int)std::max<int64_t>(1, p.rebuild_every);
-    c.coulomb = p.coulomb ? 1 : 0;
+    const bool pp_changed = (c.coulomb == 2) != (p.coulomb == 2);
+    c.coulomb = p.coulomb;
     c.energy_every = (int)p.energy_every;
+    if (pp_changed) {
+        cudaStreamSynchronize(stream_);
+        drop_graphs();
+        H_.any_pp = false;
+        for (SysHost* q : sys) H_.any_pp |= (q->c.coulomb == 2);
+    }
     if (nbits != h.nbits) {
         // a different sort grid resizes the engine's bin tables
         h.nbits = nbits;

@@ -122,6 +122,9 @@ private:
     std::vector<std::string> korder_;
 };
 
+// Eq. (2) screening length (fm) at electron density n_e (fm^-3).
+double lambda_thomas_fermi(double n_e);
+
 // Thread-local error message helpers.
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);

@@ -348,7 +348,7 @@ __device__ inline ListTest make_test(const SysConst& S, int mode, float L) {
     T.iLf = 1.0f / L;
     if (mode == 0) {
         const float rn = (float)(S.r_nuc + S.skin) + kMargin;
-        const float rc = (float)((S.coulomb ? fmax(S.r_C, S.r_nuc) : S.r_nuc) + S.skin) + kMargin;
+        const float rc = (float)((S.coulomb == 1 ? fmax(S.r_C, S.r_nuc) : S.r_nuc) + S.skin) + kMargin;
         T.R2same = rc * rc;      // used for proton-proton only, see below
         T.R2cross = rn * rn;
         T.R2nuc = rn * rn;
@@ -454,7 +454,7 @@ __global__ void k_lbuild(EngineDev E) {
         st->cur = st->cur_next;
         // small boxes: tiles are too large for one image per tile pair
         const float hm = __uint_as_float(st->hmax);
-        const double rmax = (S.coulomb ? fmax(S.r_C, S.r_nuc) : S.r_nuc);
+        const double rmax = (S.coulomb == 1 ? fmax(S.r_C, S.r_nuc) : S.r_nuc);
         st->need_wrap = (rmax + S.skin + 2.0 * (double)hm + 1e-3 >= 0.5 * st->L) ? 1 : 0;
     }
     if (I >= S.T) return;
@@ -583,7 +583,7 @@ __global__ void k_lwrite(EngineDev E, int mode, int only) {
     // small boxes: tiles are too large for one image per tile pair
     if (I == 0 && lane == 0 && mode == 0) {
         const float hm = __uint_as_float(st->hmax);
-        const double rmax = (S.coulomb ? fmax(S.r_C, S.r_nuc) : S.r_nuc);
+        const double rmax = (S.coulomb == 1 ? fmax(S.r_C, S.r_nuc) : S.r_nuc);
         st->need_wrap = (rmax + S.skin + 2.0 * (double)hm + 1e-3 >= 0.5 * st->L) ? 1 : 0;
     }
 }

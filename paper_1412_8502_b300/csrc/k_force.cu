@@ -238,7 +238,7 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
 
     PairConsts C;
     C.rn2 = (float)(S.r_nuc * S.r_nuc);
-    C.rc2 = S.coulomb ? (float)(S.r_C * S.r_C) : 0.0f;
+    C.rc2 = S.coulomb == 1 ? (float)(S.r_C * S.r_C) : 0.0f;
     C.kq = (float)(-1.0 / (2.0 * S.Lambda * 0.69314718055994530942));
     C.A2 = (float)(2.0 * S.a / S.Lambda);
     C.a = (float)S.a;
@@ -255,7 +255,7 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
     C.iLf = (float)(1.0 / L);
     // source filter radii around I's box: cutoff + skin/2 (+ FP32 margin)
     const float half = 0.5f * (float)S.skin + 2e-3f;
-    const float Rn = (float)S.r_nuc + half, Rc = (float)(S.coulomb ? S.r_C : 0.0) + half;
+    const float Rn = (float)S.r_nuc + half, Rc = (float)(S.coulomb == 1 ? S.r_C : 0.0) + half;
     const float Rn2 = Rn * Rn, Rc2 = Rc * Rc;
 
     const float4 hi = S.xhi[I * kTile + lane];
@@ -263,7 +263,7 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
     const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
     const float hIx = S.thalf[3 * I], hIy = S.thalf[3 * I + 1], hIz = S.thalf[3 * I + 2];
     const bool Ip = I < S.Tp;
-    const int cls0 = (Ip && S.coulomb) ? kPPNuc : kNucSame;
+    const int cls0 = (Ip && S.coulomb == 1) ? kPPNuc : kNucSame;
     const int* lst = S.list + (long long)I * S.T;
     const int e0 = 0, e1 = S.lcount[I];
 
@@ -279,7 +279,7 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
         const int J = ent & kJMask;
         if (lane == 0) Q.sJ[slot] = ent;
         cp_async16(&Q.sh[slot][lane], &S.xhi[J * kTile + lane]);
-        if ((ent & kNucBit) || !(Ip && J < S.Tp && S.coulomb)) cp_async16(&Q.sl[slot][lane], &S.xlo[J * kTile + lane]);
+        if ((ent & kNucBit) || !(Ip && J < S.Tp && S.coulomb == 1)) cp_async16(&Q.sl[slot][lane], &S.xlo[J * kTile + lane]);
     };
     for (int d = 0; d < kStages - 1; ++d) {
         if (e0 + d < e1) stage(e0 + d);
@@ -297,7 +297,7 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
         const bool nucflag = (tag & kNucBit) != 0;
         float4 h = Q.sh[slot][lane];
         const bool Jp = Jk < S.Tp;
-        const bool farc = Ip && Jp && S.coulomb && !nucflag;      // Coulomb-only entry
+        const bool farc = Ip && Jp && S.coulomb == 1 && !nucflag;   // Coulomb-only entry
         float4 l = farc ? make_float4(0.f, 0.f, 0.f, 0.f) : Q.sl[slot][lane];
         __syncwarp();
         const bool valid = h.x != kPad;
@@ -323,7 +323,7 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
         const float gy = fmaxf(fabsf(uy) - hIy, 0.0f);
         const float gz = fmaxf(fabsf(uz) - hIz, 0.0f);
         const float d2 = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
-        if (Ip && Jp && S.coulomb) {
+        if (Ip && Jp && S.coulomb == 1) {
             const bool nuc = valid && !farc && d2 < Rn2;
             push(Q, 0, nuc, c0, lane, h, l);
             push(Q, 1, valid && !nuc && d2 < Rc2, c1, lane, h, l);
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fp64(EngineDev E, in
         sb[w][2][lane] = qv ? x[2 * N + q] : -1e30;
         __syncwarp();
         const bool Jp = J < S.Tp;
-        const bool pp = Ip && Jp && S.coulomb;
+        const bool pp = Ip && Jp && S.coulomb == 1;
         const double bc = (Ip == Jp) ? (S.b + S.c) : (S.b - S.c);
         for (int k = 0; k < kTile; ++k) {
             if (J == I && k == lane) continue;
@@ -496,6 +496,7 @@ void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, in
         else k_force_split<false><<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
     }
     H.count(1);
+    launch_coulomb_pp(H, s, energy, only, out_alt);
 }
 
 }  // namespace pasta

@@ -190,17 +190,30 @@ __global__ void k_sub_com(EngineDev E) {
     S.v[0][2 * N + p] -= st->scratch[2];
 }
 
+// Pending thermostat factor on v; with the affine option, the pending box
+// factor on x (displacement and tile-frame positions follow).
 __global__ void k_rescale(EngineDev E, int only) {
     Slot o;
     if (!slot_of(E, only, o) || !o.valid) return;
     const SysConst& S = E.sys[o.s];
     const SysState* st = S.st;
-    const double f = st->vscale;
-    if (f == 1.0) return;
+    const double f = st->vscale, g = st->xscale;
     const int c = st->cur, N = S.N, p = o.p;
-    S.v[c][p] *= f;
-    S.v[c][N + p] *= f;
-    S.v[c][2 * N + p] *= f;
+    if (f != 1.0) {
+        S.v[c][p] *= f;
+        S.v[c][N + p] *= f;
+        S.v[c][2 * N + p] *= f;
+    }
+    if (g != 1.0) {
+        double xs[3];
+        for (int a = 0; a < 3; ++a) {
+            const double x0 = S.x[c][a * N + p];
+            xs[a] = x0 * g;
+            S.x[c][a * N + p] = xs[a];
+            S.disp[a * N + p] += (float)(xs[a] - x0);
+        }
+        write_xt(S, o.t, threadIdx.x & 31, xs, st->L, true);
+    }
 }
 
 // ---------------------------------------------------------------- relax
@@ -318,6 +331,7 @@ __global__ void k_finalize(EngineDev E, int energy) {
     st->t = __dadd_rn(st->t, S.dt);
     st->step += 1;
     st->L = __dmul_rn(st->L_base, __dadd_rn(1.0, __dmul_rn(st->xi_dot, __dsub_rn(st->t, st->t_base))));
+    st->xscale = S.affine ? st->L / Lf : 1.0;
     double ke = 0.5 * S.M * v2;
     double f = 1.0;
     if (S.thermostat_every > 0 && (st->step % S.thermostat_every) == 0 && ke > 0.0) {
@@ -428,6 +442,7 @@ __global__ void k_set_clock(EngineDev E, int only, const double* c) {
     st->force_rebuild = 1;
     st->maxdisp2 = 0u;
     st->vscale = 1.0;
+    st->xscale = 1.0;
     st->have_energy = 0;
     st->last_build = st->step;
 }

@@ -29,6 +29,7 @@ struct ClusterBufs {
 struct EngineHost {
     EngineDev dev;
     int precision = 0;
+    bool any_pp = false;     // some system uses the all-pairs Coulomb (coulomb = 2)
     void* owner = nullptr;   // Engine*, for rec/count callbacks
     void (*rec_fn)(void*, const char*, cudaStream_t) = nullptr;
     void (*count_fn)(void*, int) = nullptr;
@@ -43,6 +44,7 @@ struct EngineHost {
 void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int only);
 void launch_cluster_lists(const EngineHost& H, cudaStream_t s, int phase, int only);
 void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt);
+void launch_coulomb_pp(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt);
 void launch_init(const EngineHost& H, cudaStream_t s, const unsigned long long* d_seeds);
 void launch_sd_update(const EngineHost& H, cudaStream_t s);
 void launch_kick_drift(const EngineHost& H, cudaStream_t s);

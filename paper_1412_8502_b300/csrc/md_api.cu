@@ -65,8 +65,10 @@ void md_params_default(md_params* p) {
     p->relax_dmax = 0.1;
     p->energy_every = 0;
     p->sort_bits = 0;
-    p->reserved0 = 0;
+    p->affine = 0;
 }
+
+double md_lambda_thomas_fermi(double n_e) { return pasta::lambda_thomas_fermi(n_e); }
 
 const char* md_last_error(void) { return pasta::last_error_cstr(); }
 

@@ -45,6 +45,7 @@ struct SysState {
     float hsum;              // sum of tile half-extents at the last rebuild
     int pad1;
     double vscale;           // pending thermostat factor (1 = none)
+    double xscale;           // pending affine position factor (1 = none)
     int64_t step, last_build, n_rebuilds, e_step;
     int64_t list_total;
     double scratch[3];       // initialisation scratch (centre-of-mass velocity)
@@ -74,6 +75,7 @@ struct SysConst {
     double a, b, c, Lambda, lambda_s, alpha, r_nuc, r_C;
     double r_pp, r_np, relax_gamma, relax_dmax;
     int thermostat_every, rebuild_every, coulomb, energy_every;
+    int affine;              // scale positions with the box (option, not the paper)
     // state arrays (index [cur] is current)
     double* x[2];
     double* v[2];

@@ -37,7 +37,7 @@ class md_params(ctypes.Structure):
                 ("rebuild_every", _I64), ("thermostat_every", _I64), ("T", _D),
                 ("precision", _I32), ("coulomb", _I32), ("r_pp", _D), ("r_np", _D),
                 ("relax_iters", _I64), ("relax_gamma", _D), ("relax_dmax", _D),
-                ("energy_every", _I64), ("sort_bits", _I32), ("reserved0", _I32)]
+                ("energy_every", _I64), ("sort_bits", _I32), ("affine", _I32)]
 
 
 class md_energy_t(ctypes.Structure):
@@ -109,6 +109,7 @@ _SIGS = {
     "md_server_destroy": (ctypes.c_int, [_P]),
     "md_autotune": (ctypes.c_int, [_P, _I64, ctypes.POINTER(md_params)]),
     "md_batch_autotune": (ctypes.c_int, [_P, _I64, ctypes.POINTER(md_params)]),
+    "md_lambda_thomas_fermi": (ctypes.c_double, [_D]),
     "md_clusters_noalloc": (ctypes.c_int, [_P, _I64, _I64, _D, _D, _D, _P, _P, _P, _P, _P]),
 }
 
@@ -271,6 +272,10 @@ def md_kernel_times(h) -> dict:
     ms = (_D * max(k, 1))()
     _ck(LIB.md_kernel_times(h, k, names, cnt, ms, ctypes.byref(n)), "md_kernel_times")
     return {names[i].decode(): (cnt[i], ms[i]) for i in range(k)}
+
+
+def md_lambda_thomas_fermi(n_e: float) -> float:
+    return LIB.md_lambda_thomas_fermi(float(n_e))
 
 
 def md_autotune(h, steps: int = 10) -> md_params:

@@ -1,0 +1,74 @@
+"""Variants of the path against the oracle (next rows of the scope):
+paper-literal Coulomb (every proton pair, nearest image, no cutoff),
+the Thomas-Fermi screening length of Eq. (2), and affine position scaling."""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from test_gpu_parity import cfg_drops, cfg_liquid, load, make, min_img, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def md():
+    from paper_1412_8502_b300 import md as m
+    return m
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("cfg", ["liquid", "drops"])
+def test_paper_literal_coulomb_all_pairs(md, precision, cfg):
+    x, t, L = cfg_liquid(2000, 0.4, 0.08, 51) if cfg == "liquid" else cfg_drops(3000, 0.3, 0.005, 52)
+    s, v = load(md, x, t, L, precision, coulomb=2)
+    F = s.forces()
+    po = oracle.params(1e30)                      # every nearest image inside the "cutoff"
+    Fo, (en, ec, w) = oracle.forces(x, t, L, po)
+    tol = 1e-5 if precision == 0 else 1e-11
+    assert rel_l2(F, Fo) <= tol, rel_l2(F, Fo)
+    e = s.energy()
+    scale = oracle.kinetic(v) + abs(en) + abs(ec)
+    etol = 1e-6 if precision == 0 else 1e-12
+    assert abs(e["PE_coul"] - ec) <= etol * scale
+    assert abs(e["PE_nuc"] - en) <= etol * scale
+    n_p = int(t.sum())
+    # a few steps stay consistent with the oracle's forces at the new state
+    s.step(5, 0.0)
+    g = s.state()
+    Fo2, _ = oracle.forces(g["x"], g["type"], g["L_F"], po)
+    assert rel_l2(s.forces(), Fo2) <= tol
+    assert n_p > 0
+
+
+def test_thomas_fermi_screening_length(md):
+    N, Yp, rho = 2000, 0.4, 0.08
+    p = md.md_params_default()
+    p.lambda_s = 0.0
+    p.relax_iters = 0
+    s = md.System(N, Yp, rho, 1.0, 3, p)
+    lam = s.params.lambda_s
+    L0 = (N / rho) ** (1 / 3)
+    ref = oracle.lambda_tf(s.Np / L0 ** 3)
+    assert abs(lam - ref) <= 1e-14 * ref
+    assert abs(md.md_lambda_thomas_fermi(0.032) - oracle.lambda_tf(0.032)) <= 1e-14 * 10
+    x, t, L = cfg_liquid(N, Yp, rho, 53)
+    s.set_state(x, inputs.maxwell(N, 1.0, 1), L)
+    Fo, _ = oracle.forces(x, t, L, oracle.params(s.params.r_C, lambda_s=lam))
+    assert rel_l2(s.forces(), Fo) <= 1e-5
+
+
+def test_affine_option_trajectory_fp64(md):
+    x, t, L = cfg_liquid(1200, 0.3, 0.08, 54)
+    s, v = load(md, x, t, L, 1, T=1.0, thermostat_every=0, affine=1)
+    xi = 2e-4
+    s.step(40, xi)
+    g = s.state()
+    r = oracle.run(x, v, t, L, oracle.params(s.params.r_C), 40, xi_dot=xi, affine=True)
+    assert g["L"] == r["L"]
+    assert np.abs(min_img(g["x"] - r["x"], r["L"])).max() < 1e-6
+    assert rel_l2(g["v"], r["v"]) < 1e-6
+    # positions moved with the box beyond what the velocities alone give
+    s0, _ = load(md, x, t, L, 1, T=1.0, thermostat_every=0, affine=0)
+    s0.step(40, xi)
+    assert np.abs(min_img(s0.state()["x"] - g["x"], r["L"])).max() > 1e-3

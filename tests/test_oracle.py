@@ -446,3 +446,33 @@ def test_expansion_rebase_keeps_L_continuous():
     r3 = oracle.run(r1["x"], r1["v"], t, L1, p, 50, xi_dot=3e-4, t=t1, step=r1["step"],
                     L_base=L1, t_base=t1, F=r1["F"])
     assert abs(r3["L"] - L1 * (1 + 3e-4 * 100.0)) < 1e-12
+
+
+def test_thomas_fermi_lambda_eq2_limits():
+    """Eq. (2): for k_F >> m_e, lambda -> sqrt(pi)/(2 sqrt(alpha) k_F); for
+    k_F << m_e, lambda -> sqrt(pi)/(2 sqrt(alpha)) (k_F m_e)^(-1/2).  At
+    the Y_p = 0.4 proton density 0.032 fm^-3 it is slightly above the 10 fm
+    the paper fixes (Sec. II.A)."""
+    alpha = 1 / 137.035999084
+    me = 0.51099895 / 197.3269804
+    pre = math.sqrt(math.pi) / (2 * math.sqrt(alpha))
+    ne = 10.0
+    kF = (3 * math.pi ** 2 * ne) ** (1 / 3)
+    assert abs(oracle.lambda_tf(ne) / (pre / kF) - 1) < 1e-5
+    ne = 1e-14
+    kF = (3 * math.pi ** 2 * ne) ** (1 / 3)
+    assert abs(oracle.lambda_tf(ne) / (pre / math.sqrt(kF * me)) - 1) < 1e-3
+    lam = oracle.lambda_tf(0.4 * 0.08)
+    assert 10.0 < lam < 11.0
+    assert oracle.lambda_tf(0.05 * 0.08) > lam     # decreasing in density
+
+
+def test_affine_option_scales_positions_with_the_box():
+    x = np.array([[35.0, 40.0, 45.0], [60.0, 62.0, 66.0]])
+    t = np.array([0, 0], dtype=np.int8)
+    v = np.zeros((2, 3))
+    p = P(r_C=10.0)
+    r = oracle.run(x, v, t, 100.0, p, 10, xi_dot=1e-3, affine=True)
+    assert np.allclose(r["x"] / x, r["L"] / 100.0, rtol=1e-13)
+    r0 = oracle.run(x, v, t, 100.0, p, 10, xi_dot=1e-3)
+    assert np.array_equal(r0["x"], x)
