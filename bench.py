@@ -151,7 +151,8 @@ def run_gpu(args):
             sys_.step(1, W["xi"])
     torch.cuda.synchronize()
     sys_.set_timing(True)
-    launches0 = sys_.info()["launches"]
+    info0 = sys_.info()
+    launches0, rebuilds0 = info0["launches"], info0["rebuilds"]
     K = args.steps
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K + 1)]
     pairs_nuc = pairs_coul = cand = 0
@@ -181,6 +182,7 @@ def run_gpu(args):
     total_ms = replicas.max_over_ranks(sum(step_ms) + cl_ms, device="cuda")
     info = sys_.info()
     launches = info["launches"] - launches0 + 6   # + the cluster kernels
+    rebuilds = info["rebuilds"] - rebuilds0
     kt = sys_.kernel_times()
     sys_.set_timing(False)
 
@@ -246,6 +248,7 @@ def run_gpu(args):
                   "halfext_mean_fm": info["tile_halfext_mean"], "halfext_max_fm": info["tile_halfext_max"],
                   "need_wrap": info["need_wrap"]},
         "kernel_ms_per_step": {k: v[1] / max(K, 1) for k, v in kt.items()},
+        "cell_build": cell_build_roofline(kt, rebuilds, N, info, peaks),
         "step_ms_p50": sorted(step_ms)[len(step_ms) // 2],
         "step_ms_p99": sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)],
         "cluster_ms": cl_ms,
@@ -264,6 +267,24 @@ def run_gpu(args):
         line["cpu_baseline"] = cpu_baseline(W, args.cpu_seconds)
     replicas.finalize()
     return line
+
+
+def cell_build_roofline(kt, rebuilds, N, info, peaks):
+    """Spatial sort + tile build (hist, scan, scatter, move, tiles) per
+    rebuild: algorithmic bytes / CUDA-event time (the kernels' early exits on
+    steps without a rebuild are included in the time, conservatively)."""
+    names = ("hist", "scan", "scatter", "move", "tiles")
+    ms = sum(kt.get(k, (0, 0.0))[1] for k in names)
+    if rebuilds <= 0 or ms <= 0:
+        return None
+    bins = 2 * (1 << (3 * info["sort_bits"]))
+    # per particle: hist 28 B (x, key), scatter 12 B, move 124 B (x, v, id read+write,
+    # slot/key/bin lookups), tiles 68 B (x read, hi/lo and displacement write); per bin 12 B
+    alg = 232.0 * N + 12.0 * bins
+    per = ms / rebuilds
+    gbs = alg / (per * 1e-3) / 1e9
+    return {"bound": "hbm", "rebuilds": rebuilds, "ms_per_rebuild": per, "bytes_per_rebuild": alg,
+            "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"]}
 
 
 # ------------------------------------------------------------------ batch / serve

@@ -284,7 +284,13 @@ __global__ void k_tiles(EngineDev E) {
         const long long nthr = (long long)((S.T + kTilesPerBlock - 1) / kTilesPerBlock) * kBlock;
         for (long long b = tid; b < nb; b += nthr) E.hist[S.bin_base + b] = 0u;
     }
-    if (t >= S.T) return;
+    __shared__ float s_hm[kTilesPerBlock], s_hs[kTilesPerBlock];
+    const int w = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_hm[w] = 0.0f;
+        s_hs[w] = 0.0f;
+    }
+    if (t < S.T) {
     const int p0 = tile_slot0(S, t), p1 = tile_end(S, t);
     const int p = p0 + lane;
     const bool valid = p < p1;
@@ -319,13 +325,25 @@ __global__ void k_tiles(EngineDev E) {
             S.torgf[4 * t + a] = (float)c[a];
         }
         S.torgf[4 * t + 3] = hm;
-        atomic_max_pos(&st->hmax, hm);
-        atomicAdd(&st->hsum, (float)((h[0] + h[1] + h[2]) / 3.0));
+        s_hm[w] = hm;
+        s_hs[w] = (float)((h[0] + h[1] + h[2]) / 3.0);
         if (t == 0) {
             st->last_build = st->step;
             st->n_rebuilds += 1;
             st->L_build = L;
         }
+    }
+    }
+    // one atomic per block for the system's largest / summed half-extents
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.0f, sum = 0.0f;
+        for (int k = 0; k < kTilesPerBlock; ++k) {
+            m = fmaxf(m, s_hm[k]);
+            sum += s_hs[k];
+        }
+        atomic_max_pos(&st->hmax, m);
+        atomicAdd(&st->hsum, sum);
     }
 }
 

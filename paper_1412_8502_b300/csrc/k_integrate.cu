@@ -222,7 +222,7 @@ __global__ void k_rescale(EngineDev E, int only) {
 template <typename FT>
 __global__ void k_sd_update(EngineDev E) {
     Slot o;
-    if (!slot_of(E, -1, o)) return;
+    if (!slot_of(E, -1, o)) return;     // whole block: systems start on block boundaries
     const SysConst& S = E.sys[o.s];
     SysState* st = S.st;
     const int lane = threadIdx.x & 31;
@@ -249,14 +249,14 @@ __global__ void k_sd_update(EngineDev E) {
         write_xt(S, o.t, lane, xs, L, true);
     }
     d2 = warp_max(d2);
-    if (lane == 0 && d2 > 0.0f) atomic_max_pos(&st->maxdisp2, d2);
+    block_atomic_max(&st->maxdisp2, d2);
 }
 
 // ---------------------------------------------------------------- Verlet
 template <typename FT>
 __global__ void k_kick_drift(EngineDev E) {
     Slot o;
-    if (!slot_of(E, -1, o)) return;
+    if (!slot_of(E, -1, o)) return;     // whole block: systems start on block boundaries
     const SysConst& S = E.sys[o.s];
     SysState* st = S.st;
     const int lane = threadIdx.x & 31;
@@ -278,7 +278,7 @@ __global__ void k_kick_drift(EngineDev E) {
         write_xt(S, o.t, lane, xs, L, true);
     }
     d2 = warp_max(d2);
-    if (lane == 0 && d2 > 0.0f) atomic_max_pos(&st->maxdisp2, d2);
+    block_atomic_max(&st->maxdisp2, d2);
 }
 
 template <typename FT>

@@ -187,6 +187,21 @@ __device__ inline void write_xt(const SysConst& s, int t, int lane, const double
     s.xlo[t * kTile + lane] = l;
 }
 
+// Block-level max of a non-negative float (one value per warp, lane 0
+// holding it), then one atomicMax per block.  Every thread of the block
+// must call it.
+__device__ inline void block_atomic_max(unsigned* addr, float warp_value) {
+    __shared__ float sm[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) sm[w] = warp_value;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.0f;
+        for (int k = 0; k < nw; ++k) m = fmaxf(m, sm[k]);
+        if (m > 0.0f) atomicMax(addr, __float_as_uint(m));
+    }
+}
+
 // atomicMax on the bit pattern of a non-negative float.
 __device__ inline void atomic_max_pos(unsigned* addr, float v) {
     atomicMax(addr, __float_as_uint(fmaxf(v, 0.0f)));
