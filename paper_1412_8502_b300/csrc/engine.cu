@@ -230,6 +230,7 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     A(&c.lstart, (size_t)s.T + 1);
     A(&c.list, (size_t)c.list_cap);
     A(&c.tile_e, 8 * (size_t)s.T);
+    A(&c.facc, 3 * (size_t)N);
     A(&c.blk, 4 * (size_t)(s.Tpad / kTilesPerBlock));
     A(&s.d_st, 1);
     A(&s.d_cl, 1);
@@ -271,6 +272,7 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     st.xscale = 1.0;
     st.force_rebuild = 1;
     CK(cudaMemcpy(s.d_st, &st, sizeof(st), cudaMemcpyHostToDevice));
+    CK(cudaMemset(c.facc, 0, 3 * (size_t)N * sizeof(long long)));   // the force pass expects zeros
     sys.push_back(h);
     return MD_OK;
 }
@@ -467,7 +469,7 @@ size_t Engine::estimate_bytes(int64_t N, double Yp, const md_params& p) {
     const int64_t nb = 2ll << (3 * nbits);
     size_t b = 0;
     b += 2 * (size_t)N * (8 * 3 + 8 * 3 + 4 + 4 * 3 + 8 * 3);   // x, v, id, f32, f64
-    b += (size_t)N * (4 * 3 + 4 + 4 + 9 * 8 + 1 + 4);           // disp, key, slot, staging
+    b += (size_t)N * (4 * 3 + 4 + 4 + 9 * 8 + 1 + 4 + 8 * 3);   // disp, key, slot, staging, facc
     b += (size_t)T * (32 * 32 + 8 * 3 + 16 + 12 + 4 + 4 + 64) + 4 * 8 * Tpad;
     b += (size_t)T * T * 4;                                      // pair list
     b += (size_t)nb * 12 + 4096;                                 // engine bins

@@ -393,7 +393,7 @@ __device__ inline float box_d2(const SysConst& S, const float4& oI, const float*
     for (int a = 0; a < 3; ++a) {
         float d = dd[a];
         d -= T.Lf * rintf(d * T.iLf);
-        float gap = fabsf(d) - hI[a] - S.thalf[3 * J + a];
+        float gap = fabsf(d) - (hI[a] + S.thalf[3 * J + a]);   // symmetric in I and J
         gap = fmaxf(gap, 0.0f);
         d2 = fmaf(gap, gap, d2);
     }
@@ -457,7 +457,18 @@ __global__ void k_super(EngineDev E) {
 // Force lists in one pass: tile I's entries go to list[I*T ...], its count
 // to lcount[I] (the list buffer holds T entries per tile, the worst case).
 // Super-tiles out of range of I (widest range) are skipped whole.
-__global__ void k_lbuild(EngineDev E) {
+// half = 1 (split precision): every unordered tile pair is listed once, the
+// forces of each pair being applied to both particles.  The pair {I, J} goes
+// to I when (I < J) differs from the parity of I + J, so that every tile
+// owns about half of its neighbours wherever it sits in the Hilbert order;
+// the tile itself is left out (the force kernel treats it first).
+// half = 0 (FP64 validation): full lists, the tile itself included.
+__device__ __forceinline__ bool owns_pair(int I, int J, int half) {
+    if (!half) return true;
+    return J != I && ((I < J) != (((I + J) & 1) != 0));
+}
+
+__global__ void k_lbuild(EngineDev E, int half) {
     if (!*E.any_rebuild) return;
     const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -504,7 +515,7 @@ __global__ void k_lbuild(EngineDev E) {
             const int b = __ffs(sm) - 1;
             sm &= sm - 1;
             const int J = (s0 + b) * kTile + lane;
-            const int e = J < S.T ? list_entry(S, I, J, oI, hI, T) : -1;
+            const int e = (J < S.T && owns_pair(I, J, half)) ? list_entry(S, I, J, oI, hI, T) : -1;
             const unsigned m = __ballot_sync(0xffffffffu, e >= 0);
             if (e >= 0) lst[out + __popc(m & ((1u << lane) - 1u))] = e;
             out += __popc(m);
@@ -627,7 +638,7 @@ void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int on
     k_tiles<<<nb, kBlock, 0, s>>>(E);
     H.rec("lists", s);
     k_super<<<nb, kBlock, 0, s>>>(E);
-    k_lbuild<<<nb, kBlock, 0, s>>>(E);
+    k_lbuild<<<nb, kBlock, 0, s>>>(E, H.precision == 0 ? 1 : 0);
     H.count(10);
 }
 

@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(kPW * 32) k_coulomb_pp_split(EngineDev E, int 
         if (lane == 0) {
             S.tile_e[8 * I + 1] = 0.5 * en;
             S.tile_e[8 * I + 2] += 0.5 * wv;
-            S.tile_e[8 * I + 4] = cn;
-            S.tile_e[8 * I + 5] += (double)S.Np * kTile;
+            S.tile_e[8 * I + 4] = 0.5 * cn;     // unique pairs
+            S.tile_e[8 * I + 5] += 0.5 * (double)S.Np * kTile;
         }
     }
 }
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kPW * 32) k_coulomb_pp_fp64(EngineDev E, int o
         if (lane == 0) {
             S.tile_e[8 * I + 1] = 0.5 * en;
             S.tile_e[8 * I + 2] += 0.5 * wv;
-            S.tile_e[8 * I + 4] = cn;
+            S.tile_e[8 * I + 4] = 0.5 * cn;
         }
     }
 }

@@ -1,26 +1,36 @@
 // Pair forces of Eq. (1) (Sec. II.A): nuclear term for every pair inside
 // r_nuc, screened Coulomb for proton pairs inside r_C, nearest periodic
-// image, no Newton's-third-law sharing (each target sums over all its
-// sources, as the paper's GPU kernel also does, Sec. II.B.1).
+// image.
 //
-// Work unit: one warp per 32-particle target tile I.  The warp walks I's
-// tile-pair list; for each source tile J every lane loads one source,
-// moves it to the periodic image next to I, and tests it against I's box
-// (cutoff + skin/2 covers the drift since the rebuild).  Sources that pass
-// are compacted (ballot + popc) into shared-memory queues, one per pair
-// class: proton-proton with the nuclear term (PPN), proton-proton Coulomb
-// only (PPC), unlike species (nuclear, b - c) and like species (nuclear,
-// b + c).  Whenever a queue holds 32 sources they are broadcast to all
-// lanes (LDS.128) and each lane adds the 32 pair forces on its own target
-// in registers; block partials are summed with Kahan compensation.
+// Split precision: every pair is evaluated once and its force applied to
+// both particles (Newton's third law; the paper's GPU kernel instead sums
+// every target over all its sources, Sec. II.B.1).  Work unit: one warp per
+// 32-particle target tile I.  The warp first evaluates the tile with itself,
+// then walks I's half tile-pair list (each unordered tile pair is listed
+// once); for each source tile J every lane loads one source, moves it to the
+// periodic image next to I, and tests it against I's box (cutoff + skin/2
+// covers the drift since the rebuild).  Sources that pass are compacted
+// (ballot + popc) into shared-memory queues, one per pair class:
+// proton-proton with the nuclear term (PPN), proton-proton Coulomb only
+// (PPC), unlike species (nuclear, b - c) and like species (nuclear, b + c).
+// A queue holding 32 sources is evaluated as a rotated block: at step k lane
+// l pairs its target with source (l + k) mod 32, keeps the target's force in
+// registers and passes the reaction on the source one lane down, so that
+// after 32 steps each lane holds the full reaction on one source.  Target
+// sums are Kahan-compensated over blocks.  All force contributions go to
+// per-particle 64-bit fixed-point accumulators (2^-32 MeV/fm) with integer
+// atomics, so the result does not depend on their order; a second kernel
+// turns them into FP32 forces and clears them.
 //
-// Precision (split mode): positions are exact FP32 pairs hi + lo of the
-// image nearest the tile origin; periodic shifts of sources use an
-// error-free two-sum, so every separation dx = (hi_i - hi_j) + (lo_i - lo_j)
-// carries only the rounding of its final sum, whatever the box size.  Pair
-// arithmetic is FP32; far Coulomb-only pairs (beyond r_nuc + skin/2 of the
-// target box) use the hi part only, an error below 1e-4 fm at r > 12 fm.
-// Energies are combined in FP64.
+// Precision: positions are exact FP32 pairs hi + lo of the image nearest the
+// tile origin; periodic shifts of sources use an error-free two-sum, so every
+// separation dx = (hi_i - hi_j) + (lo_i - lo_j) carries only the rounding of
+// its final sum, whatever the box size.  Pair arithmetic is FP32; far
+// Coulomb-only pairs (beyond r_nuc + skin/2 of the target box) use the hi
+// part only, an error below 1e-4 fm at r > 12 fm.  Energies are combined in
+// FP64.
+//
+// FP64 validation mode: full lists, one FP64 thread per target, no sharing.
 //
 // Single-exponential nuclear term: with g = exp(-r^2/(2 Lambda)),
 // exp(-r^2/Lambda) = g^2, so one ex2 serves both Gaussians of Eq. (1).
@@ -129,9 +139,8 @@ __device__ __forceinline__ void one_pair(const float4& q, const float4& u, const
     if (kEnergy) acc.w = fmaf(fr, r2, acc.w);
 }
 
-// A full block of 32 queued sources (compile-time trip count) or the final
-// partial block of n < 32 (no padding entries: in small boxes the per-pair
-// image would fold a far-away pad back into the box).
+// The tile against itself: all lanes take source k in turn (broadcast), for
+// all 32 sources (compile-time trip count) or the first n (ragged tiles).
 template <int kClass, bool kLo, bool kWrap, bool kEnergy>
 __device__ __forceinline__ void pair_block(const float4* __restrict__ qh, const float4* __restrict__ ql, int n,
                                            const float4& hi, const float4& lo, const PairConsts& C, Acc& acc) {
@@ -157,10 +166,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 constexpr int kForceWarps = 4;   // warps (target tiles) per block
 constexpr int kQ = 2 * kTile;    // queue capacity
 constexpr int kStages = 4;       // source tiles in flight per warp (cp.async)
+constexpr float kFix = 4294967296.0f;        // 2^32: force accumulators count 2^-32 MeV/fm
+constexpr double kUnfix = 1.0 / 4294967296.0;
+constexpr float kForceMax = 1.0e9f;          // |partial force| beyond this (MeV/fm) is an error
 
 struct WarpQueues {
     float4 h[3][kQ];             // 0: PPN / like species, 1: PPC, 2: unlike species
-    float4 l[3][kQ];             // low parts (queue 1 does not use them)
+    float4 l[2][kQ];             // low parts of queues 0 and 2 (PPC uses the high parts only)
+    float4 dh[2 * kTile];        // block being evaluated, stored twice (rotated reads)
+    float4 dl[2 * kTile];
     float4 sh[kStages][kTile];   // staged source tiles (high parts)
     float4 sl[kStages][kTile];   // staged source tiles (low parts)
     int sJ[kStages];             // staged tile index | shift code << 24 | nuclear flag
@@ -176,14 +190,114 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 struct Totals {
     Kahan kx, ky, kz, ken, kec, kw;
-    int nn = 0, nc = 0, blocks = 0;
+    int nn = 0, nc = 0;          // unique in-range pairs of the rotated blocks
+    int nn2 = 0, nc2 = 0;        // ordered in-range pairs of the tile with itself
+    int cand = 0;                // unique candidate pairs
+    bool bad = false;            // a reaction partial was not finite or out of range
 };
 
-template <int kClass, bool kLo, bool kWrap, bool kEnergy>
-__device__ __forceinline__ void run_block(const float4* qh, const float4* ql, int n, const float4& hi,
-                                          const float4& lo, const PairConsts& C, Totals& T) {
+__device__ __forceinline__ long long to_fix(float f) { return __float2ll_rn(f * kFix); }
+
+__device__ __forceinline__ float4 shfl_f4(const float4& v, int src) {
+    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+
+__device__ __forceinline__ void red_add(long long* a, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
+}
+
+// One pair of a rotated block: returns the scalar fr with F_target += fr d
+// and F_source -= fr d, where d = x_target - x_source.  kSel: masks by
+// select (partial blocks, whose unused slots hold zeros); otherwise by
+// multiplying with 0/1 (every slot is a real source, never the target).
+template <int kClass, bool kLo, bool kWrap, bool kEnergy, bool kSel>
+__device__ __forceinline__ float pair_n3(const float4& q, const float4& u, const float4& hi, const float4& lo,
+                                         const PairConsts& C, float S, float bS, bool ok, Acc& acc,
+                                         float& dx, float& dy, float& dz) {
+    dx = hi.x - q.x;
+    dy = hi.y - q.y;
+    dz = hi.z - q.z;
+    if (kLo) {
+        dx += lo.x - u.x;
+        dy += lo.y - u.y;
+        dz += lo.z - u.z;
+    }
+    if (kWrap) {
+        const float kx = rintf(dx * C.iLf), ky = rintf(dy * C.iLf), kz = rintf(dz * C.iLf);
+        dx = fmaf(-C.Llo, kx, fmaf(-C.Lhi, kx, dx));
+        dy = fmaf(-C.Llo, ky, fmaf(-C.Lhi, ky, dy));
+        dz = fmaf(-C.Llo, kz, fmaf(-C.Lhi, kz, dz));
+    }
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    float fr = 0.0f;
+    if (kClass == kPPNuc || kClass == kPPCoul) {
+        const float ri = rsqrt_approx(r2);
+        const float r = r2 * ri;
+        const float ea = ex2_approx(fmaf(r, C.kc, C.l2a));     // alpha e^{-r/lambda}
+        const float vc = ea * ri;                             // screened Coulomb V
+        const float fc = vc * ri * (ri + C.il);
+        const bool in = ok && r2 < C.rc2;
+        if (kSel) {
+            fr = in ? fc : 0.0f;
+            if (kEnergy) acc.ec += in ? vc : 0.0f;
+        } else {
+            const float m = in ? 1.0f : 0.0f;
+            fr = fc * m;
+            if (kEnergy) acc.ec = fmaf(vc, m, acc.ec);
+        }
+        if (kEnergy) acc.nc += in ? 1.0f : 0.0f;
+    }
+    if (kClass != kPPCoul) {
+        const float gq = ex2_approx(r2 * C.kq);
+        const bool in = ok && r2 < C.rn2;
+        const float gm = in ? gq : 0.0f;
+        fr = fmaf(gm, fmaf(C.A2, gq, S), fr);
+        if (kEnergy) {
+            acc.en = fmaf(gm, fmaf(C.a, gq, bS), acc.en);
+            acc.nn += in ? 1.0f : 0.0f;
+        }
+    }
+    acc.fx = fmaf(fr, dx, acc.fx);
+    acc.fy = fmaf(fr, dy, acc.fy);
+    acc.fz = fmaf(fr, dz, acc.fz);
+    if (kEnergy) acc.w = fmaf(fr, r2, acc.w);
+    return fr;
+}
+
+// A block of n <= 32 queued sources (in Q.dh/Q.dl twice over) against the
+// warp's 32 targets, every pair once: at step k lane l pairs its target with
+// source (l + k) mod 32.  The reaction on that source rides in registers
+// that rotate one lane down after every step, so after 32 steps lane l holds
+// the whole reaction on source l and adds it to the fixed-point accumulator.
+template <int kClass, bool kLo, bool kWrap, bool kEnergy, bool kFull>
+__device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, bool tv, const float4& hi,
+                                         const float4& lo, const PairConsts& C, Totals& T, long long* facc, int N) {
+    const float S = (kClass == kNucCross) ? C.Scross : C.Ssame;
+    const float bS = (kClass == kNucCross) ? C.bcross : C.bsame;
     Acc a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    pair_block<kClass, kLo, kWrap, kEnergy>(qh, ql, n, hi, lo, C, a);
+    float rx = 0.0f, ry = 0.0f, rz = 0.0f;
+    const float4* ph = Q.dh + lane;
+    const float4* pl = Q.dl + lane;
+    const int from = (lane + 1) & (kTile - 1);
+#pragma unroll 8
+    for (int k = 0; k < kTile; ++k) {
+        const float4 q = ph[k];
+        const float4 u = kLo ? pl[k] : q;
+        const bool ok = tv && (kFull || (((lane + k) & (kTile - 1)) < n));
+        float dx, dy, dz;
+        const float fr = pair_n3<kClass, kLo, kWrap, kEnergy, !kFull>(q, u, hi, lo, C, S, bS, ok, a, dx, dy, dz);
+        rx = __shfl_sync(0xffffffffu, fmaf(-fr, dx, rx), from);
+        ry = __shfl_sync(0xffffffffu, fmaf(-fr, dy, ry), from);
+        rz = __shfl_sync(0xffffffffu, fmaf(-fr, dz, rz), from);
+    }
+    if (kFull || lane < n) {
+        const int slot = __float_as_int(ph[0].w);
+        T.bad |= !(fabsf(rx) < kForceMax && fabsf(ry) < kForceMax && fabsf(rz) < kForceMax);
+        red_add(facc + slot, to_fix(rx));
+        red_add(facc + N + slot, to_fix(ry));
+        red_add(facc + 2 * N + slot, to_fix(rz));
+    }
     T.kx.add(a.fx);
     T.ky.add(a.fy);
     T.kz.add(a.fz);
@@ -193,30 +307,46 @@ __device__ __forceinline__ void run_block(const float4* qh, const float4* ql, in
         T.kw.add(a.w);
         T.nn += (int)a.nn;
         T.nc += (int)a.nc;
-        T.blocks += 1;
     }
+    T.cand += n * kTile;
 }
 
-// Process the first min(cnt, 32) entries of queue q, shift the rest down.
+template <int kClass, bool kLo, bool kWrap, bool kEnergy>
+__device__ __forceinline__ void n3_any(const WarpQueues& Q, int n, int lane, bool tv, const float4& hi,
+                                       const float4& lo, const PairConsts& C, Totals& T, long long* facc, int N) {
+    if (n == kTile) n3_block<kClass, kLo, kWrap, kEnergy, true>(Q, n, lane, tv, hi, lo, C, T, facc, N);
+    else n3_block<kClass, kLo, kWrap, kEnergy, false>(Q, n, lane, tv, hi, lo, C, T, facc, N);
+}
+
+// Evaluate the first min(cnt, 32) entries of queue q, shift the rest down.
 template <bool kWrap, bool kEnergy>
-__device__ __forceinline__ void drain(WarpQueues& Q, int q, int cls, int& cnt, int lane, const float4& hi,
-                                      const float4& lo, const PairConsts& C, Totals& T) {
+__device__ __forceinline__ void drain(WarpQueues& Q, int q, int cls, int& cnt, int lane, bool tv, const float4& hi,
+                                      const float4& lo, const PairConsts& C, Totals& T, long long* facc, int N) {
     __syncwarp();
     const int n = min(cnt, kTile);
-    switch (cls) {
-        case kPPNuc: run_block<kPPNuc, true, kWrap, kEnergy>(Q.h[q], Q.l[q], n, hi, lo, C, T); break;
-        case kPPCoul: run_block<kPPCoul, false, kWrap, kEnergy>(Q.h[q], Q.l[q], n, hi, lo, C, T); break;
-        case kNucCross: run_block<kNucCross, true, kWrap, kEnergy>(Q.h[q], Q.l[q], n, hi, lo, C, T); break;
-        default: run_block<kNucSame, true, kWrap, kEnergy>(Q.h[q], Q.l[q], n, hi, lo, C, T); break;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 h = lane < n ? Q.h[q][lane] : zero;
+    Q.dh[lane] = h;
+    Q.dh[kTile + lane] = h;
+    if (q != 1) {
+        const float4 l = lane < n ? Q.l[q >> 1][lane] : zero;
+        Q.dl[lane] = l;
+        Q.dl[kTile + lane] = l;
     }
     __syncwarp();
     const int rest = cnt - n;
     if (lane < rest) {
         Q.h[q][lane] = Q.h[q][kTile + lane];
-        Q.l[q][lane] = Q.l[q][kTile + lane];
+        if (q != 1) Q.l[q >> 1][lane] = Q.l[q >> 1][kTile + lane];
     }
     cnt = rest;
     __syncwarp();
+    switch (cls) {
+        case kPPNuc: n3_any<kPPNuc, true, kWrap, kEnergy>(Q, n, lane, tv, hi, lo, C, T, facc, N); break;
+        case kPPCoul: n3_any<kPPCoul, false, kWrap, kEnergy>(Q, n, lane, tv, hi, lo, C, T, facc, N); break;
+        case kNucCross: n3_any<kNucCross, true, kWrap, kEnergy>(Q, n, lane, tv, hi, lo, C, T, facc, N); break;
+        default: n3_any<kNucSame, true, kWrap, kEnergy>(Q, n, lane, tv, hi, lo, C, T, facc, N); break;
+    }
 }
 
 __device__ __forceinline__ void push(WarpQueues& Q, int q, bool pred, int& cnt, int lane, const float4& h,
@@ -225,16 +355,18 @@ __device__ __forceinline__ void push(WarpQueues& Q, int q, bool pred, int& cnt, 
     if (pred) {
         const int pos = cnt + __popc(m & ((1u << lane) - 1u));
         Q.h[q][pos] = h;
-        Q.l[q][pos] = l;
+        if (q != 1) Q.l[q >> 1][pos] = l;
     }
     cnt += __popc(m);
 }
 
 template <bool kWrap, bool kEnergy>
-__device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt, WarpQueues& Q) {
+__device__ __forceinline__ void force_tile(const SysConst& S, int I, WarpQueues& Q) {
     const int lane = threadIdx.x & 31;
     SysState* st = S.st;
     const double L = st->L;
+    const int N = S.N;
+    long long* facc = S.facc;
 
     PairConsts C;
     C.rn2 = (float)(S.r_nuc * S.r_nuc);
@@ -258,8 +390,21 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
     const float Rn = (float)S.r_nuc + half, Rc = (float)(S.coulomb == 1 ? S.r_C : 0.0) + half;
     const float Rn2 = Rn * Rn, Rc2 = Rc * Rc;
 
-    const float4 hi = S.xhi[I * kTile + lane];
-    const float4 lo = S.xlo[I * kTile + lane];
+    const int p = tile_slot0(S, I) + lane;
+    const int nv = tile_end(S, I) - tile_slot0(S, I);
+    const bool valid = lane < nv;
+    // Empty lanes of a ragged tile sit on lane 0's particle (a finite,
+    // in-box position, never on a source) and their pairs are masked off, so
+    // they add no reaction to real sources.
+    float4 hi = S.xhi[I * kTile + lane];
+    float4 lo = S.xlo[I * kTile + lane];
+    {
+        const float4 h0 = shfl_f4(hi, 0), l0 = shfl_f4(lo, 0);
+        if (!valid) {
+            hi = h0;
+            lo = l0;
+        }
+    }
     const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
     const float hIx = S.thalf[3 * I], hIy = S.thalf[3 * I + 1], hIz = S.thalf[3 * I + 2];
     const bool Ip = I < S.Tp;
@@ -285,6 +430,30 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
         if (e0 + d < e1) stage(e0 + d);
         cp_async_commit();
     }
+
+    // The tile with itself (the lists leave it out): every ordered pair is
+    // evaluated by its target lane, so no reaction is added and the energies
+    // count each pair twice.
+    {
+        Q.dh[lane] = hi;
+        Q.dl[lane] = lo;
+        __syncwarp();
+        Acc a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (cls0 == kPPNuc) pair_block<kPPNuc, true, kWrap, kEnergy>(Q.dh, Q.dl, nv, hi, lo, C, a);
+        else pair_block<kNucSame, true, kWrap, kEnergy>(Q.dh, Q.dl, nv, hi, lo, C, a);
+        T.kx.add(a.fx);
+        T.ky.add(a.fy);
+        T.kz.add(a.fz);
+        if (kEnergy) {
+            T.ken.add(0.5f * a.en);
+            T.kec.add(0.5f * a.ec);
+            T.kw.add(0.5f * a.w);
+            T.nn2 += (int)a.nn;
+            T.nc2 += (int)a.nc;
+        }
+        T.cand += nv * (nv - 1) / 2;
+    }
+
     for (int e = e0; e < e1; ++e) {
         if (e + kStages - 1 < e1) stage(e + kStages - 1);
         cp_async_commit();
@@ -300,7 +469,7 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
         const bool farc = Ip && Jp && S.coulomb == 1 && !nucflag;   // Coulomb-only entry
         float4 l = farc ? make_float4(0.f, 0.f, 0.f, 0.f) : Q.sl[slot][lane];
         __syncwarp();
-        const bool valid = h.x != kPad;
+        const bool src_ok = h.x != kPad;
         if (shk != (1 | (1 << 2) | (1 << 4))) {
             const float fx = (float)((shk & 3) - 1), fy = (float)(((shk >> 2) & 3) - 1),
                         fz = (float)(((shk >> 4) & 3) - 1);
@@ -324,59 +493,58 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, int out_alt
         const float gz = fmaxf(fabsf(uz) - hIz, 0.0f);
         const float d2 = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
         if (Ip && Jp && S.coulomb == 1) {
-            const bool nuc = valid && !farc && d2 < Rn2;
+            const bool nuc = src_ok && !farc && d2 < Rn2;
             push(Q, 0, nuc, c0, lane, h, l);
-            push(Q, 1, valid && !nuc && d2 < Rc2, c1, lane, h, l);
-            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, kPPNuc, c0, lane, hi, lo, C, T);
-            if (c1 >= kTile) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, hi, lo, C, T);
+            push(Q, 1, src_ok && !nuc && d2 < Rc2, c1, lane, h, l);
+            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, kPPNuc, c0, lane, valid, hi, lo, C, T, facc, N);
+            if (c1 >= kTile) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, valid, hi, lo, C, T, facc, N);
         } else if (Ip != Jp) {
-            push(Q, 2, valid && d2 < Rn2, c2, lane, h, l);
-            if (c2 >= kTile) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, hi, lo, C, T);
+            push(Q, 2, src_ok && d2 < Rn2, c2, lane, h, l);
+            if (c2 >= kTile) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, valid, hi, lo, C, T, facc, N);
         } else {
-            push(Q, 0, valid && d2 < Rn2, c0, lane, h, l);
-            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, hi, lo, C, T);
+            push(Q, 0, src_ok && d2 < Rn2, c0, lane, h, l);
+            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, valid, hi, lo, C, T, facc, N);
         }
     }
     cp_async_wait<0>();
     // flush the partial queues (< 32 entries each)
-    if (c0 > 0) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, hi, lo, C, T);
-    if (c1 > 0) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, hi, lo, C, T);
-    if (c2 > 0) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, hi, lo, C, T);
+    if (c0 > 0) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, valid, hi, lo, C, T, facc, N);
+    if (c1 > 0) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, valid, hi, lo, C, T, facc, N);
+    if (c2 > 0) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, valid, hi, lo, C, T, facc, N);
 
-    const int p = tile_slot0(S, I) + lane;
-    const bool valid = p < tile_end(S, I);
-    const int N = S.N;
-    float* F = S.f32[out_alt ? (st->cur ^ 1) : st->cur];
     const float fx = T.kx.s - T.kx.c, fy = T.ky.s - T.ky.c, fz = T.kz.s - T.kz.c;
+    bool bad = T.bad;
     if (valid) {
-        F[p] = fx;
-        F[N + p] = fy;
-        F[2 * N + p] = fz;
-        if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&st->error, 1);
+        bad |= !(fabsf(fx) < kForceMax && fabsf(fy) < kForceMax && fabsf(fz) < kForceMax);
+        red_add(facc + p, to_fix(fx));
+        red_add(facc + N + p, to_fix(fy));
+        red_add(facc + 2 * N + p, to_fix(fz));
     }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&st->error, 1);
     if (kEnergy) {
         double en = valid ? ((double)T.ken.s - (double)T.ken.c) : 0.0;
         double ec = valid ? ((double)T.kec.s - (double)T.kec.c) : 0.0;
         double wv = valid ? ((double)T.kw.s - (double)T.kw.c) : 0.0;
-        double cn = valid ? (double)T.nn : 0.0, cc = valid ? (double)T.nc : 0.0;
+        double cn = valid ? (double)T.nn + 0.5 * (double)T.nn2 : 0.0;
+        double cc = valid ? (double)T.nc + 0.5 * (double)T.nc2 : 0.0;
         en = warp_sum(en);
         ec = warp_sum(ec);
         wv = warp_sum(wv);
         cn = warp_sum(cn);
         cc = warp_sum(cc);
         if (lane == 0) {
-            S.tile_e[8 * I] = 0.5 * en;
-            S.tile_e[8 * I + 1] = 0.5 * ec;
-            S.tile_e[8 * I + 2] = 0.5 * wv;
+            S.tile_e[8 * I] = en;
+            S.tile_e[8 * I + 1] = ec;
+            S.tile_e[8 * I + 2] = wv;
             S.tile_e[8 * I + 3] = cn;
             S.tile_e[8 * I + 4] = cc;
-            S.tile_e[8 * I + 5] = (double)T.blocks * (kTile * kTile);
+            S.tile_e[8 * I + 5] = (double)T.cand;
         }
     }
 }
 
 template <bool kEnergy>
-__global__ void __launch_bounds__(kForceWarps * 32) k_force_split(EngineDev E, int only, int out_alt) {
+__global__ void __launch_bounds__(kForceWarps * 32) k_force_split(EngineDev E, int only) {
     __shared__ WarpQueues qs[kForceWarps];
     const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
     if (g >= E.ntiles) return;
@@ -386,8 +554,31 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_split(EngineDev E, i
     const int I = g - S.tile_base;
     if (I >= S.T) return;
     WarpQueues& Q = qs[threadIdx.x >> 5];
-    if (S.st->need_wrap) force_tile<true, kEnergy>(S, I, out_alt, Q);
-    else force_tile<false, kEnergy>(S, I, out_alt, Q);
+    if (S.st->need_wrap) force_tile<true, kEnergy>(S, I, Q);
+    else force_tile<false, kEnergy>(S, I, Q);
+}
+
+// Fixed-point accumulators -> FP32 forces (rounded once), and back to zero
+// for the next pass.  One warp per tile, one lane per particle.
+__global__ void __launch_bounds__(kForceWarps * 32) k_force_fix(EngineDev E, int only, int out_alt) {
+    const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
+    if (g >= E.ntiles) return;
+    const int s = E.tile_sys[g];
+    if (s < 0 || (only >= 0 && s != only)) return;
+    const SysConst& S = E.sys[s];
+    const int I = g - S.tile_base;
+    if (I >= S.T) return;
+    const int p = tile_slot0(S, I) + (threadIdx.x & 31);
+    if (p >= tile_end(S, I)) return;
+    const SysState* st = S.st;
+    float* F = S.f32[out_alt ? (st->cur ^ 1) : st->cur];
+    const int N = S.N;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long v = S.facc[c * N + p];
+        S.facc[c * N + p] = 0;
+        F[c * N + p] = (float)((double)v * kUnfix);
+    }
 }
 
 // ---------------------------------------------------------------- FP64
@@ -475,9 +666,9 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fp64(EngineDev E, in
             S.tile_e[8 * I] = 0.5 * en;
             S.tile_e[8 * I + 1] = 0.5 * ec;
             S.tile_e[8 * I + 2] = 0.5 * wv;
-            S.tile_e[8 * I + 3] = cn;
-            S.tile_e[8 * I + 4] = cc;
-            S.tile_e[8 * I + 5] = (double)(e1 - e0) * (kTile * kTile);
+            S.tile_e[8 * I + 3] = 0.5 * cn;     // unique pairs
+            S.tile_e[8 * I + 4] = 0.5 * cc;
+            S.tile_e[8 * I + 5] = 0.5 * (double)(e1 - e0) * (kTile * kTile);
         }
     }
 }
@@ -491,11 +682,14 @@ void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, in
     if (H.precision == 1) {
         if (energy) k_force_fp64<true><<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
         else k_force_fp64<false><<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
+        H.count(1);
     } else {
-        if (energy) k_force_split<true><<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
-        else k_force_split<false><<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
+        if (energy) k_force_split<true><<<nb, kForceWarps * 32, 0, s>>>(E, only);
+        else k_force_split<false><<<nb, kForceWarps * 32, 0, s>>>(E, only);
+        H.rec("force_fix", s);
+        k_force_fix<<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
+        H.count(2);
     }
-    H.count(1);
     launch_coulomb_pp(H, s, energy, only, out_alt);
 }
 

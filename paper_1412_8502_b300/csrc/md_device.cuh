@@ -96,6 +96,7 @@ struct SysConst {
     int* lstart;             // [T+1]
     int* list;               // [list_cap] tile-pair entries: J | kNucBit
     double* tile_e;          // [T*8] per-tile PE_nuc, PE_coul, virial, pair counts
+    long long* facc;         // [3N] split precision: forces in 2^-32 MeV/fm fixed point
     double* blk;             // [T/8 * 4] per-block KE partials
     ClusterBufs* cl;         // cluster-analysis buffers (device struct)
     SysState* st;
@@ -162,10 +163,12 @@ __device__ inline float warp_max(float v) {
 }
 
 // Store slot (t, lane)'s position as hi + lo FP32 pair of its image nearest
-// the tile origin (empty slots: far away, zero low part).
+// the tile origin (empty slots: far away, zero low part).  h.w carries the
+// particle's slot index (bit pattern of an int; -1 for an empty slot).
 __device__ inline void write_xt(const SysConst& s, int t, int lane, const double* xs, double L, bool valid) {
     float4 h, l;
-    h.w = l.w = 0.0f;
+    h.w = __int_as_float(valid ? tile_slot0(s, t) + lane : -1);
+    l.w = 0.0f;
     if (valid) {
         const double hL = 0.5 * L;
         double xt[3];
