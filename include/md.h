@@ -93,9 +93,10 @@ typedef struct {
     double L;        /* box side the energies were evaluated with */
     double t;        /* simulated time, fm/c */
     int64_t step;    /* steps taken since md_create */
-    int64_t pairs_nuc;   /* ordered pairs inside r_nuc in that force pass */
-    int64_t pairs_coul;  /* ordered proton pairs inside r_C in that pass */
-    int64_t candidates;  /* pairs evaluated in that pass (md_step_energy only) */
+    int64_t pairs_nuc;   /* pairs i<j inside r_nuc in that force pass */
+    int64_t pairs_coul;  /* proton pairs i<j inside r_C in that pass */
+    int64_t candidates;  /* pairs i<j evaluated in that pass, in range or not
+                            (md_step_energy only) */
 } md_energy_t;
 
 /* State exchange (md_get_state / md_set_state).  The caller owns x, v
