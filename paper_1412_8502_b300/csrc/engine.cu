@@ -7,6 +7,29 @@
 
 namespace pasta {
 
+// FP32 pair constants of Eq. (1) for the split-precision force pass.
+static PairF pair_consts(const SysConst& c) {
+    const double ln2 = 0.69314718055994530942;
+    PairF f;
+    f.rn2 = (float)(c.r_nuc * c.r_nuc);
+    f.rc2 = c.coulomb == 1 ? (float)(c.r_C * c.r_C) : 0.0f;
+    f.kq = (float)(-1.0 / (2.0 * c.Lambda * ln2));
+    f.A2 = (float)(2.0 * c.a / c.Lambda);
+    f.a = (float)c.a;
+    f.Ssame = (float)((c.b + c.c) / c.Lambda);
+    f.Scross = (float)((c.b - c.c) / c.Lambda);
+    f.bsame = (float)(c.b + c.c);
+    f.bcross = (float)(c.b - c.c);
+    f.kc = (float)(-1.0 / (c.lambda_s * ln2));
+    f.l2a = (float)std::log2(c.alpha);
+    f.il = (float)(1.0 / c.lambda_s);
+    const float half = 0.5f * (float)c.skin + 2e-3f;
+    const float Rn = (float)c.r_nuc + half, Rc = (float)(c.coulomb == 1 ? c.r_C : 0.0) + half;
+    f.Rn2 = Rn * Rn;
+    f.Rc2 = Rc * Rc;
+    return f;
+}
+
 namespace {
 thread_local std::string g_err;
 
@@ -265,6 +288,7 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     c.rebuild_every = (int)std::max<int64_t>(1, p.rebuild_every);
     c.coulomb = p.coulomb;
     c.energy_every = (int)p.energy_every;
+    c.pf = pair_consts(c);
 
     SysState st{};
     st.L = st.L_base = st.L_F = st.L_build = L0;
@@ -714,6 +738,7 @@ int Engine::set_params(int idx, const md_params& p) {
     const bool pp_changed = (c.coulomb == 2) != (p.coulomb == 2);
     c.coulomb = p.coulomb;
     c.energy_every = (int)p.energy_every;
+    c.pf = pair_consts(c);
     if (pp_changed) {
         cudaStreamSynchronize(stream_);
         drop_graphs();

@@ -164,10 +164,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 constexpr int kForceWarps = 4;   // warps (target tiles) per block
+#ifndef PASTA_FORCE_MIN_BLOCKS
+#define PASTA_FORCE_MIN_BLOCKS 5     // resident blocks per SM asked of the register allocator
+#endif
 constexpr int kQ = 2 * kTile;    // queue capacity
 constexpr int kStages = 4;       // source tiles in flight per warp (cp.async)
-constexpr float kFix = 4294967296.0f;        // 2^32: force accumulators count 2^-32 MeV/fm
-constexpr double kUnfix = 1.0 / 4294967296.0;
+constexpr double kUnfix = 1.0 / 4294967296.0;  // force accumulators count 2^-32 MeV/fm
 constexpr float kForceMax = 1.0e9f;          // |partial force| beyond this (MeV/fm) is an error
 
 struct WarpQueues {
@@ -196,7 +198,23 @@ struct Totals {
     bool bad = false;            // a reaction partial was not finite or out of range
 };
 
-__device__ __forceinline__ long long to_fix(float f) { return __float2ll_rn(f * kFix); }
+// f in units of 2^-32 MeV/fm, rounded to nearest (|f| < 2^31; larger values
+// are flagged as errors by the callers).
+__device__ __forceinline__ long long to_fix(float f) { return __float2ll_rn(f * 4294967296.0f); }
+
+// Warp total of one FP32 value per lane, compensated (two-sum tree), as FP64.
+__device__ __forceinline__ double warp_sum_f(float v) {
+    float s = v, c = 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, o), co = __shfl_xor_sync(0xffffffffu, c, o);
+        float t, e;
+        two_sum(s, so, t, e);
+        s = t;
+        c = c + co + e;
+    }
+    return (double)s + (double)c;
+}
 
 __device__ __forceinline__ float4 shfl_f4(const float4& v, int src) {
     return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
@@ -369,26 +387,25 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, WarpQueues&
     long long* facc = S.facc;
 
     PairConsts C;
-    C.rn2 = (float)(S.r_nuc * S.r_nuc);
-    C.rc2 = S.coulomb == 1 ? (float)(S.r_C * S.r_C) : 0.0f;
-    C.kq = (float)(-1.0 / (2.0 * S.Lambda * 0.69314718055994530942));
-    C.A2 = (float)(2.0 * S.a / S.Lambda);
-    C.a = (float)S.a;
-    C.Ssame = (float)((S.b + S.c) / S.Lambda);
-    C.Scross = (float)((S.b - S.c) / S.Lambda);
-    C.bsame = (float)(S.b + S.c);
-    C.bcross = (float)(S.b - S.c);
-    C.kc = (float)(-1.0 / (S.lambda_s * 0.69314718055994530942));
-    C.l2a = (float)log2(S.alpha);
-    C.il = (float)(1.0 / S.lambda_s);
-    const float Lhi = (float)L, Llo = (float)(L - (double)Lhi);
+    C.rn2 = S.pf.rn2;
+    C.rc2 = S.pf.rc2;
+    C.kq = S.pf.kq;
+    C.A2 = S.pf.A2;
+    C.a = S.pf.a;
+    C.Ssame = S.pf.Ssame;
+    C.Scross = S.pf.Scross;
+    C.bsame = S.pf.bsame;
+    C.bcross = S.pf.bcross;
+    C.kc = S.pf.kc;
+    C.l2a = S.pf.l2a;
+    C.il = S.pf.il;
+    // L as an exact FP32 pair; 1/L only picks images (FP32 division)
+    const float Lhi = __double2float_rn(L), Llo = __double2float_rn(L - (double)Lhi);
     C.Lhi = Lhi;
     C.Llo = Llo;
-    C.iLf = (float)(1.0 / L);
+    C.iLf = 1.0f / Lhi;
     // source filter radii around I's box: cutoff + skin/2 (+ FP32 margin)
-    const float half = 0.5f * (float)S.skin + 2e-3f;
-    const float Rn = (float)S.r_nuc + half, Rc = (float)(S.coulomb == 1 ? S.r_C : 0.0) + half;
-    const float Rn2 = Rn * Rn, Rc2 = Rc * Rc;
+    const float Rn2 = S.pf.Rn2, Rc2 = S.pf.Rc2;
 
     const int p = tile_slot0(S, I) + lane;
     const int nv = tile_end(S, I) - tile_slot0(S, I);
@@ -522,29 +539,24 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, WarpQueues&
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&st->error, 1);
     if (kEnergy) {
-        double en = valid ? ((double)T.ken.s - (double)T.ken.c) : 0.0;
-        double ec = valid ? ((double)T.kec.s - (double)T.kec.c) : 0.0;
-        double wv = valid ? ((double)T.kw.s - (double)T.kw.c) : 0.0;
-        double cn = valid ? (double)T.nn + 0.5 * (double)T.nn2 : 0.0;
-        double cc = valid ? (double)T.nc + 0.5 * (double)T.nc2 : 0.0;
-        en = warp_sum(en);
-        ec = warp_sum(ec);
-        wv = warp_sum(wv);
-        cn = warp_sum(cn);
-        cc = warp_sum(cc);
+        const double en = warp_sum_f(valid ? T.ken.s - T.ken.c : 0.0f);
+        const double ec = warp_sum_f(valid ? T.kec.s - T.kec.c : 0.0f);
+        const double wv = warp_sum_f(valid ? T.kw.s - T.kw.c : 0.0f);
+        const int cn = __reduce_add_sync(0xffffffffu, valid ? 2 * T.nn + T.nn2 : 0);   // twice the pairs
+        const int cc = __reduce_add_sync(0xffffffffu, valid ? 2 * T.nc + T.nc2 : 0);
         if (lane == 0) {
             S.tile_e[8 * I] = en;
             S.tile_e[8 * I + 1] = ec;
             S.tile_e[8 * I + 2] = wv;
-            S.tile_e[8 * I + 3] = cn;
-            S.tile_e[8 * I + 4] = cc;
+            S.tile_e[8 * I + 3] = 0.5 * (double)cn;
+            S.tile_e[8 * I + 4] = 0.5 * (double)cc;
             S.tile_e[8 * I + 5] = (double)T.cand;
         }
     }
 }
 
 template <bool kEnergy>
-__global__ void __launch_bounds__(kForceWarps * 32) k_force_split(EngineDev E, int only) {
+__global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS) k_force_split(EngineDev E, int only) {
     __shared__ WarpQueues qs[kForceWarps];
     const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
     if (g >= E.ntiles) return;

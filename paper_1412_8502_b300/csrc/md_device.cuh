@@ -63,6 +63,21 @@ struct SysState {
 };
 
 // Per-system constants and device pointers.
+// FP32 constants of the split-precision pair terms, computed on the host
+// from the FP64 parameters of the system (pair_consts in engine.cu).
+struct PairF {
+    float rn2, rc2;          // squared cutoffs (rc2 = 0 unless coulomb == 1)
+    float kq;                // -1/(2 Lambda ln 2): g = 2^(r2 kq)
+    float A2;                // 2a/Lambda
+    float a;                 // a
+    float Ssame, Scross;     // (b+c)/Lambda, (b-c)/Lambda
+    float bsame, bcross;     // b+c, b-c
+    float kc;                // -1/(lambda ln 2)
+    float l2a;               // log2(alpha)
+    float il;                // 1/lambda
+    float Rn2, Rc2;          // source filter radii^2: cutoff + skin/2 + 2e-3 fm
+};
+
 struct SysConst {
     int N, Np, T, Tp;        // particles, protons, tiles, proton tiles
     int tile_base;           // first global tile (multiple of kTilesPerBlock)
@@ -76,6 +91,7 @@ struct SysConst {
     double r_pp, r_np, relax_gamma, relax_dmax;
     int thermostat_every, rebuild_every, coulomb, energy_every;
     int affine;              // scale positions with the box (option, not the paper)
+    PairF pf;
     // state arrays (index [cur] is current)
     double* x[2];
     double* v[2];
