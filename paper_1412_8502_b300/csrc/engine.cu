@@ -113,12 +113,13 @@ Engine::~Engine() {
 }
 
 void Engine::free_tables() {
-    void* ptrs[] = {d_sys_, d_tile_sys_, d_hist_, d_binstart_, d_cursor_, d_blocksum_, d_any_, d_out_, d_clock_,
-                    d_seeds_};
+    void* ptrs[] = {d_sys_, d_tile_sys_, d_item_sys_, d_hist_, d_binstart_, d_cursor_, d_blocksum_, d_any_, d_out_,
+                    d_clock_, d_seeds_};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d_sys_ = nullptr;
     d_tile_sys_ = nullptr;
+    d_item_sys_ = nullptr;
     d_hist_ = d_binstart_ = d_cursor_ = d_blocksum_ = nullptr;
     d_any_ = nullptr;
     d_out_ = d_clock_ = nullptr;
@@ -250,9 +251,9 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     A(&c.sorg, (size_t)(s.T + kTile - 1) / kTile);
     A(&c.shalf, (size_t)(s.T + kTile - 1) / kTile);
     A(&c.lcount, (size_t)s.T);
-    A(&c.lstart, (size_t)s.T + 1);
+    A(&c.lnear, (size_t)s.T);
     A(&c.list, (size_t)c.list_cap);
-    A(&c.tile_e, 8 * (size_t)s.T);
+    A(&c.tile_e, 8 * (size_t)sys_items(s.T, s.Tp));
     A(&c.facc, 3 * (size_t)N);
     A(&c.blk, 4 * (size_t)(s.Tpad / kTilesPerBlock));
     A(&s.d_st, 1);
@@ -320,19 +321,25 @@ int Engine::build_tables() {
     drop_graphs();
     free_tables();
     const int n = (int)sys.size();
-    int tiles = 0;
+    int tiles = 0, items = 0;
     long long bins = 0;
     for (SysHost* h : sys) {
         h->c.tile_base = tiles;
         h->c.bin_base = bins;
+        h->c.item_base = items;
+        h->c.n_items = sys_items(h->c.T, h->c.Tp);
         tiles += h->Tpad;
+        items += (h->c.n_items + 3) / 4 * 4;
         bins += 2 * h->nbins;
     }
     if (tiles == 0) tiles = kTilesPerBlock;
+    if (items == 0) items = 4;
     if (bins == 0) bins = 1;
-    std::vector<int> ts(tiles, -1);
-    for (int s = 0; s < n; ++s)
+    std::vector<int> ts(tiles, -1), is(items, -1);
+    for (int s = 0; s < n; ++s) {
         for (int t = 0; t < sys[s]->Tpad; ++t) ts[sys[s]->c.tile_base + t] = s;
+        for (int v = 0; v < (sys[s]->c.n_items + 3) / 4 * 4; ++v) is[sys[s]->c.item_base + v] = s;
+    }
     const int nscan = (int)((bins + 8191) / 8192);
     auto A = [&](auto** p, size_t bytes) -> int {
         cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(bytes, 16));
@@ -347,6 +354,7 @@ int Engine::build_tables() {
     int rc = MD_OK;
     if ((rc = A(&d_sys_, sizeof(SysConst) * std::max(n, 1)))) return rc;
     if ((rc = A(&d_tile_sys_, sizeof(int) * tiles))) return rc;
+    if ((rc = A(&d_item_sys_, sizeof(int) * items))) return rc;
     if ((rc = A(&d_hist_, sizeof(unsigned) * bins))) return rc;
     if ((rc = A(&d_binstart_, sizeof(unsigned) * bins))) return rc;
     if ((rc = A(&d_cursor_, sizeof(unsigned) * bins))) return rc;
@@ -359,9 +367,12 @@ int Engine::build_tables() {
     for (int s = 0; s < n; ++s) hs[s] = sys[s]->c;
     if (n) CK(cudaMemcpy(d_sys_, hs.data(), sizeof(SysConst) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_tile_sys_, ts.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_item_sys_, is.data(), sizeof(int) * items, cudaMemcpyHostToDevice));
     EngineDev& E = H_.dev;
     E.sys = d_sys_;
     E.tile_sys = d_tile_sys_;
+    E.item_sys = d_item_sys_;
+    E.nitems = items;
     E.nsys = n;
     E.ntiles = tiles;
     E.nbins_total = bins;
@@ -494,7 +505,8 @@ size_t Engine::estimate_bytes(int64_t N, double Yp, const md_params& p) {
     size_t b = 0;
     b += 2 * (size_t)N * (8 * 3 + 8 * 3 + 4 + 4 * 3 + 8 * 3);   // x, v, id, f32, f64
     b += (size_t)N * (4 * 3 + 4 + 4 + 9 * 8 + 1 + 4 + 8 * 3);   // disp, key, slot, staging, facc
-    b += (size_t)T * (32 * 32 + 8 * 3 + 16 + 12 + 4 + 4 + 64) + 4 * 8 * Tpad;
+    b += (size_t)T * (32 * 32 + 8 * 3 + 16 + 12 + 4 + 4) + 64 * (size_t)sys_items((int)T, (int)((Np + kTile - 1) / kTile)) +
+         4 * 8 * Tpad;
     b += (size_t)T * T * 4;                                      // pair list
     b += (size_t)nb * 12 + 4096;                                 // engine bins
     return b;

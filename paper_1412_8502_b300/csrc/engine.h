@@ -103,6 +103,7 @@ private:
     EngineHost H_;
     SysConst* d_sys_ = nullptr;
     int* d_tile_sys_ = nullptr;
+    int* d_item_sys_ = nullptr;
     unsigned* d_hist_ = nullptr;
     unsigned* d_binstart_ = nullptr;
     unsigned* d_cursor_ = nullptr;

@@ -491,7 +491,7 @@ __global__ void k_lbuild(EngineDev E, int half) {
     const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
     const float hI[3] = {S.thalf[3 * I], S.thalf[3 * I + 1], S.thalf[3 * I + 2]};
     int* lst = S.list + (long long)I * S.T;
-    int out = 0;
+    int out = 0, outf = 0;         // near entries from the front, Coulomb-only from the back
     const int nsup = (S.T + kTile - 1) / kTile;
     const float R2max = fmaxf(T.R2same, T.R2cross);
     for (int s0 = 0; s0 < nsup; s0 += 32) {
@@ -516,20 +516,26 @@ __global__ void k_lbuild(EngineDev E, int half) {
             sm &= sm - 1;
             const int J = (s0 + b) * kTile + lane;
             const int e = (J < S.T && owns_pair(I, J, half)) ? list_entry(S, I, J, oI, hI, T) : -1;
-            const unsigned m = __ballot_sync(0xffffffffu, e >= 0);
-            if (e >= 0) lst[out + __popc(m & ((1u << lane) - 1u))] = e;
-            out += __popc(m);
+            const bool near = e >= 0 && (e & kNucBit);
+            const unsigned mn = __ballot_sync(0xffffffffu, near);
+            const unsigned mf = __ballot_sync(0xffffffffu, e >= 0 && !near);
+            const unsigned below = (1u << lane) - 1u;
+            if (near) lst[out + __popc(mn & below)] = e;
+            else if (e >= 0) lst[S.T - 1 - (outf + __popc(mf & below))] = e;
+            out += __popc(mn);
+            outf += __popc(mf);
         }
     }
     if (lane == 0) {
-        S.lcount[I] = out;
-        atomicAdd((unsigned long long*)&st->list_total, (unsigned long long)out);
+        S.lcount[I] = out + outf;
+        S.lnear[I] = out;
+        atomicAdd((unsigned long long*)&st->list_total, (unsigned long long)(out + outf));
     }
 }
 
-// Cluster lists (mode 1): count, scan, write into a buffer sized by the host.
-__global__ void k_lcount(EngineDev E, int mode, int only) {
-    if (mode == 0 && !*E.any_rebuild) return;
+// Cluster lists: count, scan, write into a buffer sized by the host.  Boxes
+// are those of the last rebuild; the cluster ranges add the skin.
+__global__ void k_lcount(EngineDev E, int only) {
     const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= E.ntiles) return;
@@ -537,34 +543,28 @@ __global__ void k_lcount(EngineDev E, int mode, int only) {
     if (s < 0 || (only >= 0 && s != only)) return;
     const SysConst& S = E.sys[s];
     SysState* st = S.st;
-    if (mode == 0 && !sys_rebuilds(S)) return;
     const int I = g - S.tile_base;
-    if (I == 0 && lane == 0 && mode == 0) st->cur = st->cur_next;
     if (I >= S.T) return;
-    const ListTest T = make_test(S, mode, (float)st->L);
+    const ListTest T = make_test(S, 1, (float)st->L);
     const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
     const float hI[3] = {S.thalf[3 * I], S.thalf[3 * I + 1], S.thalf[3 * I + 2]};
     int cnt = 0;
-    const int Jend = T.cluster ? S.Tp : S.T;
-    for (int J0 = 0; J0 < Jend; J0 += 32) {
+    for (int J0 = 0; J0 < S.Tp; J0 += 32) {
         const int J = J0 + lane;
-        const bool hit = J < Jend && list_entry(S, I, J, oI, hI, T) >= 0;
+        const bool hit = J < S.Tp && list_entry(S, I, J, oI, hI, T) >= 0;
         cnt += __popc(__ballot_sync(0xffffffffu, hit));
     }
-    if (lane == 0) (mode ? S.cl->count : S.lcount)[I] = cnt;
+    if (lane == 0) S.cl->count[I] = cnt;
 }
 
 // One block per system: exclusive scan of the tile counts.
-__global__ void k_lscan(EngineDev E, int mode, int only) {
-    if (mode == 0 && !*E.any_rebuild) return;
+__global__ void k_lscan(EngineDev E, int only) {
     const int s = blockIdx.x;
     if (only >= 0 && s != only) return;
     const SysConst& S = E.sys[s];
-    SysState* st = S.st;
-    if (mode == 0 && !sys_rebuilds(S)) return;
     __shared__ unsigned sm[33];
-    const int* cnt = mode ? S.cl->count : S.lcount;
-    int* start = mode ? S.cl->start : S.lstart;
+    const int* cnt = S.cl->count;
+    int* start = S.cl->start;
     const int per = (S.T + blockDim.x - 1) / blockDim.x;
     const int t0 = threadIdx.x * per;
     unsigned sum = 0;
@@ -579,13 +579,11 @@ __global__ void k_lscan(EngineDev E, int mode, int only) {
         }
     if (threadIdx.x == 0) {
         start[S.T] = (int)tot;
-        if (mode) *S.cl->total = tot;
-        else st->list_total = tot;
+        *S.cl->total = tot;
     }
 }
 
-__global__ void k_lwrite(EngineDev E, int mode, int only) {
-    if (mode == 0 && !*E.any_rebuild) return;
+__global__ void k_lwrite(EngineDev E, int only) {
     const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= E.ntiles) return;
@@ -593,27 +591,19 @@ __global__ void k_lwrite(EngineDev E, int mode, int only) {
     if (s < 0 || (only >= 0 && s != only)) return;
     const SysConst& S = E.sys[s];
     SysState* st = S.st;
-    if (mode == 0 && !sys_rebuilds(S)) return;
     const int I = g - S.tile_base;
     if (I >= S.T) return;
-    const ListTest T = make_test(S, mode, (float)st->L);
+    const ListTest T = make_test(S, 1, (float)st->L);
     const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
     const float hI[3] = {S.thalf[3 * I], S.thalf[3 * I + 1], S.thalf[3 * I + 2]};
-    int* lst = mode ? S.cl->list : S.list;
-    int out = (mode ? S.cl->start : S.lstart)[I];
-    const int Jend = T.cluster ? S.Tp : S.T;
-    for (int J0 = 0; J0 < Jend; J0 += 32) {
+    int* lst = S.cl->list;
+    int out = S.cl->start[I];
+    for (int J0 = 0; J0 < S.Tp; J0 += 32) {
         const int J = J0 + lane;
-        const int e = J < Jend ? list_entry(S, I, J, oI, hI, T) : -1;
+        const int e = J < S.Tp ? list_entry(S, I, J, oI, hI, T) : -1;
         const unsigned m = __ballot_sync(0xffffffffu, e >= 0);
         if (e >= 0) lst[out + __popc(m & ((1u << lane) - 1u))] = e;
         out += __popc(m);
-    }
-    // small boxes: tiles are too large for one image per tile pair
-    if (I == 0 && lane == 0 && mode == 0) {
-        const float hm = __uint_as_float(st->hmax);
-        const double rmax = (S.coulomb == 1 ? fmax(S.r_C, S.r_nuc) : S.r_nuc);
-        st->need_wrap = (rmax + S.skin + 2.0 * (double)hm + 1e-3 >= 0.5 * st->L) ? 1 : 0;
     }
 }
 
@@ -648,12 +638,12 @@ void launch_cluster_lists(const EngineHost& H, cudaStream_t s, int phase, int on
     const int nb = (E.ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
     if (phase == 0) {
         H.rec("cl_lcount", s);
-        k_lcount<<<nb, kBlock, 0, s>>>(E, 1, only);
-        k_lscan<<<E.nsys, 1024, 0, s>>>(E, 1, only);
+        k_lcount<<<nb, kBlock, 0, s>>>(E, only);
+        k_lscan<<<E.nsys, 1024, 0, s>>>(E, only);
         H.count(2);
     } else {
         H.rec("cl_lwrite", s);
-        k_lwrite<<<nb, kBlock, 0, s>>>(E, 1, only);
+        k_lwrite<<<nb, kBlock, 0, s>>>(E, only);
         H.count(1);
     }
 }

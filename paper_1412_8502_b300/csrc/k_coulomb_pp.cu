@@ -116,10 +116,11 @@ __global__ void __launch_bounds__(kPW * 32) k_coulomb_pp_split(EngineDev E, int 
         double wv = warp_sum(valid ? (double)kw.s - (double)kw.c : 0.0);
         double cn = warp_sum(valid ? (double)nc : 0.0);
         if (lane == 0) {
-            S.tile_e[8 * I + 1] = 0.5 * en;
-            S.tile_e[8 * I + 2] += 0.5 * wv;
-            S.tile_e[8 * I + 4] = 0.5 * cn;     // unique pairs
-            S.tile_e[8 * I + 5] += 0.5 * (double)S.Np * kTile;
+            double* te = S.tile_e + 8 * item_index(S, I, 0);
+            te[1] = 0.5 * en;
+            te[2] += 0.5 * wv;
+            te[4] = 0.5 * cn;     // unique pairs
+            te[5] += 0.5 * (double)S.Np * kTile;
         }
     }
 }
@@ -190,9 +191,10 @@ __global__ void __launch_bounds__(kPW * 32) k_coulomb_pp_fp64(EngineDev E, int o
         wv = warp_sum(valid ? wv : 0.0);
         const double cn = warp_sum(valid ? (double)nc : 0.0);
         if (lane == 0) {
-            S.tile_e[8 * I + 1] = 0.5 * en;
-            S.tile_e[8 * I + 2] += 0.5 * wv;
-            S.tile_e[8 * I + 4] = 0.5 * cn;
+            double* te = S.tile_e + 8 * item_index(S, I, 0);
+            te[1] = 0.5 * en;
+            te[2] += 0.5 * wv;
+            te[4] = 0.5 * cn;
         }
     }
 }

@@ -163,12 +163,20 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-constexpr int kForceWarps = 4;   // warps (target tiles) per block
+constexpr int kForceWarps = 4;   // warps (work items) per block
+static_assert(kForceWarps == kItemGroup, "a block takes one item of each tile of a group");
 #ifndef PASTA_FORCE_MIN_BLOCKS
-#define PASTA_FORCE_MIN_BLOCKS 5     // resident blocks per SM asked of the register allocator
+#define PASTA_FORCE_MIN_BLOCKS 4     // resident blocks per SM asked of the register allocator
 #endif
 constexpr int kQ = 2 * kTile;    // queue capacity
-constexpr int kStages = 4;       // source tiles in flight per warp (cp.async)
+#ifndef PASTA_FORCE_STAGES
+#define PASTA_FORCE_STAGES 2
+#endif
+#ifndef PASTA_N3_UNROLL
+#define PASTA_N3_UNROLL 2
+#endif
+constexpr int kStages = PASTA_FORCE_STAGES;   // source tiles in flight per warp (cp.async)
+constexpr int kN3Unroll = PASTA_N3_UNROLL;    // unrolled steps of a rotated block
 constexpr double kUnfix = 1.0 / 4294967296.0;  // force accumulators count 2^-32 MeV/fm
 constexpr float kForceMax = 1.0e9f;          // |partial force| beyond this (MeV/fm) is an error
 
@@ -191,11 +199,18 @@ template <int kN>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(kN) : "memory"); }
 
 struct Totals {
-    Kahan kx, ky, kz, ken, kec, kw;
+    Kahan k0x, k0y, k0z;         // this lane's share of the force on target j = lane mod 16
+    Kahan k1x, k1y, k1z;         // ... and on target j + 16
+    Kahan ken, kec, kw;
     int nn = 0, nc = 0;          // unique in-range pairs of the rotated blocks
     int nn2 = 0, nc2 = 0;        // ordered in-range pairs of the tile with itself
     int cand = 0;                // unique candidate pairs
     bool bad = false;            // a reaction partial was not finite or out of range
+};
+
+struct EAcc {
+    float en, ec, w;
+    float nn, nc;                // in-range pairs (energy pass only), exact below 2^24
 };
 
 // f in units of 2^-32 MeV/fm, rounded to nearest (|f| < 2^31; larger values
@@ -216,23 +231,19 @@ __device__ __forceinline__ double warp_sum_f(float v) {
     return (double)s + (double)c;
 }
 
-__device__ __forceinline__ float4 shfl_f4(const float4& v, int src) {
-    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
-                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
-}
-
 __device__ __forceinline__ void red_add(long long* a, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
 }
 
 // One pair of a rotated block: returns the scalar fr with F_target += fr d
-// and F_source -= fr d, where d = x_target - x_source.  kSel: masks by
-// select (partial blocks, whose unused slots hold zeros); otherwise by
-// multiplying with 0/1 (every slot is a real source, never the target).
+// and F_source -= fr d, where d = x_target - x_source; adds fr d to the
+// target sums (fx, fy, fz) and the energies to e.  kSel: masks by select
+// (partial blocks, whose unused slots hold zeros); otherwise by multiplying
+// with 0/1 (every slot is a real source, never the target).
 template <int kClass, bool kLo, bool kWrap, bool kEnergy, bool kSel>
 __device__ __forceinline__ float pair_n3(const float4& q, const float4& u, const float4& hi, const float4& lo,
-                                         const PairConsts& C, float S, float bS, bool ok, Acc& acc,
-                                         float& dx, float& dy, float& dz) {
+                                         const PairConsts& C, float S, float bS, bool ok, float& fx, float& fy,
+                                         float& fz, EAcc& e, float& dx, float& dy, float& dz) {
     dx = hi.x - q.x;
     dy = hi.y - q.y;
     dz = hi.z - q.z;
@@ -258,13 +269,13 @@ __device__ __forceinline__ float pair_n3(const float4& q, const float4& u, const
         const bool in = ok && r2 < C.rc2;
         if (kSel) {
             fr = in ? fc : 0.0f;
-            if (kEnergy) acc.ec += in ? vc : 0.0f;
+            if (kEnergy) e.ec += in ? vc : 0.0f;
         } else {
             const float m = in ? 1.0f : 0.0f;
             fr = fc * m;
-            if (kEnergy) acc.ec = fmaf(vc, m, acc.ec);
+            if (kEnergy) e.ec = fmaf(vc, m, e.ec);
         }
-        if (kEnergy) acc.nc += in ? 1.0f : 0.0f;
+        if (kEnergy) e.nc += in ? 1.0f : 0.0f;
     }
     if (kClass != kPPCoul) {
         const float gq = ex2_approx(r2 * C.kq);
@@ -272,84 +283,107 @@ __device__ __forceinline__ float pair_n3(const float4& q, const float4& u, const
         const float gm = in ? gq : 0.0f;
         fr = fmaf(gm, fmaf(C.A2, gq, S), fr);
         if (kEnergy) {
-            acc.en = fmaf(gm, fmaf(C.a, gq, bS), acc.en);
-            acc.nn += in ? 1.0f : 0.0f;
+            e.en = fmaf(gm, fmaf(C.a, gq, bS), e.en);
+            e.nn += in ? 1.0f : 0.0f;
         }
     }
-    acc.fx = fmaf(fr, dx, acc.fx);
-    acc.fy = fmaf(fr, dy, acc.fy);
-    acc.fz = fmaf(fr, dz, acc.fz);
-    if (kEnergy) acc.w = fmaf(fr, r2, acc.w);
+    fx = fmaf(fr, dx, fx);
+    fy = fmaf(fr, dy, fy);
+    fz = fmaf(fr, dz, fz);
+    if (kEnergy) e.w = fmaf(fr, r2, e.w);
     return fr;
 }
 
-// A block of n <= 32 queued sources (in Q.dh/Q.dl twice over) against the
-// warp's 32 targets, every pair once: at step k lane l pairs its target with
-// source (l + k) mod 32.  The reaction on that source rides in registers
-// that rotate one lane down after every step, so after 32 steps lane l holds
-// the whole reaction on source l and adds it to the fixed-point accumulator.
+// The warp's targets for the rotated blocks: lanes l and l ^ 16 both hold
+// targets j = l mod 16 and j + 16 (empty lanes of a ragged tile sit on a real
+// particle and are masked off by t0ok / t1ok).
+struct Targets {
+    float4 h0, l0, h1, l1;
+    bool ok0, ok1;
+};
+
+// A block of n <= 32 queued sources against the warp's 32 targets, every pair
+// once.  Half-warp h = l >> 4 takes sources 16h .. 16h + 15 (stored in Q.dh /
+// Q.dl as dh[32h + i] = source 16h + i mod 16, so rotated reads need no
+// index arithmetic).  At step k lane l pairs both of its targets with source
+// 16h + (j + k) mod 16 and adds the two reactions to registers that rotate
+// one lane down within the half after every step: after 16 steps lane l holds
+// the whole reaction on source 16h + j.  One source load and one rotation
+// serve two pairs.
 template <int kClass, bool kLo, bool kWrap, bool kEnergy, bool kFull>
-__device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, bool tv, const float4& hi,
-                                         const float4& lo, const PairConsts& C, Totals& T, long long* facc, int N) {
+__device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, const Targets& X,
+                                         const PairConsts& C, Totals& T, long long* facc, int N) {
     const float S = (kClass == kNucCross) ? C.Scross : C.Ssame;
     const float bS = (kClass == kNucCross) ? C.bcross : C.bsame;
-    Acc a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float f0x = 0.f, f0y = 0.f, f0z = 0.f, f1x = 0.f, f1y = 0.f, f1z = 0.f;
+    EAcc e{0.f, 0.f, 0.f, 0.f, 0.f};
     float rx = 0.0f, ry = 0.0f, rz = 0.0f;
-    const float4* ph = Q.dh + lane;
-    const float4* pl = Q.dl + lane;
-    const int from = (lane + 1) & (kTile - 1);
-#pragma unroll 8
-    for (int k = 0; k < kTile; ++k) {
+    const int half = lane & 16, j = lane & 15;
+    const float4* ph = Q.dh + 2 * half + j;
+    const float4* pl = Q.dl + 2 * half + j;
+    const int from = half | ((lane + 1) & 15);
+#pragma unroll kN3Unroll
+    for (int k = 0; k < 16; ++k) {
         const float4 q = ph[k];
         const float4 u = kLo ? pl[k] : q;
-        const bool ok = tv && (kFull || (((lane + k) & (kTile - 1)) < n));
+        const bool sv = kFull || ((half | ((j + k) & 15)) < n);
         float dx, dy, dz;
-        const float fr = pair_n3<kClass, kLo, kWrap, kEnergy, !kFull>(q, u, hi, lo, C, S, bS, ok, a, dx, dy, dz);
-        rx = __shfl_sync(0xffffffffu, fmaf(-fr, dx, rx), from);
-        ry = __shfl_sync(0xffffffffu, fmaf(-fr, dy, ry), from);
-        rz = __shfl_sync(0xffffffffu, fmaf(-fr, dz, rz), from);
+        const float fr0 = pair_n3<kClass, kLo, kWrap, kEnergy, !kFull>(q, u, X.h0, X.l0, C, S, bS, X.ok0 && sv, f0x,
+                                                                         f0y, f0z, e, dx, dy, dz);
+        rx = fmaf(-fr0, dx, rx);
+        ry = fmaf(-fr0, dy, ry);
+        rz = fmaf(-fr0, dz, rz);
+        const float fr1 = pair_n3<kClass, kLo, kWrap, kEnergy, !kFull>(q, u, X.h1, X.l1, C, S, bS, X.ok1 && sv, f1x,
+                                                                         f1y, f1z, e, dx, dy, dz);
+        rx = __shfl_sync(0xffffffffu, fmaf(-fr1, dx, rx), from);
+        ry = __shfl_sync(0xffffffffu, fmaf(-fr1, dy, ry), from);
+        rz = __shfl_sync(0xffffffffu, fmaf(-fr1, dz, rz), from);
     }
-    if (kFull || lane < n) {
+    if (kFull || (half | j) < n) {
         const int slot = __float_as_int(ph[0].w);
         T.bad |= !(fabsf(rx) < kForceMax && fabsf(ry) < kForceMax && fabsf(rz) < kForceMax);
         red_add(facc + slot, to_fix(rx));
         red_add(facc + N + slot, to_fix(ry));
         red_add(facc + 2 * N + slot, to_fix(rz));
     }
-    T.kx.add(a.fx);
-    T.ky.add(a.fy);
-    T.kz.add(a.fz);
+    T.k0x.add(f0x);
+    T.k0y.add(f0y);
+    T.k0z.add(f0z);
+    T.k1x.add(f1x);
+    T.k1y.add(f1y);
+    T.k1z.add(f1z);
     if (kEnergy) {
-        T.ken.add(a.en);
-        T.kec.add(a.ec);
-        T.kw.add(a.w);
-        T.nn += (int)a.nn;
-        T.nc += (int)a.nc;
+        T.ken.add(e.en);
+        T.kec.add(e.ec);
+        T.kw.add(e.w);
+        T.nn += (int)e.nn;
+        T.nc += (int)e.nc;
     }
     T.cand += n * kTile;
 }
 
 template <int kClass, bool kLo, bool kWrap, bool kEnergy>
-__device__ __forceinline__ void n3_any(const WarpQueues& Q, int n, int lane, bool tv, const float4& hi,
-                                       const float4& lo, const PairConsts& C, Totals& T, long long* facc, int N) {
-    if (n == kTile) n3_block<kClass, kLo, kWrap, kEnergy, true>(Q, n, lane, tv, hi, lo, C, T, facc, N);
-    else n3_block<kClass, kLo, kWrap, kEnergy, false>(Q, n, lane, tv, hi, lo, C, T, facc, N);
+__device__ __forceinline__ void n3_any(const WarpQueues& Q, int n, int lane, const Targets& X, const PairConsts& C,
+                                       Totals& T, long long* facc, int N) {
+    if (n == kTile) n3_block<kClass, kLo, kWrap, kEnergy, true>(Q, n, lane, X, C, T, facc, N);
+    else n3_block<kClass, kLo, kWrap, kEnergy, false>(Q, n, lane, X, C, T, facc, N);
 }
 
 // Evaluate the first min(cnt, 32) entries of queue q, shift the rest down.
 template <bool kWrap, bool kEnergy>
-__device__ __forceinline__ void drain(WarpQueues& Q, int q, int cls, int& cnt, int lane, bool tv, const float4& hi,
-                                      const float4& lo, const PairConsts& C, Totals& T, long long* facc, int N) {
+__device__ __forceinline__ void drain(WarpQueues& Q, int q, int cls, int& cnt, int lane, const Targets& X,
+                                      const PairConsts& C, Totals& T, long long* facc, int N) {
     __syncwarp();
     const int n = min(cnt, kTile);
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int half = lane & 16, j = lane & 15;
     const float4 h = lane < n ? Q.h[q][lane] : zero;
-    Q.dh[lane] = h;
-    Q.dh[kTile + lane] = h;
+    Q.dh[2 * half + j] = h;
+    Q.dh[2 * half + 16 + j] = h;
     if (q != 1) {
         const float4 l = lane < n ? Q.l[q >> 1][lane] : zero;
-        Q.dl[lane] = l;
-        Q.dl[kTile + lane] = l;
+        Q.dl[2 * half + j] = l;
+        Q.dl[2 * half + 16 + j] = l;
     }
     __syncwarp();
     const int rest = cnt - n;
@@ -360,10 +394,10 @@ __device__ __forceinline__ void drain(WarpQueues& Q, int q, int cls, int& cnt, i
     cnt = rest;
     __syncwarp();
     switch (cls) {
-        case kPPNuc: n3_any<kPPNuc, true, kWrap, kEnergy>(Q, n, lane, tv, hi, lo, C, T, facc, N); break;
-        case kPPCoul: n3_any<kPPCoul, false, kWrap, kEnergy>(Q, n, lane, tv, hi, lo, C, T, facc, N); break;
-        case kNucCross: n3_any<kNucCross, true, kWrap, kEnergy>(Q, n, lane, tv, hi, lo, C, T, facc, N); break;
-        default: n3_any<kNucSame, true, kWrap, kEnergy>(Q, n, lane, tv, hi, lo, C, T, facc, N); break;
+        case kPPNuc: n3_any<kPPNuc, true, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N); break;
+        case kPPCoul: n3_any<kPPCoul, false, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N); break;
+        case kNucCross: n3_any<kNucCross, true, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N); break;
+        default: n3_any<kNucSame, true, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N); break;
     }
 }
 
@@ -378,9 +412,27 @@ __device__ __forceinline__ void push(WarpQueues& Q, int q, bool pred, int& cnt, 
     cnt += __popc(m);
 }
 
+// Work item v of a system (see item_index): the near entries of a proton
+// tile with the tile itself, a third of its Coulomb-only entries, or the
+// whole list of a neutron tile with the tile itself.
 template <bool kWrap, bool kEnergy>
-__device__ __forceinline__ void force_tile(const SysConst& S, int I, WarpQueues& Q) {
+__device__ __forceinline__ void force_item(const SysConst& S, int v, WarpQueues& Q) {
     const int lane = threadIdx.x & 31;
+    const int Pi = proton_items(S.Tp);
+    int I, c;                      // c: -1 whole list, 0 near part, 1.. Coulomb-only part c
+    if (v < Pi) {
+        const int b = v / kItemGroup;
+        I = (b / kPChunks) * kItemGroup + v % kItemGroup;
+        c = b % kPChunks;
+        if (I >= S.Tp) {           // past the last proton tile of the group
+            if (kEnergy && lane == 0)
+                for (int k = 0; k < 6; ++k) S.tile_e[8 * v + k] = 0.0;
+            return;
+        }
+    } else {
+        I = S.Tp + (v - Pi);
+        c = -1;
+    }
     SysState* st = S.st;
     const double L = st->L;
     const int N = S.N;
@@ -410,24 +462,34 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, WarpQueues&
     const int p = tile_slot0(S, I) + lane;
     const int nv = tile_end(S, I) - tile_slot0(S, I);
     const bool valid = lane < nv;
-    // Empty lanes of a ragged tile sit on lane 0's particle (a finite,
-    // in-box position, never on a source) and their pairs are masked off, so
+    const int j = lane & 15;
+    // Empty lanes of a ragged tile sit on particle 0 of the tile (a finite,
+    // in-box position, never a source) and their pairs are masked off, so
     // they add no reaction to real sources.
-    float4 hi = S.xhi[I * kTile + lane];
-    float4 lo = S.xlo[I * kTile + lane];
+    Targets X;
     {
-        const float4 h0 = shfl_f4(hi, 0), l0 = shfl_f4(lo, 0);
-        if (!valid) {
-            hi = h0;
-            lo = l0;
-        }
+        const float4 a0 = S.xhi[I * kTile], b0 = S.xlo[I * kTile];
+        X.ok0 = j < nv;
+        X.ok1 = j + 16 < nv;
+        X.h0 = X.ok0 ? S.xhi[I * kTile + j] : a0;
+        X.l0 = X.ok0 ? S.xlo[I * kTile + j] : b0;
+        X.h1 = X.ok1 ? S.xhi[I * kTile + j + 16] : a0;
+        X.l1 = X.ok1 ? S.xlo[I * kTile + j + 16] : b0;
     }
     const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
     const float hIx = S.thalf[3 * I], hIy = S.thalf[3 * I + 1], hIz = S.thalf[3 * I + 2];
     const bool Ip = I < S.Tp;
     const int cls0 = (Ip && S.coulomb == 1) ? kPPNuc : kNucSame;
     const int* lst = S.list + (long long)I * S.T;
-    const int e0 = 0, e1 = S.lcount[I];
+    const int nl = S.lcount[I], nn = S.lnear[I];
+    int e0 = 0, e1 = nl;
+    if (c == 0) {
+        e1 = nn;
+    } else if (c > 0) {
+        const int nf = nl - nn;
+        e0 = nn + (int)((long long)nf * (c - 1) / (kPChunks - 1));
+        e1 = nn + (int)((long long)nf * c / (kPChunks - 1));
+    }
 
     Totals T;
     int c0 = 0, c1 = 0, c2 = 0;
@@ -437,7 +499,7 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, WarpQueues&
     // the low parts only when the nuclear term is reachable).
     auto stage = [&](int e) {
         const int slot = (e - e0) % kStages;
-        const int ent = lst[e];
+        const int ent = lst[list_pos(S, e, nn)];
         const int J = ent & kJMask;
         if (lane == 0) Q.sJ[slot] = ent;
         cp_async16(&Q.sh[slot][lane], &S.xhi[J * kTile + lane]);
@@ -448,23 +510,25 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, WarpQueues&
         cp_async_commit();
     }
 
-    // The tile with itself (the lists leave it out): every ordered pair is
-    // evaluated by its target lane, so no reaction is added and the energies
-    // count each pair twice.
-    {
-        Q.dh[lane] = hi;
-        Q.dl[lane] = lo;
+    // The tile with itself (the lists leave it out): lane l takes target l
+    // against every particle of the tile, so no reaction is added and the
+    // energies count each pair twice.
+    float sfx = 0.0f, sfy = 0.0f, sfz = 0.0f;
+    if (c <= 0) {
+        const float4 hs = (lane & 16) ? X.h1 : X.h0, ls = (lane & 16) ? X.l1 : X.l0;
+        Q.dh[lane] = hs;
+        Q.dl[lane] = ls;
         __syncwarp();
         Acc a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (cls0 == kPPNuc) pair_block<kPPNuc, true, kWrap, kEnergy>(Q.dh, Q.dl, nv, hi, lo, C, a);
-        else pair_block<kNucSame, true, kWrap, kEnergy>(Q.dh, Q.dl, nv, hi, lo, C, a);
-        T.kx.add(a.fx);
-        T.ky.add(a.fy);
-        T.kz.add(a.fz);
+        if (cls0 == kPPNuc) pair_block<kPPNuc, true, kWrap, kEnergy>(Q.dh, Q.dl, nv, hs, ls, C, a);
+        else pair_block<kNucSame, true, kWrap, kEnergy>(Q.dh, Q.dl, nv, hs, ls, C, a);
+        sfx = a.fx;
+        sfy = a.fy;
+        sfz = a.fz;
         if (kEnergy) {
-            T.ken.add(0.5f * a.en);
-            T.kec.add(0.5f * a.ec);
-            T.kw.add(0.5f * a.w);
+            T.ken.add(valid ? 0.5f * a.en : 0.0f);
+            T.kec.add(valid ? 0.5f * a.ec : 0.0f);
+            T.kw.add(valid ? 0.5f * a.w : 0.0f);
             T.nn2 += (int)a.nn;
             T.nc2 += (int)a.nc;
         }
@@ -513,23 +577,33 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, WarpQueues&
             const bool nuc = src_ok && !farc && d2 < Rn2;
             push(Q, 0, nuc, c0, lane, h, l);
             push(Q, 1, src_ok && !nuc && d2 < Rc2, c1, lane, h, l);
-            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, kPPNuc, c0, lane, valid, hi, lo, C, T, facc, N);
-            if (c1 >= kTile) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, valid, hi, lo, C, T, facc, N);
+            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, kPPNuc, c0, lane, X, C, T, facc, N);
+            if (c1 >= kTile) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, X, C, T, facc, N);
         } else if (Ip != Jp) {
             push(Q, 2, src_ok && d2 < Rn2, c2, lane, h, l);
-            if (c2 >= kTile) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, valid, hi, lo, C, T, facc, N);
+            if (c2 >= kTile) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, X, C, T, facc, N);
         } else {
             push(Q, 0, src_ok && d2 < Rn2, c0, lane, h, l);
-            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, valid, hi, lo, C, T, facc, N);
+            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, X, C, T, facc, N);
         }
     }
     cp_async_wait<0>();
     // flush the partial queues (< 32 entries each)
-    if (c0 > 0) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, valid, hi, lo, C, T, facc, N);
-    if (c1 > 0) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, valid, hi, lo, C, T, facc, N);
-    if (c2 > 0) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, valid, hi, lo, C, T, facc, N);
+    if (c0 > 0) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, X, C, T, facc, N);
+    if (c1 > 0) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, X, C, T, facc, N);
+    if (c2 > 0) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, X, C, T, facc, N);
 
-    const float fx = T.kx.s - T.kx.c, fy = T.ky.s - T.ky.c, fz = T.kz.s - T.kz.c;
+    // Target l = j + 16 (l >> 4): this lane's share plus its partner's
+    // (lane l ^ 16 holds the same two targets), plus the tile's own pairs.
+    const bool upper = (lane & 16) != 0;
+    const float m0x = T.k0x.s - T.k0x.c, m0y = T.k0y.s - T.k0y.c, m0z = T.k0z.s - T.k0z.c;
+    const float m1x = T.k1x.s - T.k1x.c, m1y = T.k1y.s - T.k1y.c, m1z = T.k1z.s - T.k1z.c;
+    const float ox = __shfl_xor_sync(0xffffffffu, upper ? m0x : m1x, 16);
+    const float oy = __shfl_xor_sync(0xffffffffu, upper ? m0y : m1y, 16);
+    const float oz = __shfl_xor_sync(0xffffffffu, upper ? m0z : m1z, 16);
+    const float fx = ((upper ? m1x : m0x) + ox) + sfx;
+    const float fy = ((upper ? m1y : m0y) + oy) + sfy;
+    const float fz = ((upper ? m1z : m0z) + oz) + sfz;
     bool bad = T.bad;
     if (valid) {
         bad |= !(fabsf(fx) < kForceMax && fabsf(fy) < kForceMax && fabsf(fz) < kForceMax);
@@ -539,18 +613,22 @@ __device__ __forceinline__ void force_tile(const SysConst& S, int I, WarpQueues&
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&st->error, 1);
     if (kEnergy) {
-        const double en = warp_sum_f(valid ? T.ken.s - T.ken.c : 0.0f);
-        const double ec = warp_sum_f(valid ? T.kec.s - T.kec.c : 0.0f);
-        const double wv = warp_sum_f(valid ? T.kw.s - T.kw.c : 0.0f);
-        const int cn = __reduce_add_sync(0xffffffffu, valid ? 2 * T.nn + T.nn2 : 0);   // twice the pairs
-        const int cc = __reduce_add_sync(0xffffffffu, valid ? 2 * T.nc + T.nc2 : 0);
+        // energies and counts of the rotated blocks were summed over every
+        // lane's pairs, empty targets masked; those of the tile's own pairs
+        // only over valid lanes
+        const double en = warp_sum_f(T.ken.s - T.ken.c);
+        const double ec = warp_sum_f(T.kec.s - T.kec.c);
+        const double wv = warp_sum_f(T.kw.s - T.kw.c);
+        const int cn = __reduce_add_sync(0xffffffffu, 2 * T.nn + (valid ? T.nn2 : 0));   // twice the pairs
+        const int cc = __reduce_add_sync(0xffffffffu, 2 * T.nc + (valid ? T.nc2 : 0));
         if (lane == 0) {
-            S.tile_e[8 * I] = en;
-            S.tile_e[8 * I + 1] = ec;
-            S.tile_e[8 * I + 2] = wv;
-            S.tile_e[8 * I + 3] = 0.5 * (double)cn;
-            S.tile_e[8 * I + 4] = 0.5 * (double)cc;
-            S.tile_e[8 * I + 5] = (double)T.cand;
+            double* te = S.tile_e + 8 * v;
+            te[0] = en;
+            te[1] = ec;
+            te[2] = wv;
+            te[3] = 0.5 * (double)cn;
+            te[4] = 0.5 * (double)cc;
+            te[5] = (double)T.cand;
         }
     }
 }
@@ -559,15 +637,15 @@ template <bool kEnergy>
 __global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS) k_force_split(EngineDev E, int only) {
     __shared__ WarpQueues qs[kForceWarps];
     const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
-    if (g >= E.ntiles) return;
-    const int s = E.tile_sys[g];
+    if (g >= E.nitems) return;
+    const int s = E.item_sys[g];
     if (s < 0 || (only >= 0 && s != only)) return;
     const SysConst& S = E.sys[s];
-    const int I = g - S.tile_base;
-    if (I >= S.T) return;
+    const int v = g - S.item_base;
+    if (v >= S.n_items) return;
     WarpQueues& Q = qs[threadIdx.x >> 5];
-    if (S.st->need_wrap) force_tile<true, kEnergy>(S, I, Q);
-    else force_tile<false, kEnergy>(S, I, Q);
+    if (S.st->need_wrap) force_item<true, kEnergy>(S, v, Q);
+    else force_item<false, kEnergy>(S, v, Q);
 }
 
 // Fixed-point accumulators -> FP32 forces (rounded once), and back to zero
@@ -619,9 +697,9 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fp64(EngineDev E, in
     double fx = 0, fy = 0, fz = 0, en = 0, ec = 0, wv = 0;
     int nn = 0, nc = 0;
     const int* lst = S.list + (long long)I * S.T;
-    const int e0 = 0, e1 = S.lcount[I];
+    const int e0 = 0, e1 = S.lcount[I], nnear = S.lnear[I];
     for (int e = e0; e < e1; ++e) {
-        const int J = lst[e] & kJMask;
+        const int J = lst[list_pos(S, e, nnear)] & kJMask;
         const int q = tile_slot0(S, J) + lane;
         const bool qv = q < tile_end(S, J);
         __syncwarp();
@@ -675,12 +753,16 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fp64(EngineDev E, in
         wv = warp_sum(valid ? wv : 0.0);
         const double cn = warp_sum(valid ? (double)nn : 0.0), cc = warp_sum(valid ? (double)nc : 0.0);
         if (lane == 0) {
-            S.tile_e[8 * I] = 0.5 * en;
-            S.tile_e[8 * I + 1] = 0.5 * ec;
-            S.tile_e[8 * I + 2] = 0.5 * wv;
-            S.tile_e[8 * I + 3] = 0.5 * cn;     // unique pairs
-            S.tile_e[8 * I + 4] = 0.5 * cc;
-            S.tile_e[8 * I + 5] = 0.5 * (double)(e1 - e0) * (kTile * kTile);
+            double* te = S.tile_e + 8 * item_index(S, I, 0);
+            te[0] = 0.5 * en;
+            te[1] = 0.5 * ec;
+            te[2] = 0.5 * wv;
+            te[3] = 0.5 * cn;     // unique pairs
+            te[4] = 0.5 * cc;
+            te[5] = 0.5 * (double)(e1 - e0) * (kTile * kTile);
+            if (Ip)               // the other work items of a proton tile hold nothing here
+                for (int c = 1; c < kPChunks; ++c)
+                    for (int k = 0; k < 6; ++k) S.tile_e[8 * item_index(S, I, c) + k] = 0.0;
         }
     }
 }
@@ -690,14 +772,15 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fp64(EngineDev E, in
 void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt) {
     const EngineDev& E = H.dev;
     const int nb = (E.ntiles + kForceWarps - 1) / kForceWarps;
+    const int nbi = (E.nitems + kForceWarps - 1) / kForceWarps;
     H.rec("force", s);
     if (H.precision == 1) {
         if (energy) k_force_fp64<true><<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
         else k_force_fp64<false><<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
         H.count(1);
     } else {
-        if (energy) k_force_split<true><<<nb, kForceWarps * 32, 0, s>>>(E, only);
-        else k_force_split<false><<<nb, kForceWarps * 32, 0, s>>>(E, only);
+        if (energy) k_force_split<true><<<nbi, kForceWarps * 32, 0, s>>>(E, only);
+        else k_force_split<false><<<nbi, kForceWarps * 32, 0, s>>>(E, only);
         H.rec("force_fix", s);
         k_force_fix<<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
         H.count(2);

@@ -310,7 +310,7 @@ __global__ void k_finalize(EngineDev E, int energy) {
     const double v2 = sys_sum(S, 0);
     double pn = 0, pc = 0, w = 0, cn = 0, cc = 0, ca = 0;
     if (energy) {
-        for (int t = lane; t < S.T; t += kRed) {
+        for (int t = lane; t < S.n_items; t += kRed) {
             pn += S.tile_e[8 * t];
             pc += S.tile_e[8 * t + 1];
             w += S.tile_e[8 * t + 2];
@@ -364,7 +364,7 @@ __global__ void k_energy_now(EngineDev E, int only, double* out) {
     const int lane = threadIdx.x;
     const double v2 = sys_sum(S, 0);
     double pn = 0, pc = 0, w = 0, cn = 0, cc = 0;
-    for (int t = lane; t < S.T; t += kRed) {
+    for (int t = lane; t < S.n_items; t += kRed) {
         pn += S.tile_e[8 * t];
         pc += S.tile_e[8 * t + 1];
         w += S.tile_e[8 * t + 2];

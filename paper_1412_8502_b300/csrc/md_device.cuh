@@ -81,6 +81,8 @@ struct PairF {
 struct SysConst {
     int N, Np, T, Tp;        // particles, protons, tiles, proton tiles
     int tile_base;           // first global tile (multiple of kTilesPerBlock)
+    int item_base;           // first global force work item (multiple of 4)
+    int n_items;             // force work items: kPChunks per proton tile, 1 per neutron tile
     int nbits;               // spatial-sort bits per axis
     long long bin_base;      // first global bin (2 species x 2^(3 nbits) bins)
     long long nbins;         // bins per species
@@ -108,10 +110,10 @@ struct SysConst {
     float* thalf;            // [T*3] tile half-extents at rebuild
     float4* sorg;            // [ceil(T/32)] super-tile (32 tiles) box centre
     float4* shalf;           // [ceil(T/32)] super-tile box half extents
-    int* lcount;             // [T]
-    int* lstart;             // [T+1]
+    int* lcount;             // [T] entries per tile
+    int* lnear;              // [T] of which near (written from the front of the region)
     int* list;               // [list_cap] tile-pair entries: J | kNucBit
-    double* tile_e;          // [T*8] per-tile PE_nuc, PE_coul, virial, pair counts
+    double* tile_e;          // [n_items*8] per work item PE_nuc, PE_coul, virial, pair counts
     long long* facc;         // [3N] split precision: forces in 2^-32 MeV/fm fixed point
     double* blk;             // [T/8 * 4] per-block KE partials
     ClusterBufs* cl;         // cluster-analysis buffers (device struct)
@@ -122,6 +124,8 @@ struct SysConst {
 struct EngineDev {
     const SysConst* sys;     // [nsys]
     const int* tile_sys;     // [ntiles] global tile -> system (-1: padding)
+    const int* item_sys;     // [nitems] global force work item -> system (-1: padding)
+    int nitems;              // global force work items (multiple of 4)
     int nsys;
     int ntiles;              // global tiles (multiple of kTilesPerBlock)
     long long nbins_total;   // global bins
@@ -131,6 +135,25 @@ struct EngineDev {
     unsigned* blocksum;      // [scan blocks]
     int* any_rebuild;        // set when any system rebuilds this step
 };
+
+// Force work items of a system.  A proton tile's list holds its near
+// entries (nuclear range) first and its Coulomb-only entries from the back of
+// its region; it gives kPChunks items: item 0 the near entries (and the tile
+// with itself), items 1.. equal parts of the Coulomb-only entries.  A neutron
+// tile is one item.  Proton items come first, item c of kItemGroup adjacent
+// tiles side by side (one block of the force kernel).
+constexpr int kPChunks = 4;
+constexpr int kItemGroup = 4;
+__host__ __device__ inline int proton_items(int Tp) {
+    return (Tp + kItemGroup - 1) / kItemGroup * kItemGroup * kPChunks;
+}
+__host__ __device__ inline int sys_items(int T, int Tp) { return proton_items(Tp) + (T - Tp); }
+__host__ __device__ inline int item_index(const SysConst& s, int t, int c) {
+    if (t >= s.Tp) return proton_items(s.Tp) + (t - s.Tp);
+    return ((t / kItemGroup) * kPChunks + c) * kItemGroup + t % kItemGroup;
+}
+// Position in tile I's list region of its e-th entry (near entries first).
+__device__ inline int list_pos(const SysConst& s, int e, int nnear) { return e < nnear ? e : s.T - 1 - (e - nnear); }
 
 __host__ __device__ inline int tile_slot0(const SysConst& s, int t) {
     return t < s.Tp ? t * kTile : s.Np + (t - s.Tp) * kTile;
