@@ -263,29 +263,31 @@ __device__ __forceinline__ float pair_n3(const float4& q, const float4& u, const
     if (kClass == kPPNuc || kClass == kPPCoul) {
         const float ri = rsqrt_approx(r2);
         const float r = r2 * ri;
-        const float ea = ex2_approx(fmaf(r, C.kc, C.l2a));     // alpha e^{-r/lambda}
-        const float vc = ea * ri;                             // screened Coulomb V
-        const float fc = vc * ri * (ri + C.il);
         const bool in = ok && r2 < C.rc2;
         if (kSel) {
+            const float ea = ex2_approx(fmaf(r, C.kc, C.l2a));     // alpha e^{-r/lambda}
+            const float vc = ea * ri;                             // screened Coulomb V
+            const float fc = vc * ri * (ri + C.il);
             fr = in ? fc : 0.0f;
             if (kEnergy) e.ec += in ? vc : 0.0f;
         } else {
-            const float m = in ? 1.0f : 0.0f;
-            fr = fc * m;
-            if (kEnergy) e.ec = fmaf(vc, m, e.ec);
+            // out of range: 2^-inf = +0 exactly, so V and the force vanish
+            // (ri is finite: a real source is never on the target)
+            const float arg = in ? fmaf(r, C.kc, C.l2a) : -INFINITY;
+            const float ea = ex2_approx(arg);
+            const float vc = ea * ri;
+            fr = vc * ri * (ri + C.il);
+            if (kEnergy) e.ec += vc;
         }
-        if (kEnergy) e.nc += in ? 1.0f : 0.0f;
+        if (kEnergy && in) e.nc += 1.0f;
     }
     if (kClass != kPPCoul) {
         const float gq = ex2_approx(r2 * C.kq);
         const bool in = ok && r2 < C.rn2;
         const float gm = in ? gq : 0.0f;
         fr = fmaf(gm, fmaf(C.A2, gq, S), fr);
-        if (kEnergy) {
-            e.en = fmaf(gm, fmaf(C.a, gq, bS), e.en);
-            e.nn += in ? 1.0f : 0.0f;
-        }
+        if (kEnergy) e.en = fmaf(gm, fmaf(C.a, gq, bS), e.en);
+        if (kEnergy && in) e.nn += 1.0f;
     }
     fx = fmaf(fr, dx, fx);
     fy = fmaf(fr, dy, fy);
@@ -573,8 +575,11 @@ __device__ __forceinline__ void force_item(const SysConst& S, int v, WarpQueues&
         const float gy = fmaxf(fabsf(uy) - hIy, 0.0f);
         const float gz = fmaxf(fabsf(uz) - hIz, 0.0f);
         const float d2 = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
-        if (Ip && Jp && S.coulomb == 1) {
-            const bool nuc = src_ok && !farc && d2 < Rn2;
+        if (farc) {                // Coulomb-only entry: every source goes to PPC or nowhere
+            push(Q, 1, src_ok && d2 < Rc2, c1, lane, h, l);
+            if (c1 >= kTile) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, X, C, T, facc, N);
+        } else if (Ip && Jp && S.coulomb == 1) {
+            const bool nuc = src_ok && d2 < Rn2;
             push(Q, 0, nuc, c0, lane, h, l);
             push(Q, 1, src_ok && !nuc && d2 < Rc2, c1, lane, h, l);
             if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, kPPNuc, c0, lane, X, C, T, facc, N);
