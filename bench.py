@@ -49,7 +49,7 @@ WORKLOADS = {
                    desc="2,000 nucleons, Yp=0.30, T=1.0 MeV, rho 0.080 fm^-3, no expansion"),
 }
 
-# nominal algorithmic FP32 flops per in-range ordered pair (FMA = 2 flops;
+# nominal algorithmic FP32 flops per in-range pair i<j, its force applied to both (FMA = 2 flops;
 # the ex2 / rsqrt special-function operations are not counted)
 FLOP_NUC, FLOP_COUL = 20.0, 30.0
 SMS, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
@@ -410,11 +410,12 @@ def cpu_baseline(W, seconds):
     N = W["N"]
     p = oracle.params(min(40.0, 0.5 * (N / W["rho"]) ** (1 / 3)))
     x, v, t, L = oracle.init(N, W["Yp"], W["rho"], W["T"], W["seed"], p)
-    n = 16
+    oracle.forces(x, t, L, p, 0, 64)              # start the thread pool
+    n = 1024                                      # calibrate on enough targets for every core
     t0 = time.perf_counter()
     oracle.forces(x, t, L, p, 0, n)
     dt = time.perf_counter() - t0
-    n = int(max(16, min(N, n * seconds / max(dt, 1e-6))))
+    n = int(max(64, min(N, n * seconds / max(dt, 1e-6))))
     t0 = time.perf_counter()
     F, _ = oracle.forces(x, t, L, p, 0, n)
     h = 0.5 * 2.0 / 939.0
