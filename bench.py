@@ -141,6 +141,11 @@ def run_gpu(args):
     p = md.md_params_default()
     p.energy_every = 1
     p.T = W["T"]
+    if args.lists == "verlet":          # the paper's per-particle neighbour lists, delta r = 4 fm
+        p.list_kind = 1
+        p.skin = 4.0
+    if args.skin is not None:
+        p.skin = args.skin
     sys_ = md.System(N, W["Yp"], W["rho"], W["T"], replicas.replica_seed(W["seed"], rank), p)
     stream = torch.cuda.Stream()
     sys_.set_stream(stream)
@@ -230,6 +235,8 @@ def run_gpu(args):
         "dtype": "f32 pair math / f64 state",
         "data": "synthetic: seeded uniform positions + 500 steepest-descent iterations, Maxwell velocities",
         "config": {"workload": W["desc"], "N": N, "Yp": W["Yp"], "T_MeV": W["T"], "rho_start": W["rho"],
+                   "lists": "half tile-pair lists" if args.lists == "tiles" else "per-particle Verlet lists",
+                   "skin_fm": p.skin,
                    "xi_dot": W["xi"], "window": "first steps of the expansion (densest, slowest)",
                    "clusters": "one cluster analysis inside the timed region",
                    "l2": "flushed between timed steps (256 MB write)",
@@ -247,6 +254,10 @@ def run_gpu(args):
         "tiles": {"count": info["tiles"], "list_entries": info["list_entries"], "rebuilds": info["rebuilds"],
                   "halfext_mean_fm": info["tile_halfext_mean"], "halfext_max_fm": info["tile_halfext_max"],
                   "need_wrap": info["need_wrap"]},
+        "lists": {"kind": args.lists, "skin_fm": p.skin, "rebuilds_in_timed_steps": rebuilds,
+                  "steps_per_rebuild": K / max(rebuilds, 1),
+                  "verlet_entries": info["verlet_entries"], "verlet_slots": info["verlet_slots"],
+                  "verlet_capacity": info["verlet_capacity"]},
         "kernel_ms_per_step": {k: v[1] / max(K, 1) for k, v in kt.items()},
         "cell_build": cell_build_roofline(kt, rebuilds, N, info, peaks),
         "step_ms_p50": sorted(step_ms)[len(step_ms) // 2],
@@ -456,6 +467,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="md409600", choices=list(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--lists", default="tiles", choices=["tiles", "verlet"],
+                    help="pair lists: half tile-pair lists (default) or per-particle Verlet lists (delta r = 4 fm)")
+    ap.add_argument("--skin", type=float, default=None, help="pair-list skin / Verlet delta r, fm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")

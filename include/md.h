@@ -83,6 +83,16 @@ typedef struct {
     int32_t affine;          /* 1: scale positions by L_{n+1}/L_n after each box
                                 update (an option; the paper does not rescale,
                                 Sec. II.A); 0 = off (default) */
+    int32_t list_kind;       /* pair lists: 0 = half tile-pair lists (default);
+                                1 = per-particle Verlet lists of every pair within
+                                its cutoff + skin, rebuilt by the same displacement
+                                rule (the paper's neighbour lists, Sec. II.B.1,
+                                where skin = delta r = 4 fm).  Split precision
+                                only (MD_EINVAL with MD_PREC_FP64). */
+    double verlet_pool;      /* list_kind 1: list entries reserved per particle,
+                                as a multiple of the expected neighbour count at
+                                the initial density (default 2).  A rebuild that
+                                needs more makes md_step return MD_ENOMEM. */
 } md_params;
 
 typedef struct {
@@ -133,6 +143,11 @@ typedef struct {
     int32_t sort_bits;
     double tile_halfext_mean;  /* mean / max tile half-extent at the last rebuild, fm */
     double tile_halfext_max;
+    int64_t verlet_entries;  /* list_kind 1: neighbour entries (ordered pairs) built
+                                at the last rebuild */
+    int64_t verlet_slots;    /* list_kind 1: pool slots used (entries + padding of
+                                the per-tile blocks) / available */
+    int64_t verlet_capacity;
 } md_info_t;
 
 /* Fill the defaults listed above. */

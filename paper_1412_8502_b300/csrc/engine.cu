@@ -7,6 +7,19 @@
 
 namespace pasta {
 
+// Pool slots for per-particle Verlet lists: verlet_pool x the expected
+// number of ordered neighbours within cutoff + skin at the initial density,
+// plus one block of 32 x 32 padding slots per tile.
+static long long verlet_capacity(int64_t N, int64_t Np, double L0, int T, const md_params& p, double rC) {
+    const double V = L0 * L0 * L0, pi = 3.14159265358979323846;
+    auto vol = [&](double R) { return std::min(4.0 / 3.0 * pi * R * R * R, V); };
+    const double rp = (double)Np / V, rn = (double)(N - Np) / V;
+    const double Rn = p.r_nuc + p.skin, Rc = (p.coulomb == 1 ? std::max(rC, p.r_nuc) : p.r_nuc) + p.skin;
+    const double per_p = rp * vol(Rc) + rn * vol(Rn), per_n = (rp + rn) * vol(Rn);
+    const double expect = (double)Np * per_p + (double)(N - Np) * per_n;
+    return (long long)std::ceil(p.verlet_pool * expect) + (long long)T * kTile * kTile;
+}
+
 // FP32 pair constants of Eq. (1) for the split-precision force pass.
 static PairF pair_consts(const SysConst& c) {
     const double ln2 = 0.69314718055994530942;
@@ -194,6 +207,10 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
     if (p.coulomb < 0 || p.coulomb > 2) return fail(MD_EINVAL, "coulomb must be 0, 1 or 2");
     if (p.affine != 0 && p.affine != 1) return fail(MD_EINVAL, "affine must be 0 or 1");
+    if (p.list_kind != 0 && p.list_kind != 1) return fail(MD_EINVAL, "list_kind must be 0 or 1");
+    if (p.list_kind == 1 && p.precision != MD_PREC_SPLIT)
+        return fail(MD_EINVAL, "Verlet lists (list_kind 1) need split precision");
+    if (p.list_kind == 1 && !(p.verlet_pool > 0.0)) return fail(MD_EINVAL, "verlet_pool must be > 0");
     const double L0 = std::cbrt((double)N / rho);
     double rC = p.r_C > 0.0 ? p.r_C : std::min(40.0, 0.5 * L0);
     // (relative slack of 1e-12 absorbs the rounding of cbrt)
@@ -255,6 +272,13 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     A(&c.list, (size_t)c.list_cap);
     A(&c.tile_e, 8 * (size_t)sys_items(s.T, s.Tp));
     A(&c.facc, 3 * (size_t)N);
+    if (p.list_kind == 1) {
+        c.vcap = verlet_capacity(N, s.Np, L0, s.T, p, rC);
+        A(&c.vlist, (size_t)c.vcap);
+        A(&c.vcount, (size_t)s.T * kTile);
+        A(&c.voff, (size_t)s.T);
+        A(&c.vwidth, (size_t)s.T);
+    }
     A(&c.blk, 4 * (size_t)(s.Tpad / kTilesPerBlock));
     A(&s.d_st, 1);
     A(&s.d_cl, 1);
@@ -289,6 +313,7 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     c.rebuild_every = (int)std::max<int64_t>(1, p.rebuild_every);
     c.coulomb = p.coulomb;
     c.energy_every = (int)p.energy_every;
+    c.list_kind = p.list_kind;
     c.pf = pair_consts(c);
 
     SysState st{};
@@ -383,7 +408,11 @@ int Engine::build_tables() {
     E.any_rebuild = d_any_;
     H_.precision = precision;
     H_.any_pp = false;
-    for (SysHost* h : sys) H_.any_pp |= (h->c.coulomb == 2);
+    H_.any_verlet = false;
+    for (SysHost* h : sys) {
+        H_.any_pp |= (h->c.coulomb == 2);
+        H_.any_verlet |= (h->c.list_kind == 1);
+    }
     return MD_OK;
 }
 
@@ -485,8 +514,12 @@ int Engine::check_errors() {
     for (int s = 0; s < n; ++s)
         CK(cudaMemcpyAsync(&errs[s], &sys[s]->d_st->error, sizeof(int), cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));
-    for (int s = 0; s < n; ++s)
+    for (int s = 0; s < n; ++s) {
+        if (errs[s] & 4)
+            return fail(MD_ENOMEM, "Verlet list pool of system " + std::to_string(s) +
+                                       " exhausted at a rebuild (raise verlet_pool)");
         if (errs[s]) return fail(MD_ENUMERIC, "non-finite force in system " + std::to_string(s));
+    }
     return MD_OK;
 }
 
@@ -496,7 +529,7 @@ int Engine::step(int64_t n, const std::vector<double>* xi) {
     return check_errors();
 }
 
-size_t Engine::estimate_bytes(int64_t N, double Yp, const md_params& p) {
+size_t Engine::estimate_bytes(int64_t N, double Yp, double rho, const md_params& p) {
     const int64_t Np = (int64_t)std::floor(Yp * (double)N + 0.5);
     const int64_t T = (Np + kTile - 1) / kTile + (N - Np + kTile - 1) / kTile;
     const int64_t Tpad = (T + kTilesPerBlock - 1) / kTilesPerBlock * kTilesPerBlock;
@@ -509,6 +542,11 @@ size_t Engine::estimate_bytes(int64_t N, double Yp, const md_params& p) {
          4 * 8 * Tpad;
     b += (size_t)T * T * 4;                                      // pair list
     b += (size_t)nb * 12 + 4096;                                 // engine bins
+    if (p.list_kind == 1) {
+        const double L0 = std::cbrt((double)N / rho);
+        const double rC = p.r_C > 0.0 ? p.r_C : std::min(40.0, 0.5 * L0);
+        b += 4 * (size_t)verlet_capacity(N, Np, L0, (int)T, p, rC) + (size_t)T * (32 * 4 + 12);
+    }
     return b;
 }
 
@@ -722,7 +760,35 @@ int Engine::set_params(int idx, const md_params& p) {
     if (p.affine != 0 && p.affine != 1) return fail(MD_EINVAL, "affine must be 0 or 1");
     if (p.precision != MD_PREC_SPLIT && p.precision != MD_PREC_FP64) return fail(MD_EINVAL, "bad precision");
     if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
+    if (p.list_kind != 0 && p.list_kind != 1) return fail(MD_EINVAL, "list_kind must be 0 or 1");
+    if (p.list_kind == 1 && p.precision != MD_PREC_SPLIT)
+        return fail(MD_EINVAL, "Verlet lists (list_kind 1) need split precision");
+    if (p.list_kind == 1 && !(p.verlet_pool > 0.0)) return fail(MD_EINVAL, "verlet_pool must be > 0");
     const int nbits = p.sort_bits ? p.sort_bits : auto_bits(h.N);
+    if (p.list_kind == 1) {
+        // (re)allocate the list pool when it is missing or too small
+        const long long cap = verlet_capacity(h.N, h.Np, h.L0, h.T, p, rC);
+        if (h.c.vlist == nullptr || cap > h.c.vcap) {
+            cudaStreamSynchronize(stream_);
+            drop_graphs();
+            void* old[] = {h.c.vlist, h.c.vcount, h.c.voff, h.c.vwidth};
+            for (void* q : old)
+                if (q) {
+                    cudaFree(q);
+                    h.allocs.erase(std::find(h.allocs.begin(), h.allocs.end(), q));
+                }
+            h.c.vlist = nullptr;
+            h.c.vcount = nullptr;
+            h.c.voff = nullptr;
+            h.c.vwidth = nullptr;
+            int rc = dalloc(h, &h.c.vlist, (size_t)cap);
+            if (!rc) rc = dalloc(h, &h.c.vcount, (size_t)h.T * kTile);
+            if (!rc) rc = dalloc(h, &h.c.voff, (size_t)h.T);
+            if (!rc) rc = dalloc(h, &h.c.vwidth, (size_t)h.T);
+            if (rc) return rc;
+            h.c.vcap = cap;
+        }
+    }
     if (p.precision != precision) {
         if (sys.size() > 1) return fail(MD_EINVAL, "precision is shared by all systems of a batch");
         precision = p.precision;
@@ -748,14 +814,20 @@ int Engine::set_params(int idx, const md_params& p) {
     c.thermostat_every = (int)p.thermostat_every;
     c.rebuild_every = (int)std::max<int64_t>(1, p.rebuild_every);
     const bool pp_changed = (c.coulomb == 2) != (p.coulomb == 2);
+    const bool lists_changed = c.list_kind != p.list_kind;
     c.coulomb = p.coulomb;
     c.energy_every = (int)p.energy_every;
+    c.list_kind = p.list_kind;
     c.pf = pair_consts(c);
-    if (pp_changed) {
+    if (pp_changed || lists_changed) {
         cudaStreamSynchronize(stream_);
         drop_graphs();
         H_.any_pp = false;
-        for (SysHost* q : sys) H_.any_pp |= (q->c.coulomb == 2);
+        H_.any_verlet = false;
+        for (SysHost* q : sys) {
+            H_.any_pp |= (q->c.coulomb == 2);
+            H_.any_verlet |= (q->c.list_kind == 1);
+        }
     }
     if (nbits != h.nbits) {
         // a different sort grid resizes the engine's bin tables
@@ -855,6 +927,9 @@ int Engine::info(int idx, md_info_t* out) {
     out->sort_bits = h.nbits;
     out->tile_halfext_mean = h.T ? (double)st.hsum / h.T : 0.0;
     out->tile_halfext_max = (double)__uint_as_float_host(st.hmax);
+    out->verlet_entries = h.c.list_kind == 1 ? (int64_t)st.vpairs : 0;
+    out->verlet_slots = h.c.list_kind == 1 ? (int64_t)st.vtop : 0;
+    out->verlet_capacity = h.c.list_kind == 1 ? (int64_t)h.c.vcap : 0;
     return MD_OK;
 }
 

@@ -64,7 +64,7 @@ public:
     // null) are recorded on the stream around every step.
     int step_async(int64_t n, const std::vector<double>* xi_per_sys, cudaEvent_t* events);
     // Device bytes a system with these arguments would allocate (engine of one).
-    static size_t estimate_bytes(int64_t N, double Yp, const md_params& p);
+    static size_t estimate_bytes(int64_t N, double Yp, double rho, const md_params& p);
     int refresh(int only);                  // forced rebuild + forces
     int forces(int idx, double* f_out);
     int energy(int idx, md_energy_t* e);

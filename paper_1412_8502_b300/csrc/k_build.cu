@@ -120,6 +120,8 @@ __global__ void k_decide(EngineDev E, int forced_only, int only) {
             st->hmax = 0u;
             st->hsum = 0.0f;
             st->list_total = 0;
+            st->vtop = 0ull;
+            st->vpairs = 0ull;
             atomicOr(&any, 1);
         }
     }
@@ -515,7 +517,7 @@ __global__ void k_lbuild(EngineDev E, int half) {
             const int b = __ffs(sm) - 1;
             sm &= sm - 1;
             const int J = (s0 + b) * kTile + lane;
-            const int e = (J < S.T && owns_pair(I, J, half)) ? list_entry(S, I, J, oI, hI, T) : -1;
+            const int e = (J < S.T && owns_pair(I, J, half && S.list_kind == 0)) ? list_entry(S, I, J, oI, hI, T) : -1;
             const bool near = e >= 0 && (e & kNucBit);
             const unsigned mn = __ballot_sync(0xffffffffu, near);
             const unsigned mf = __ballot_sync(0xffffffffu, e >= 0 && !near);
@@ -530,6 +532,128 @@ __global__ void k_lbuild(EngineDev E, int half) {
         S.lcount[I] = out + outf;
         S.lnear[I] = out;
         atomicAdd((unsigned long long*)&st->list_total, (unsigned long long)(out + outf));
+    }
+}
+
+// Per-particle Verlet lists (list_kind 1), built from the full tile-pair
+// lists: one block of kVB warps per tile I; lane l keeps every particle j of
+// the listed tiles (I itself included, l excluded) with |x_l - x_j| <
+// cutoff + skin, the Coulomb cutoff for proton pairs when the Coulomb term
+// is on.  Warp w takes list entries w, w + kVB, ...; pass 1 counts, the
+// counts are prefixed over the warps (warp order), the tile takes
+// 32 x (largest lane total) pool slots, and pass 2 writes each warp's part
+// at its offset.  An entry is the source's tile slot 32 J + k, the tile
+// pair's periodic shift code and kNucBit when the pair lies inside the
+// nuclear range + skin (its low parts are then needed).  A tile that finds
+// the pool exhausted keeps an empty list and raises error bit 2.
+constexpr int kVB = 4;
+
+__global__ void __launch_bounds__(kVB * 32) k_vbuild(EngineDev E) {
+    __shared__ float4 sh[kVB][kTile], sl[kVB][kTile];
+    __shared__ int cnts[kVB][kTile];
+    __shared__ long long s_base;
+    __shared__ int s_width;
+    if (!*E.any_rebuild) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x;
+    if (g >= E.ntiles) return;
+    const int s = E.tile_sys[g];
+    if (s < 0) return;
+    const SysConst& S = E.sys[s];
+    if (S.list_kind != 1 || !sys_rebuilds(S)) return;
+    const int I = g - S.tile_base;
+    if (I >= S.T) return;
+    SysState* st = S.st;
+    const double L = st->L;
+    const float Lhi = __double2float_rn(L), Llo = __double2float_rn(L - (double)Lhi), iLf = 1.0f / Lhi;
+    const bool wrap = st->need_wrap != 0;
+    const int nv = tile_end(S, I) - tile_slot0(S, I);
+    const bool valid = lane < nv;
+    const float4 hi = S.xhi[I * kTile + lane], lo = S.xlo[I * kTile + lane];
+    const bool Ip = I < S.Tp;
+    const float rn = (float)(S.r_nuc + S.skin) + kMargin;
+    const float rc = (float)((S.coulomb == 1 ? fmax(S.r_C, S.r_nuc) : S.r_nuc) + S.skin) + kMargin;
+    const float R2n = rn * rn, R2c = rc * rc;
+    const int* lst = S.list + (long long)I * S.T;
+    const int nl = S.lcount[I], nnear = S.lnear[I];
+    long long base = 0;
+    int cnt = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int e = w; e < nl; e += kVB) {
+            const int ent = lst[list_pos(S, e, nnear)];
+            const int J = ent & kJMask;
+            const int shk = (ent >> kShiftPos) & 63;
+            float4 h = S.xhi[J * kTile + lane], l = S.xlo[J * kTile + lane];
+            if (shk != kShiftNone) apply_shift(shk, Lhi, Llo, h, l);
+            __syncwarp();
+            sh[w][lane] = h;
+            sl[w][lane] = l;
+            __syncwarp();
+            const float R2 = (Ip && J < S.Tp) ? R2c : R2n;
+            const int nJ = tile_end(S, J) - tile_slot0(S, J);
+            for (int k = 0; k < nJ; ++k) {
+                const float4 q = sh[w][k], u = sl[w][k];
+                float dx = (hi.x - q.x) + (lo.x - u.x);
+                float dy = (hi.y - q.y) + (lo.y - u.y);
+                float dz = (hi.z - q.z) + (lo.z - u.z);
+                if (wrap) {
+                    const float kx = rintf(dx * iLf), ky = rintf(dy * iLf), kz = rintf(dz * iLf);
+                    dx = fmaf(-Llo, kx, fmaf(-Lhi, kx, dx));
+                    dy = fmaf(-Llo, ky, fmaf(-Lhi, ky, dy));
+                    dz = fmaf(-Llo, kz, fmaf(-Lhi, kz, dz));
+                }
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                if (valid && r2 < R2 && !(J == I && k == lane)) {
+                    if (pass == 1)
+                        S.vlist[base + 32ll * cnt + lane] =
+                            (J * kTile + k) | (shk << kShiftPos) | (r2 < R2n ? kNucBit : 0);
+                    ++cnt;
+                }
+            }
+        }
+        if (pass == 0) {
+            cnts[w][lane] = cnt;
+            __syncthreads();
+            int off = 0, tot = 0;
+            for (int q = 0; q < kVB; ++q) {
+                if (q < w) off += cnts[q][lane];
+                tot += cnts[q][lane];
+            }
+            if (w == 0) {
+                const int width = (int)__reduce_max_sync(0xffffffffu, (unsigned)tot);
+                if (lane == 0) {
+                    const unsigned long long b = atomicAdd(&st->vtop, 32ull * (unsigned long long)width);
+                    s_base = (long long)b;
+                    s_width = width;
+                    if ((long long)b + 32ll * width > S.vcap) {
+                        atomicOr(&st->error, 4);
+                        s_width = -1;
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_width < 0) {                      // pool exhausted: empty list
+                if (w == 0) S.vcount[I * kTile + lane] = 0;
+                if (threadIdx.x == 0) {
+                    S.voff[I] = 0;
+                    S.vwidth[I] = 0;
+                }
+                return;
+            }
+            base = s_base;
+            cnt = off;                              // this warp writes after the lower warps
+            if (w == 0) S.vcount[I * kTile + lane] = tot;
+        }
+    }
+    if (threadIdx.x == 0) {
+        S.voff[I] = s_base;
+        S.vwidth[I] = s_width;
+    }
+    if (w == 0) {
+        int tot = 0;
+        for (int q = 0; q < kVB; ++q) tot += cnts[q][lane];
+        const unsigned all = __reduce_add_sync(0xffffffffu, (unsigned)tot);
+        if (lane == 0) atomicAdd(&st->vpairs, (unsigned long long)all);
     }
 }
 
@@ -630,6 +754,11 @@ void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int on
     k_super<<<nb, kBlock, 0, s>>>(E);
     k_lbuild<<<nb, kBlock, 0, s>>>(E, H.precision == 0 ? 1 : 0);
     H.count(10);
+    if (H.any_verlet) {
+        H.rec("verlet_lists", s);
+        k_vbuild<<<E.ntiles, kVB * 32, 0, s>>>(E);
+        H.count(1);
+    }
 }
 
 // phase 0: count and scan (host then checks capacity); phase 1: write.

@@ -553,17 +553,7 @@ __device__ __forceinline__ void force_item(const SysConst& S, int v, WarpQueues&
         float4 l = farc ? make_float4(0.f, 0.f, 0.f, 0.f) : Q.sl[slot][lane];
         __syncwarp();
         const bool src_ok = h.x != kPad;
-        if (shk != (1 | (1 << 2) | (1 << 4))) {
-            const float fx = (float)((shk & 3) - 1), fy = (float)(((shk >> 2) & 3) - 1),
-                        fz = (float)(((shk >> 4) & 3) - 1);
-            float er;
-            two_sum(h.x, fx * Lhi, h.x, er);
-            l.x = l.x + fx * Llo + er;
-            two_sum(h.y, fy * Lhi, h.y, er);
-            l.y = l.y + fy * Llo + er;
-            two_sum(h.z, fz * Lhi, h.z, er);
-            l.z = l.z + fz * Llo + er;
-        }
+        if (shk != kShiftNone) apply_shift(shk, Lhi, Llo, h, l);
         // distance of the source to I's box (small boxes: nearest image)
         float ux = h.x - oI.x, uy = h.y - oI.y, uz = h.z - oI.z;
         if (kWrap) {
@@ -646,11 +636,189 @@ __global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS) k_fo
     const int s = E.item_sys[g];
     if (s < 0 || (only >= 0 && s != only)) return;
     const SysConst& S = E.sys[s];
+    if (S.list_kind != 0) return;          // per-particle lists: k_force_verlet
     const int v = g - S.item_base;
     if (v >= S.n_items) return;
     WarpQueues& Q = qs[threadIdx.x >> 5];
     if (S.st->need_wrap) force_item<true, kEnergy>(S, v, Q);
     else force_item<false, kEnergy>(S, v, Q);
+}
+
+// ---------------------------------------------------------------- Verlet
+// Split precision over per-particle Verlet lists (list_kind 1): one block of
+// kVW warps per tile; lane l of warp w sums its target over entries
+// k = w, w + kVW, ... of its list (two entries in flight), and the warps'
+// partial sums are added in warp order (deterministic).  Every neighbour is
+// listed on both sides, so no reaction is shared.  Sources are gathered by
+// tile slot; the entry's periodic shift is applied with an error-free sum
+// and the low parts are read for entries inside the nuclear range + skin,
+// so separations are exact as in k_force_split (far Coulomb-only pairs use
+// the high parts, as there).  The result goes to the fixed-point
+// accumulators (plain stores: one writer per particle), which k_force_fix
+// turns into FP32 forces.
+constexpr int kVW = 4;
+
+struct VAcc {
+    float fx, fy, fz, en, ec, w, nn, nc;
+};
+
+template <bool kWrap, bool kEnergy>
+__device__ __forceinline__ void verlet_pair(const SysConst& S, int ent, const float4& hi, const float4& lo, bool Ip,
+                                            bool coul, int pslots, float Lhi, float Llo, float iLf, VAcc& a) {
+    const PairF& P = S.pf;
+    const int j = ent & kJMask;
+    const int shk = (ent >> kShiftPos) & 63;
+    const bool near = (ent & kNucBit) != 0;
+    float4 h = S.xhi[j];
+    float4 l = near ? S.xlo[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (shk != kShiftNone) apply_shift(shk, Lhi, Llo, h, l);
+    float dx = hi.x - h.x, dy = hi.y - h.y, dz = hi.z - h.z;
+    if (near) {                          // far Coulomb-only pairs: high parts only
+        dx += lo.x - l.x;
+        dy += lo.y - l.y;
+        dz += lo.z - l.z;
+    }
+    if (kWrap) {
+        const float qx = rintf(dx * iLf), qy = rintf(dy * iLf), qz = rintf(dz * iLf);
+        dx = fmaf(-Llo, qx, fmaf(-Lhi, qx, dx));
+        dy = fmaf(-Llo, qy, fmaf(-Lhi, qy, dy));
+        dz = fmaf(-Llo, qz, fmaf(-Lhi, qz, dz));
+    }
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const bool jp = j < pslots;
+    float fr = 0.0f;
+    if (coul && Ip && jp) {
+        const float ri = rsqrt_approx(r2);
+        const float ea = ex2_approx(fmaf(r2 * ri, P.kc, P.l2a));
+        const float vc = ea * ri;
+        const bool in = r2 < P.rc2;
+        fr = in ? vc * ri * (ri + P.il) : 0.0f;
+        if (kEnergy && in) {
+            a.ec += vc;
+            a.nc += 1.0f;
+        }
+    }
+    if (near) {
+        const float gq = ex2_approx(r2 * P.kq);
+        const bool in = r2 < P.rn2;
+        const bool same = Ip == jp;
+        const float gm = in ? gq : 0.0f;
+        fr = fmaf(gm, fmaf(P.A2, gq, same ? P.Ssame : P.Scross), fr);
+        if (kEnergy && in) {
+            a.en = fmaf(gq, fmaf(P.a, gq, same ? P.bsame : P.bcross), a.en);
+            a.nn += 1.0f;
+        }
+    }
+    a.fx = fmaf(fr, dx, a.fx);
+    a.fy = fmaf(fr, dy, a.fy);
+    a.fz = fmaf(fr, dz, a.fz);
+    if (kEnergy) a.w = fmaf(fr, r2, a.w);
+}
+
+template <bool kWrap, bool kEnergy>
+__device__ __forceinline__ void verlet_tile(const SysConst& S, int I, float (*red)[8][kTile]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    SysState* st = S.st;
+    const double L = st->L;
+    const int N = S.N;
+    const float Lhi = __double2float_rn(L), Llo = __double2float_rn(L - (double)Lhi), iLf = 1.0f / Lhi;
+    const int p = tile_slot0(S, I) + lane;
+    const bool valid = p < tile_end(S, I);
+    const float4 hi = S.xhi[I * kTile + lane], lo = S.xlo[I * kTile + lane];
+    const bool Ip = I < S.Tp;
+    const bool coul = S.coulomb == 1;
+    const int cnt = valid ? S.vcount[I * kTile + lane] : 0;
+    const int* vl = S.vlist + S.voff[I] + lane;
+    const int width = S.vwidth[I];
+    const int pslots = S.Tp * kTile;             // tile slots below this are protons
+    Kahan kx, ky, kz, ken, kec, kw;
+    int nn = 0, nc = 0;
+    // blocks of 16 steps of kVW entries, two entries in flight per step
+    for (int k0 = w; k0 < width; k0 += 32 * kVW) {
+        VAcc a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int k1 = min(cnt, k0 + 32 * kVW);
+        for (int k = k0; k < k1; k += 2 * kVW) {
+            const bool two = k + kVW < k1;
+            const int e0 = vl[32ll * k];
+            const int e1 = two ? vl[32ll * (k + kVW)] : 0;
+            verlet_pair<kWrap, kEnergy>(S, e0, hi, lo, Ip, coul, pslots, Lhi, Llo, iLf, a);
+            if (two) verlet_pair<kWrap, kEnergy>(S, e1, hi, lo, Ip, coul, pslots, Lhi, Llo, iLf, a);
+        }
+        kx.add(a.fx);
+        ky.add(a.fy);
+        kz.add(a.fz);
+        if (kEnergy) {
+            ken.add(a.en);
+            kec.add(a.ec);
+            kw.add(a.w);
+            nn += (int)a.nn;
+            nc += (int)a.nc;
+        }
+    }
+    // partial sums of the kVW warps, added in warp order by warp 0
+    red[w][0][lane] = kx.s - kx.c;
+    red[w][1][lane] = ky.s - ky.c;
+    red[w][2][lane] = kz.s - kz.c;
+    red[w][3][lane] = ken.s - ken.c;
+    red[w][4][lane] = kec.s - kec.c;
+    red[w][5][lane] = kw.s - kw.c;
+    red[w][6][lane] = __int_as_float(nn);
+    red[w][7][lane] = __int_as_float(nc);
+    __syncthreads();
+    if (w != 0) return;
+    float fx = 0.f, fy = 0.f, fz = 0.f, en = 0.f, ec = 0.f, wv = 0.f;
+    int tn = 0, tc = 0;
+    for (int q = 0; q < kVW; ++q) {
+        fx += red[q][0][lane];
+        fy += red[q][1][lane];
+        fz += red[q][2][lane];
+        en += red[q][3][lane];
+        ec += red[q][4][lane];
+        wv += red[q][5][lane];
+        tn += __float_as_int(red[q][6][lane]);
+        tc += __float_as_int(red[q][7][lane]);
+    }
+    bool bad = false;
+    if (valid) {
+        bad = !(fabsf(fx) < kForceMax && fabsf(fy) < kForceMax && fabsf(fz) < kForceMax);
+        S.facc[p] = to_fix(fx);
+        S.facc[N + p] = to_fix(fy);
+        S.facc[2 * N + p] = to_fix(fz);
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&st->error, 1);
+    if (kEnergy) {
+        // every pair is in both particles' lists: halve the sums
+        const double e_n = warp_sum_f(en), e_c = warp_sum_f(ec), w_v = warp_sum_f(wv);
+        const int cn = __reduce_add_sync(0xffffffffu, tn), cc = __reduce_add_sync(0xffffffffu, tc);
+        const int ca = __reduce_add_sync(0xffffffffu, cnt);
+        if (lane == 0) {
+            double* te = S.tile_e + 8 * item_index(S, I, 0);
+            te[0] = 0.5 * e_n;
+            te[1] = 0.5 * e_c;
+            te[2] = 0.5 * w_v;
+            te[3] = 0.5 * (double)cn;
+            te[4] = 0.5 * (double)cc;
+            te[5] = 0.5 * (double)ca;
+            if (Ip)
+                for (int c = 1; c < kPChunks; ++c)
+                    for (int k = 0; k < 6; ++k) S.tile_e[8 * item_index(S, I, c) + k] = 0.0;
+        }
+    }
+}
+
+template <bool kEnergy>
+__global__ void __launch_bounds__(kVW * 32) k_force_verlet(EngineDev E, int only) {
+    __shared__ float red[kVW][8][kTile];
+    const int g = blockIdx.x;
+    if (g >= E.ntiles) return;
+    const int s = E.tile_sys[g];
+    if (s < 0 || (only >= 0 && s != only)) return;
+    const SysConst& S = E.sys[s];
+    if (S.list_kind != 1) return;
+    const int I = g - S.tile_base;
+    if (I >= S.T) return;
+    if (S.st->need_wrap) verlet_tile<true, kEnergy>(S, I, red);
+    else verlet_tile<false, kEnergy>(S, I, red);
 }
 
 // Fixed-point accumulators -> FP32 forces (rounded once), and back to zero
@@ -786,6 +954,12 @@ void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, in
     } else {
         if (energy) k_force_split<true><<<nbi, kForceWarps * 32, 0, s>>>(E, only);
         else k_force_split<false><<<nbi, kForceWarps * 32, 0, s>>>(E, only);
+        if (H.any_verlet) {
+            H.rec("force_verlet", s);
+            if (energy) k_force_verlet<true><<<E.ntiles, kVW * 32, 0, s>>>(E, only);
+            else k_force_verlet<false><<<E.ntiles, kVW * 32, 0, s>>>(E, only);
+            H.count(1);
+        }
         H.rec("force_fix", s);
         k_force_fix<<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
         H.count(2);

@@ -30,6 +30,7 @@ struct EngineHost {
     EngineDev dev;
     int precision = 0;
     bool any_pp = false;     // some system uses the all-pairs Coulomb (coulomb = 2)
+    bool any_verlet = false; // some system uses per-particle Verlet lists (list_kind 1)
     void* owner = nullptr;   // Engine*, for rec/count callbacks
     void (*rec_fn)(void*, const char*, cudaStream_t) = nullptr;
     void (*count_fn)(void*, int) = nullptr;

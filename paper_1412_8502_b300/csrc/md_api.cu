@@ -66,6 +66,8 @@ void md_params_default(md_params* p) {
     p->energy_every = 0;
     p->sort_bits = 0;
     p->affine = 0;
+    p->list_kind = 0;
+    p->verlet_pool = 2.0;
 }
 
 double md_lambda_thomas_fermi(double n_e) { return pasta::lambda_thomas_fermi(n_e); }

@@ -32,6 +32,7 @@ constexpr float kPad = 1.0e9f;          // local coordinate of an empty slot
 constexpr int kJMask = (1 << 24) - 1;
 constexpr int kShiftPos = 24;
 constexpr int kNucBit = 1 << 30;
+constexpr int kShiftNone = 1 | (1 << 2) | (1 << 4);   // shift code of (0, 0, 0)
 
 // Mutable per-system scalars (device memory).
 struct SysState {
@@ -40,7 +41,7 @@ struct SysState {
     double L_build;          // box side at the last rebuild
     double KE, PE_nuc, PE_coul, virial;     // last recorded energies
     double e_L, e_t;         // box side / time of the recorded energies
-    int64_t e_pairs_nuc, e_pairs_coul;   // in-range ordered pairs of that pass
+    int64_t e_pairs_nuc, e_pairs_coul;   // in-range pairs i<j of that pass
     int64_t e_cand;                      // candidate pairs evaluated in that pass
     float hsum;              // sum of tile half-extents at the last rebuild
     int pad1;
@@ -56,13 +57,14 @@ struct SysState {
     int keep_forces;         // permute cached forces during the rebuild
     int need_wrap;           // per-pair minimum image needed in FP32
     int have_energy;         // energies recorded by a step
-    int error;               // bit 0: non-finite force
+    int error;               // bit 0: non-finite force; bit 2: Verlet list pool exhausted
     unsigned maxdisp2;       // float bits of max |disp|^2 since the rebuild
     unsigned hmax;           // float bits of max tile half-extent at rebuild
     int pad0;
+    unsigned long long vtop;     // Verlet list pool slots taken at the last rebuild
+    unsigned long long vpairs;   // Verlet list entries written at the last rebuild
 };
 
-// Per-system constants and device pointers.
 // FP32 constants of the split-precision pair terms, computed on the host
 // from the FP64 parameters of the system (pair_consts in engine.cu).
 struct PairF {
@@ -78,6 +80,7 @@ struct PairF {
     float Rn2, Rc2;          // source filter radii^2: cutoff + skin/2 + 2e-3 fm
 };
 
+// Per-system constants and device pointers.
 struct SysConst {
     int N, Np, T, Tp;        // particles, protons, tiles, proton tiles
     int tile_base;           // first global tile (multiple of kTilesPerBlock)
@@ -93,6 +96,7 @@ struct SysConst {
     double r_pp, r_np, relax_gamma, relax_dmax;
     int thermostat_every, rebuild_every, coulomb, energy_every;
     int affine;              // scale positions with the box (option, not the paper)
+    int list_kind;           // 0 half tile-pair lists, 1 per-particle Verlet lists
     PairF pf;
     // state arrays (index [cur] is current)
     double* x[2];
@@ -115,6 +119,14 @@ struct SysConst {
     int* list;               // [list_cap] tile-pair entries: J | kNucBit
     double* tile_e;          // [n_items*8] per work item PE_nuc, PE_coul, virial, pair counts
     long long* facc;         // [3N] split precision: forces in 2^-32 MeV/fm fixed point
+    // per-particle Verlet lists (list_kind 1): for tile t, lane l's k-th entry
+    // is vlist[voff[t] + 32 k + l], k < vcount[32 t + l] <= vwidth[t]; an entry
+    // is the source's tile slot (32 J + lane) | shift code | nuclear flag
+    int* vlist;              // [vcap]
+    int* vcount;             // [T*32]
+    long long* voff;         // [T]
+    int* vwidth;             // [T]
+    long long vcap;          // pool capacity (entries)
     double* blk;             // [T/8 * 4] per-block KE partials
     ClusterBufs* cl;         // cluster-analysis buffers (device struct)
     SysState* st;
@@ -160,6 +172,26 @@ __host__ __device__ inline int tile_slot0(const SysConst& s, int t) {
 }
 __host__ __device__ inline int tile_end(const SysConst& s, int t) {
     return t < s.Tp ? min(s.Np, (t + 1) * kTile) : min(s.N, s.Np + (t - s.Tp + 1) * kTile);
+}
+
+// error-free a + b = s + e (FP32)
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Move a source (hi + lo) by the periodic shift of a list entry: each axis
+// code c in {0, 1, 2} adds (c - 1) L, L = Lhi + Llo, with an error-free sum.
+__device__ __forceinline__ void apply_shift(int shk, float Lhi, float Llo, float4& h, float4& l) {
+    const float fx = (float)((shk & 3) - 1), fy = (float)(((shk >> 2) & 3) - 1), fz = (float)(((shk >> 4) & 3) - 1);
+    float er;
+    two_sum_f(h.x, fx * Lhi, h.x, er);
+    l.x = l.x + fx * Llo + er;
+    two_sum_f(h.y, fy * Lhi, h.y, er);
+    l.y = l.y + fy * Llo + er;
+    two_sum_f(h.z, fz * Lhi, h.z, er);
+    l.z = l.z + fz * Llo + er;
 }
 
 // Wrap into [0, L): one period at most (displacements per step << L).

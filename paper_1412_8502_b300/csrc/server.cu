@@ -232,7 +232,7 @@ int md_server_submit(md_server* sv, const md_job* job, int64_t* id) {
         return fail(MD_EINVAL, "invalid job");
     Job* j = new Job();
     j->job = *job;
-    j->bytes = Engine::estimate_bytes(job->N, job->Yp, sv->prm);
+    j->bytes = Engine::estimate_bytes(job->N, job->Yp, job->rho, sv->prm);
     j->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
