@@ -87,6 +87,7 @@ def lib():
         L.orc_kinetic.restype = ctypes.c_double
         L.orc_clusters.argtypes = [ctypes.c_int64, _D, _I8, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, _I32, _I64, _I64, _D]
+        L.orc_mste.argtypes = [ctypes.c_int64, _D, _D, _I8, ctypes.c_double, _P, _I32, _I64, _I64, _D]
     return _lib
 
 
@@ -202,4 +203,21 @@ def clusters(x, typ, L: float, r_pp: float = 4.5, r_np: float = 3.0):
     lib().orc_clusters(N, _dp(x), typ.ctypes.data_as(_I8), float(L), float(r_pp), float(r_np),
                        lab.ctypes.data_as(_I32), hA.ctypes.data_as(_I64),
                        hZ.ctypes.data_as(_I64), _dp(st))
+    return lab, hA, hZ, st
+
+
+def mste(x, v, typ, L: float, p: Params):
+    """MSTE clusters (energy criterion; reading of Sec. II.C, which names the
+    method): returns (labels [N] int32, hist_A [N+1], hist_Z [Np+1], stats[5])."""
+    x = _as(x, np.float64).reshape(-1, 3)
+    v = _as(v, np.float64).reshape(-1, 3)
+    typ = _as(typ, np.int8)
+    N = x.shape[0]
+    Np = int((typ == 1).sum())
+    lab = np.zeros(N, dtype=np.int32)
+    hA = np.zeros(N + 1, dtype=np.int64)
+    hZ = np.zeros(Np + 1, dtype=np.int64)
+    st = np.zeros(5)
+    lib().orc_mste(N, _dp(x), _dp(v), typ.ctypes.data_as(_I8), float(L), ctypes.byref(p),
+                   lab.ctypes.data_as(_I32), hA.ctypes.data_as(_I64), hZ.ctypes.data_as(_I64), _dp(st))
     return lab, hA, hZ, st

@@ -353,3 +353,104 @@ void orc_clusters(int64_t N, const double* x, const int8_t* type, double L,
     free(pidx);
     free(parent);
 }
+
+/* ------------------------------------------------------------------------
+ * Minimum spanning tree in two-particle energy space (MSTE), the
+ * energy-based cluster criterion the paper names beside its distance
+ * algorithm (Sec. II.C).  Reading: nucleons i and j are bound when
+ *   e_ij = V_ij(r_ij) + (M/4) |v_i - v_j|^2 < 0,
+ * V_ij the pair potential of Eq. (1) (nuclear part for r < r_nuc; screened
+ * Coulomb for proton pairs, inside r_C when coulomb == 1, always when
+ * coulomb == 2) at the nearest image, (M/4)|dv|^2 the kinetic energy of the
+ * relative motion (reduced mass M/2).  Clusters are the connected
+ * components of the bound pairs (the components of a minimum spanning tree
+ * over the negative-energy edges).  Pairs at r >= r_nuc have V >= 0 and are
+ * never bound.  Every operation below is one IEEE FP64 operation in this
+ * order (no contraction):
+ *   d = x_i - x_j per axis, nearest image by comparison with L/2;
+ *   r2 = (dx*dx + dy*dy) + dz*dz;  g = exp(-r2 / (2 Lambda));
+ *   V = ((a*g)*g + s*g) + [pp] (alpha*exp(-sqrt(r2)/lambda)) / sqrt(r2);
+ *   k = (dvx*dvx + dvy*dvy) + dvz*dvz;  e = V + (M/4)*k.
+ * Labels: the smallest index of the component; a neutron bound to nothing
+ * is free (-1); a proton bound to nothing is a cluster by itself (as in
+ * Sec. II.C).  hist_A / hist_Z / stats as in orc_clusters (clusters of
+ * neutrons only count in hist_Z[0]).
+ * ---------------------------------------------------------------------- */
+static double ms_pair_energy(const double* xi, const double* xj, const double* vi, const double* vj,
+                             int ti, int tj, double L, const orc_params* p, int* in_range)
+{
+    const double r2 = cl_d2(xi, xj, L);
+    *in_range = r2 < p->r_nuc * p->r_nuc;
+    if (!*in_range) return 0.0;
+    const double s = (ti == tj) ? (p->b + p->c) : (p->b - p->c);
+    const double g = exp(-r2 / (2.0 * p->Lambda));
+    double v = (p->a * g) * g + s * g;
+    if (ti == 1 && tj == 1 && p->coulomb && (p->coulomb == 2 || r2 < p->r_C * p->r_C)) {
+        const double r = sqrt(r2);
+        v = v + (p->alpha * exp(-r / p->lambda_s)) / r;
+    }
+    const double dx = vi[0] - vj[0], dy = vi[1] - vj[1], dz = vi[2] - vj[2];
+    const double k = (dx * dx + dy * dy) + dz * dz;
+    return v + (0.25 * p->M) * k;
+}
+
+void orc_mste(int64_t N, const double* x, const double* v, const int8_t* type, double L,
+              const orc_params* p, int32_t* labels, int64_t* hist_A, int64_t* hist_Z, double* stats)
+{
+    int64_t* parent = (int64_t*)malloc((size_t)(N > 0 ? N : 1) * sizeof(int64_t));
+    int64_t* deg = (int64_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(int64_t));
+    int64_t Np = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        parent[i] = i;
+        Np += (type[i] == 1);
+    }
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = i + 1; j < N; ++j) {
+            int in = 0;
+            const double e = ms_pair_energy(&x[3 * i], &x[3 * j], &v[3 * i], &v[3 * j], type[i], type[j], L, p, &in);
+            if (in && e < 0.0) {
+                deg[i]++;
+                deg[j]++;
+                int64_t ri = uf_find(parent, i), rj = uf_find(parent, j);
+                if (ri != rj) {
+                    if (ri < rj) parent[rj] = ri;
+                    else parent[ri] = rj;
+                }
+            }
+        }
+    for (int64_t i = 0; i < N; ++i)
+        labels[i] = (type[i] == 0 && deg[i] == 0) ? -1 : (int32_t)uf_find(parent, i);
+
+    int64_t* zc = (int64_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(int64_t));
+    int64_t* ac = (int64_t*)calloc((size_t)(N > 0 ? N : 1), sizeof(int64_t));
+    int64_t nfree = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (labels[i] < 0) { nfree++; continue; }
+        ac[labels[i]] += 1;
+        if (type[i] == 1) zc[labels[i]] += 1;
+    }
+    memset(hist_A, 0, (size_t)(N + 1) * sizeof(int64_t));
+    memset(hist_Z, 0, (size_t)(Np + 1) * sizeof(int64_t));
+    int64_t ncl = 0, nbig = 0, sumA = 0, sumZ = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (labels[i] == (int32_t)i) {
+            ncl++;
+            hist_A[ac[i]] += 1;
+            hist_Z[zc[i]] += 1;
+            if (ac[i] >= 12) {
+                nbig++;
+                sumA += ac[i];
+                sumZ += zc[i];
+            }
+        }
+    }
+    stats[0] = (double)ncl;
+    stats[1] = (double)nfree / (double)N;
+    stats[2] = nbig ? (double)sumA / (double)nbig : 0.0;
+    stats[3] = nbig ? (double)sumZ / (double)nbig : 0.0;
+    stats[4] = (double)nbig;
+    free(zc);
+    free(ac);
+    free(deg);
+    free(parent);
+}

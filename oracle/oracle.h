@@ -131,6 +131,17 @@ void orc_clusters(int64_t N, const double* x, const int8_t* type, double L,
                   double r_pp, double r_np, int32_t* labels,
                   int64_t* hist_A, int64_t* hist_Z, double* stats);
 
+/* MSTE clusters (energy criterion, a reading: the paper names the method in
+ * Sec. II.C without defining it).  Nucleons i, j are bound when
+ * V_ij(r) + (M/4)|v_i - v_j|^2 < 0 with V of Eq. (1) at the nearest image
+ * (nuclear part inside r_nuc; Coulomb for proton pairs inside r_C, or always
+ * with coulomb == 2); clusters are the connected components of bound pairs,
+ * labelled by their smallest index; a neutron bound to nothing is free (-1),
+ * a proton bound to nothing is its own cluster.  Outputs as orc_clusters.
+ * v is [N][3] like x. */
+void orc_mste(int64_t N, const double* x, const double* v, const int8_t* type, double L,
+              const orc_params* p, int32_t* labels, int64_t* hist_A, int64_t* hist_Z, double* stats);
+
 #ifdef __cplusplus
 }
 #endif

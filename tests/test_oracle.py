@@ -476,3 +476,110 @@ def test_affine_option_scales_positions_with_the_box():
     assert np.allclose(r["x"] / x, r["L"] / 100.0, rtol=1e-13)
     r0 = oracle.run(x, v, t, 100.0, p, 10, xi_dot=1e-3)
     assert np.array_equal(r0["x"], x)
+
+
+# ------------------------------------------------------------------ MSTE
+# Energy-criterion clusters (reading of Sec. II.C: the paper names MSTE
+# without defining it): i, j bound when V_ij + (M/4)|v_i - v_j|^2 < 0.
+
+def _pair_min_r(s, a=110.0, Lam=1.25):
+    """Eq. (1) nuclear term a g^2 + s g, g = exp(-r^2/(2 Lambda)): minimum
+    -s^2/(4a) at g = -s/(2a)."""
+    r2 = 2.0 * Lam * math.log(2.0 * a / abs(s))
+    return math.sqrt(r2), -s * s / (4.0 * a)
+
+
+def _mste2(t0, t1, r, dv=0.0, L=60.0, coulomb=True):
+    x = np.array([[20.0, 20.0, 20.0], [20.0 + r, 20.0, 20.0]])
+    v = np.zeros((2, 3))
+    v[1, 1] = dv
+    t = np.array([t0, t1], dtype=np.int8)
+    return oracle.mste(x, v, t, L, P(r_C=20.0, coulomb=coulomb))
+
+
+def test_mste_np_pair_binding_threshold():
+    r, vmin = _pair_min_r(-26.0 - 24.0)                 # unlike species: s = b - c
+    lab, hA, hZ, st = _mste2(1, 0, r)
+    assert list(lab) == [0, 0] and hA[2] == 1 and hZ[1] == 1 and st[0] == 1 and st[1] == 0
+    M = 939.0
+    for f, bound in ((1.0 - 1e-9, True), (1.0 + 1e-9, False)):
+        dv = math.sqrt(4.0 * (-vmin) * f / M)          # (M/4) dv^2 = f |V_min|
+        lab, hA, hZ, st = _mste2(1, 0, r, dv)
+        if bound:
+            assert list(lab) == [0, 0]
+        else:                                            # lone proton is a cluster, neutron free
+            assert list(lab) == [0, -1] and hA[1] == 1 and st[1] == 0.5
+
+
+def test_mste_like_pairs_and_coulomb():
+    r, vmin = _pair_min_r(-26.0 + 24.0)                 # like species: s = b + c
+    lab, hA, hZ, st = _mste2(0, 0, r)                    # nn at rest: bound, no proton
+    assert list(lab) == [0, 0] and hZ[0] == 1 and st[0] == 1
+    lab, _, _, st = _mste2(1, 1, r)                       # pp: Coulomb (~0.3 MeV) unbinds
+    assert list(lab) == [0, 1] and st[0] == 2
+    lab, _, _, _ = _mste2(1, 1, r, coulomb=False)        # without it the pp pair binds
+    assert list(lab) == [0, 0]
+
+
+def test_mste_strict_nuclear_range_and_periodic_image():
+    # at rest any r < r_nuc binds an np pair (V < 0, however small); r_nuc is strict
+    assert list(_mste2(1, 0, 11.4)[0]) == [0, 0]
+    assert list(_mste2(1, 0, 11.6)[0]) == [0, -1]
+    assert list(_mste2(1, 0, 11.5)[0]) == [0, -1]        # r^2 = 132.25 exactly, not < r_nuc^2
+    # the same pair across the periodic face
+    r, _ = _pair_min_r(-50.0)
+    x = np.array([[0.2, 5.0, 5.0], [0.2 - r + 30.0, 5.0, 5.0]])
+    lab, _, _, _ = oracle.mste(x, np.zeros((2, 3)), np.array([0, 1], dtype=np.int8), 30.0, P(r_C=10.0))
+    assert list(lab) == [0, 0]
+
+
+def test_mste_chain_connectivity():
+    """n - p - n, each neutron at the np minimum distance from the proton:
+    connected through the proton, one cluster A = 3, Z = 1."""
+    r, _ = _pair_min_r(-50.0)
+    x = np.array([[20.0 - r, 20.0, 20.0], [20.0, 20.0, 20.0], [20.0 + r, 20.0, 20.0]])
+    v = np.zeros((3, 3))
+    v[0, 2], v[2, 2] = 0.01, -0.01
+    t = np.array([0, 1, 0], dtype=np.int8)
+    lab, hA, hZ, st = oracle.mste(x, v, t, 60.0, P(r_C=20.0))
+    assert list(lab) == [0, 0, 0] and hA[3] == 1 and hZ[1] == 1
+
+
+def test_mste_bfs_on_random_inputs():
+    """Independent brute force: the bound-pair matrix from numpy and a BFS."""
+    rng = np.random.default_rng(5)
+    for trial in range(4):
+        N, L = 60, 14.0
+        x = rng.uniform(0, L, (N, 3))
+        v = rng.normal(0, 0.02, (N, 3))
+        t = (rng.uniform(size=N) < 0.4).astype(np.int8)
+        p = P(r_C=7.0)
+        lab, hA, hZ, st = oracle.mste(x, v, t, L, p)
+        d = x[:, None, :] - x[None, :, :]
+        d -= L * np.round(d / L)
+        r2 = (d ** 2).sum(-1)
+        g = np.exp(-r2 / 2.5)
+        s = np.where(t[:, None] == t[None, :], -2.0, -50.0)
+        V = 110.0 * g * g + s * g
+        pp = (t[:, None] == 1) & (t[None, :] == 1) & (r2 < 49.0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            r = np.sqrt(r2)
+            V = V + np.where(pp, 1.4399645 * np.exp(-r / 10.0) / np.where(r > 0, r, 1.0), 0.0)
+        e = V + 0.25 * 939.0 * ((v[:, None, :] - v[None, :, :]) ** 2).sum(-1)
+        B = (e < 0.0) & (r2 < 11.5 ** 2)
+        np.fill_diagonal(B, False)
+        ref = np.full(N, -1)
+        for i in range(N):
+            if ref[i] >= 0 or (t[i] == 0 and not B[i].any()):
+                continue
+            comp, stack = {i}, [i]
+            while stack:
+                k = stack.pop()
+                for j in np.nonzero(B[k])[0]:
+                    if j not in comp:
+                        comp.add(j)
+                        stack.append(j)
+            for j in comp:
+                ref[j] = min(comp)
+        assert np.array_equal(lab, ref), trial
+        assert B.sum() > 0
