@@ -198,6 +198,23 @@ MD_API int md_step_energy(md_system* s, md_energy_t* out);
 MD_API int md_clusters(md_system* s, int32_t* labels, int64_t* hist_A, int64_t* hist_Z,
                 md_cluster_stats* stats);
 
+/* Energy-criterion clusters: the minimum spanning tree in two-particle
+ * energy space (MSTE), which Sec. II.C names beside its distance algorithm
+ * without defining it.  Reading taken: nucleons i, j are bound when
+ *   V_ij(r_ij) + (M/4) |v_i - v_j|^2 < 0,
+ * V the pair potential of Eq. (1) at the nearest image (nuclear part inside
+ * r_nuc, screened Coulomb for proton pairs as in the force) and (M/4)|dv|^2
+ * the kinetic energy of the relative motion; clusters are the connected
+ * components of bound pairs.  labels [N] (may be NULL): smallest original
+ * index of the cluster (any species); -1 for a neutron bound to nothing; a
+ * proton bound to nothing is a cluster by itself.  hist_A [N+1], hist_Z
+ * [Np+1] (may be NULL) count clusters by mass and charge (neutron-only
+ * clusters in hist_Z[0]); stats as md_clusters.  Decisions are those of
+ * FP64 arithmetic in a fixed order (pairs far from the threshold are
+ * screened in FP32). */
+MD_API int md_clusters_mste(md_system* s, int32_t* labels, int64_t* hist_A, int64_t* hist_Z,
+                            md_cluster_stats* stats);
+
 /* Copy the state to the caller (md_state_view above). */
 MD_API int md_get_state(md_system* s, md_state_view* view);
 /* Replace x, v (and the clock fields) from the caller; N and Np must match,

@@ -645,10 +645,10 @@ int Engine::ensure_cluster_bufs(SysHost& h, long long need) {
         auto A = [&](auto** p, size_t count) {
             if (rc == MD_OK) rc = dalloc(h, p, count);
         };
-        A(&B.parent, (size_t)h.Np);
-        A(&B.minid, (size_t)h.Np);
-        A(&B.zc, (size_t)h.Np);
-        A(&B.ac, (size_t)h.Np);
+        A(&B.parent, (size_t)h.N);
+        A(&B.minid, (size_t)h.N);
+        A(&B.zc, (size_t)h.N);
+        A(&B.ac, (size_t)h.N);
         A(&B.label, (size_t)h.N);
         A(&B.hist_A, (size_t)h.N + 1);
         A(&B.hist_Z, (size_t)h.Np + 1);
@@ -682,6 +682,31 @@ int Engine::clusters(int idx, int32_t* labels, int64_t* hA, int64_t* hZ, md_clus
     if ((rc = ensure_cluster_bufs(h, total))) return rc;
     launch_cluster_lists(H_, stream_, 1, idx);
     launch_clusters(H_, stream_, idx, (int)h.Np, (int)h.N, h.Tp, h.T, h.d_stage_lab);
+    CK(cudaGetLastError());
+    long long st[8];
+    if (labels)
+        CK(cudaMemcpyAsync(labels, h.d_stage_lab, sizeof(int32_t) * h.N, cudaMemcpyDeviceToHost, stream_));
+    if (hA) CK(cudaMemcpyAsync(hA, h.hcl.hist_A, sizeof(int64_t) * (h.N + 1), cudaMemcpyDeviceToHost, stream_));
+    if (hZ) CK(cudaMemcpyAsync(hZ, h.hcl.hist_Z, sizeof(int64_t) * (h.Np + 1), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaMemcpyAsync(st, h.hcl.stats, sizeof(st), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    if (out) {
+        out->n_clusters = st[0];
+        out->n_free = st[1];
+        out->n_big = st[2];
+        out->m_free_n = (double)st[1] / (double)h.N;
+        out->A_mean = st[2] ? (double)st[3] / (double)st[2] : 0.0;
+        out->Z_mean = st[2] ? (double)st[4] / (double)st[2] : 0.0;
+    }
+    return MD_OK;
+}
+
+int Engine::clusters_mste(int idx, int32_t* labels, int64_t* hA, int64_t* hZ, md_cluster_stats* out) {
+    SysHost& h = *sys[idx];
+    int rc;
+    if (h.dirty && (rc = refresh(idx))) return rc;
+    if ((rc = ensure_cluster_bufs(h, 0))) return rc;
+    launch_mste(H_, stream_, idx, (int)h.N, h.T, h.d_stage_lab);
     CK(cudaGetLastError());
     long long st[8];
     if (labels)

@@ -70,6 +70,7 @@ public:
     int energy(int idx, md_energy_t* e);
     int step_energy(int idx, md_energy_t* e);
     int clusters(int idx, int32_t* labels, int64_t* hA, int64_t* hZ, md_cluster_stats* st);
+    int clusters_mste(int idx, int32_t* labels, int64_t* hA, int64_t* hZ, md_cluster_stats* st);
     int get_state(int idx, md_state_view* v);
     int set_state(int idx, const md_state_view* v);
     int set_params(int idx, const md_params& p);

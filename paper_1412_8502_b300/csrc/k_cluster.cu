@@ -62,6 +62,12 @@ __device__ inline void uf_union(int* parent, int a, int b) {
 }
 
 constexpr int kCW = 4;   // warps per block
+
+__device__ __forceinline__ float ex2f_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 constexpr float kBand = 1e-3f;   // fm^2, far above the FP32 screening error
 
 struct Frame {
@@ -270,6 +276,217 @@ __global__ void k_cl_hist(EngineDev E, int only, int32_t* labels_out) {
             atomicAdd((unsigned long long*)&B.stats[4], (unsigned long long)Z);
         }
     }
+}
+
+// ------------------------------------------------------------------ MSTE
+// Energy-criterion clusters, the minimum spanning tree in two-particle
+// energy space that Sec. II.C names beside its distance algorithm (reading
+// of the definition): nucleons i, j are bound when
+//   e_ij = V_ij(r_ij) + (M/4) |v_i - v_j|^2 < 0,
+// V_ij of Eq. (1) at the nearest image (nuclear part inside r_nuc; screened
+// Coulomb for proton pairs, inside r_C when coulomb == 1, always when
+// coulomb == 2).  Clusters are the connected components of bound pairs.
+// Candidate pairs: the tile with itself and the near entries of the force
+// lists (every pair inside r_nuc; pairs beyond have V >= 0).  Each pair is
+// screened in FP32 (exact hi + lo separations, velocities rounded to FP32);
+// pairs within a margin of the threshold take the decision of FP64
+// arithmetic in a fixed order (no contraction):
+//   r2 as for the distance clusters; g = exp(-r2 / (2 Lambda));
+//   V = ((a g) g + s g) + [pp] (alpha exp(-sqrt(r2) / lambda)) / sqrt(r2);
+//   e = V + (M/4) ((dvx dvx + dvy dvy) + dvz dvz).
+
+namespace {
+
+__device__ inline bool ms_bound_exact(const SysConst& S, const double* x, const double* v, int p, int q,
+                                      double L, double hL) {
+    const int N = S.N;
+    const double r2 = d2_exact(x[p], x[N + p], x[2 * N + p], x[q], x[N + q], x[2 * N + q], L, hL);
+    if (!(r2 < __dmul_rn(S.r_nuc, S.r_nuc))) return false;
+    const bool pi = p < S.Np, pj = q < S.Np;
+    const double sc = (pi == pj) ? __dadd_rn(S.b, S.c) : __dsub_rn(S.b, S.c);
+    const double g = exp(__ddiv_rn(-r2, __dmul_rn(2.0, S.Lambda)));
+    double V = __dadd_rn(__dmul_rn(__dmul_rn(S.a, g), g), __dmul_rn(sc, g));
+    if (pi && pj && S.coulomb != 0 && (S.coulomb == 2 || r2 < __dmul_rn(S.r_C, S.r_C))) {
+        const double r = __dsqrt_rn(r2);
+        V = __dadd_rn(V, __ddiv_rn(__dmul_rn(S.alpha, exp(__ddiv_rn(-r, S.lambda_s))), r));
+    }
+    const double dx = __dsub_rn(v[p], v[q]), dy = __dsub_rn(v[N + p], v[N + q]), dz = __dsub_rn(v[2 * N + p], v[2 * N + q]);
+    const double k = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return __dadd_rn(V, __dmul_rn(__dmul_rn(0.25, S.M), k)) < 0.0;
+}
+
+constexpr float kMsRel = 1e-4f;     // FP32 screening margin, relative to the terms' magnitudes
+constexpr float kMsAbs = 1e-9f;     // and absolute (MeV)
+
+}  // namespace
+
+// All N slots: parent = self; minid, per-root counts, outputs cleared.
+__global__ void k_ms_init(EngineDev E, int only) {
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < S.N) {
+        B.parent[i] = i;
+        B.minid[i] = 0x7fffffff;
+        B.zc[i] = 0;
+        B.ac[i] = 0;
+    }
+    if (i <= S.N) B.hist_A[i] = 0;
+    if (i <= S.Np) B.hist_Z[i] = 0;
+    if (i < 8) B.stats[i] = 0;
+}
+
+// Warp per tile: union of every bound pair (i in I, j in I or a near entry).
+// half: the force lists hold each tile pair once and leave the tile itself
+// out (split precision, tile lists); otherwise they are full.
+__global__ void k_ms_link(EngineDev E, int only, int prec) {
+    __shared__ float4 sh[kCW][kTile], sl[kCW][kTile], sv[kCW][kTile];
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int I = blockIdx.x * kCW + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (I >= S.T) return;
+    const SysState* st = S.st;
+    const Frame F = frame_of(st);
+    const double L = st->L, hL = 0.5 * L;
+    const int N = S.N, c = st->cur;
+    const double* x = S.x[c];
+    const double* v = S.v[c];
+    const bool half = prec == 0 && S.list_kind == 0;
+    const PairF& P = S.pf;
+    const float far2 = P.rn2 + kBand, near2 = P.rn2 - kBand;
+    const float a = (float)S.a, qM = (float)(0.25 * S.M);
+    const int p0 = tile_slot0(S, I), p = p0 + lane;
+    const bool valid = p < tile_end(S, I);
+    const bool Ip = I < S.Tp;
+    const float4 hi = S.xhi[I * kTile + lane], lo = S.xlo[I * kTile + lane];
+    const float vx = valid ? (float)v[p] : 0.f, vy = valid ? (float)v[N + p] : 0.f, vz = valid ? (float)v[2 * N + p] : 0.f;
+    const int* lst = S.list + (long long)I * S.T;
+    const int nnear = S.lnear[I];
+    // source 0 .. nnear (+1 for the tile itself when the lists leave it out)
+    const int nsrc = nnear + (half ? 1 : 0);
+    for (int e = 0; e < nsrc; ++e) {
+        int J = I, shk = kShiftNone;
+        if (!half || e > 0) {
+            const int ent = lst[half ? e - 1 : e];
+            J = ent & kJMask;
+            shk = (ent >> kShiftPos) & 63;
+        }
+        float4 h = S.xhi[J * kTile + lane], l = S.xlo[J * kTile + lane];
+        if (shk != kShiftNone) apply_shift(shk, F.Lhi, F.Llo, h, l);
+        const int q0 = tile_slot0(S, J), nJ = tile_end(S, J) - q0;
+        const int qs = q0 + lane;
+        float4 vq = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane < nJ) vq = make_float4((float)v[qs], (float)v[N + qs], (float)v[2 * N + qs], 0.f);
+        __syncwarp();
+        sh[w][lane] = h;
+        sl[w][lane] = l;
+        sv[w][lane] = vq;
+        __syncwarp();
+        if (!valid) continue;
+        const bool Jp = J < S.Tp;
+        const bool pp = Ip && Jp;
+        const bool coul = pp && S.coulomb != 0;
+        const float sfac = (Ip == Jp) ? (float)(S.b + S.c) : (float)(S.b - S.c);
+        for (int k = 0; k < nJ; ++k) {
+            const int q = q0 + k;
+            if (J == I && q <= p) continue;            // each pair of the tile once
+            const float r2 = d2_screen(hi, lo, sh[w][k], sl[w][k], F);
+            if (r2 >= far2) continue;
+            const float g = ex2f_approx(r2 * P.kq);
+            float V = g * fmaf(a, g, sfac);
+            float mag = g * fmaf(a, g, fabsf(sfac));
+            if (coul && (S.coulomb == 2 || r2 < P.rc2)) {
+                const float ri = rsqrtf(r2);
+                const float vc = ex2f_approx(fmaf(r2 * ri, P.kc, P.l2a)) * ri;
+                V += vc;
+                mag += vc;
+            }
+            const float4 u = sv[w][k];
+            const float dx = vx - u.x, dy = vy - u.y, dz = vz - u.z;
+            const float ke = qM * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float e = V + ke, band = kMsRel * (mag + ke) + kMsAbs;
+            // (a Coulomb cutoff inside the nuclear range: its edge is decided in FP64)
+            const bool cedge = coul && S.coulomb == 1 && fabsf(r2 - P.rc2) < kBand;
+            bool bound;
+            if (cedge) bound = ms_bound_exact(S, x, v, p, q, L, hL);
+            else if (e > band) bound = false;
+            else if (e < -band && r2 < near2) bound = true;
+            else bound = ms_bound_exact(S, x, v, p, q, L, hL);
+            if (bound) uf_union(B.parent, p, q);
+        }
+    }
+}
+
+// Per root: smallest original index and component size.
+__global__ void k_ms_root(EngineDev E, int only) {
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= S.N) return;
+    const int r = uf_find(B.parent, q);
+    atomicMin(&B.minid[r], S.id[S.st->cur][q]);
+    atomicAdd(&B.ac[r], 1);
+}
+
+// Labels (a neutron alone in its component is free); counts cleared for
+// the per-label pass.
+__global__ void k_ms_label(EngineDev E, int only) {
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= S.N) return;
+    const int r = uf_find(B.parent, q);
+    B.label[q] = (q >= S.Np && B.ac[r] == 1) ? -1 : B.minid[r];
+}
+
+__global__ void k_ms_clear(EngineDev E, int only) {
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= S.N) return;
+    B.ac[q] = 0;
+    B.zc[q] = 0;
+}
+
+// Histograms over clusters (the representative is the member whose original
+// index is the label, of either species); labels written in original order.
+__global__ void k_ms_hist(EngineDev E, int only, int32_t* labels_out) {
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.N) return;
+    const int i = S.id[S.st->cur][p];
+    const int lab = B.label[p];
+    if (labels_out) labels_out[i] = lab;
+    if (lab >= 0 && lab == i) {
+        const int A = B.ac[i], Z = B.zc[i];
+        atomicAdd((unsigned long long*)&B.hist_A[A], 1ull);
+        atomicAdd((unsigned long long*)&B.hist_Z[Z], 1ull);
+        atomicAdd((unsigned long long*)&B.stats[0], 1ull);
+        if (A >= 12) {
+            atomicAdd((unsigned long long*)&B.stats[2], 1ull);
+            atomicAdd((unsigned long long*)&B.stats[3], (unsigned long long)A);
+            atomicAdd((unsigned long long*)&B.stats[4], (unsigned long long)Z);
+        }
+    }
+}
+
+void launch_mste(const EngineHost& H, cudaStream_t s, int only, int N, int T, int32_t* d_labels_out) {
+    const EngineDev& E = H.dev;
+    const int n1 = (N + 1 + 255) / 256, n = (N + 255) / 256;
+    H.rec("ms_init", s);
+    k_ms_init<<<n1, 256, 0, s>>>(E, only);
+    H.rec("ms_link", s);
+    k_ms_link<<<(T + kCW - 1) / kCW, kCW * 32, 0, s>>>(E, only, H.precision);
+    H.rec("ms_label", s);
+    k_ms_root<<<n, 256, 0, s>>>(E, only);
+    k_ms_label<<<n, 256, 0, s>>>(E, only);
+    k_ms_clear<<<n, 256, 0, s>>>(E, only);
+    k_cl_count<<<n, 256, 0, s>>>(E, only);
+    H.rec("ms_hist", s);
+    k_ms_hist<<<n, 256, 0, s>>>(E, only, d_labels_out);
+    H.count(7);
 }
 
 void launch_clusters(const EngineHost& H, cudaStream_t s, int only, int Np, int N, int Tp, int T,

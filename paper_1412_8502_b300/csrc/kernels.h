@@ -9,10 +9,10 @@ namespace pasta {
 
 // Buffers of the on-demand cluster analysis (allocated on first use).
 struct ClusterBufs {
-    int* parent;             // [Np] union-find over sorted proton slots
-    int* minid;              // [Np] smallest original index per root
-    int* zc;                 // [Np] protons per cluster label
-    int* ac;                 // [Np] nucleons per cluster label
+    int* parent;             // [N] union-find over sorted slots (protons only for Sec. II.C)
+    int* minid;              // [N] smallest original index per root
+    int* zc;                 // [N] protons per cluster label
+    int* ac;                 // [N] nucleons per cluster label (per root in the MSTE pass)
     int* label;              // [N] label per sorted slot
     long long* hist_A;       // [N+1]
     long long* hist_Z;       // [Np+1]
@@ -58,5 +58,6 @@ void launch_set_clock(const EngineHost& H, cudaStream_t s, int only, const doubl
 void launch_set_rate(const EngineHost& H, cudaStream_t s, int only, double xi_dot);
 void launch_clusters(const EngineHost& H, cudaStream_t s, int only, int Np, int N, int Tp, int T,
                      int32_t* d_labels_out);
+void launch_mste(const EngineHost& H, cudaStream_t s, int only, int N, int T, int32_t* d_labels_out);
 
 }  // namespace pasta

@@ -154,6 +154,11 @@ int md_clusters(md_system* s, int32_t* labels, int64_t* hist_A, int64_t* hist_Z,
     return s->eng->clusters(s->idx, labels, hist_A, hist_Z, st);
 }
 
+int md_clusters_mste(md_system* s, int32_t* labels, int64_t* hist_A, int64_t* hist_Z, md_cluster_stats* st) {
+    GUARD(s);
+    return s->eng->clusters_mste(s->idx, labels, hist_A, hist_Z, st);
+}
+
 int md_get_state(md_system* s, md_state_view* v) {
     GUARD(s);
     if (!v) return fail(MD_EINVAL, "view is null");

@@ -92,6 +92,8 @@ _SIGS = {
     "md_step_energy": (ctypes.c_int, [_P, ctypes.POINTER(md_energy_t)]),
     "md_clusters": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                    ctypes.POINTER(md_cluster_stats)]),
+    "md_clusters_mste": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                        ctypes.POINTER(md_cluster_stats)]),
     "md_get_state": (ctypes.c_int, [_P, ctypes.POINTER(md_state_view)]),
     "md_set_state": (ctypes.c_int, [_P, ctypes.POINTER(md_state_view)]),
     "md_get_info": (ctypes.c_int, [_P, ctypes.POINTER(md_info_t)]),
@@ -226,15 +228,19 @@ def md_set_state(h, x, v, L, L_base=None, t=0.0, t_base=0.0, xi_dot=0.0, step=0,
     _ck(LIB.md_set_state(h, ctypes.byref(view)), "md_set_state")
 
 
-def md_clusters(h, N: int, Np: int, labels=True):
+def md_clusters(h, N: int, Np: int, labels=True, fn="md_clusters"):
     lab = np.empty(N, dtype=np.int32) if labels else None
     hA = np.zeros(N + 1, dtype=np.int64)
     hZ = np.zeros(Np + 1, dtype=np.int64)
     st = md_cluster_stats()
-    _ck(LIB.md_clusters(h, lab.ctypes.data_as(ctypes.POINTER(_I32)) if lab is not None else None,
-                        hA.ctypes.data_as(ctypes.POINTER(_I64)), hZ.ctypes.data_as(ctypes.POINTER(_I64)),
-                        ctypes.byref(st)), "md_clusters")
+    _ck(getattr(LIB, fn)(h, lab.ctypes.data_as(ctypes.POINTER(_I32)) if lab is not None else None,
+                         hA.ctypes.data_as(ctypes.POINTER(_I64)), hZ.ctypes.data_as(ctypes.POINTER(_I64)),
+                         ctypes.byref(st)), fn)
     return lab, hA, hZ, {k: getattr(st, k) for k, _ in md_cluster_stats._fields_}
+
+
+def md_clusters_mste(h, N: int, Np: int, labels=True):
+    return md_clusters(h, N, Np, labels, fn="md_clusters_mste")
 
 
 def md_clusters_noalloc(d_x, N, Np, L, r_pp, r_np, d_labels, d_hist_A, d_hist_Z, d_counts, stream=None) -> None:
@@ -394,6 +400,9 @@ class System:
 
     def clusters(self, labels=True):
         return md_clusters(self.h, self.N, self.Np, labels)
+
+    def clusters_mste(self, labels=True):
+        return md_clusters_mste(self.h, self.N, self.Np, labels)
 
     def info(self):
         return md_get_info(self.h)
