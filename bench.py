@@ -191,6 +191,18 @@ def run_gpu(args):
     kt = sys_.kernel_times()
     sys_.set_timing(False)
 
+    # energy-criterion (MSTE) clusters of the final state, timed on their own
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        flush.zero_()
+        ev0.record(stream)
+        _, _, _, mst = sys_.clusters_mste(labels=False)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    mste = {"ms": ev0.elapsed_time(ev1), "n_clusters": mst["n_clusters"], "n_big": mst["n_big"],
+            "m_free_n": mst["m_free_n"], "distance_clusters_n_big": cst["n_big"],
+            "note": "outside the timed region; bound when V_ij + (M/4)|v_i - v_j|^2 < 0"}
+
     # end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -263,6 +275,7 @@ def run_gpu(args):
         "step_ms_p50": sorted(step_ms)[len(step_ms) // 2],
         "step_ms_p99": sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)],
         "cluster_ms": cl_ms,
+        "mste": mste,
         "clusters": {"n": cst["n_clusters"], "m_free_n": cst["m_free_n"]},
         "gpu_launches": launches,
         "clocks": clk.summary(),
