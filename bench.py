@@ -361,7 +361,7 @@ def run_batch(steps):
         s.close()
     return {"systems": len(jobs), "nucleons": ntot, "steps": steps, "tuned_skin_fm": tuned_skin,
             "batched": ntot * steps / tb, "serial": ntot * steps / ts, "speedup": ts / tb,
-            "unit": "nucleon-steps/s", "graph_nodes_per_step": 16,
+            "unit": "nucleon-steps/s", "graph_nodes_per_step": 17,
             "note": "15 systems (Yp x T sweep), N from {4000,12800,25600,51200}, rho log-uniform "
                     "[0.00125, 0.08]; batched = one graph launch per step for all; serial = one system at a time"}
 

@@ -270,7 +270,6 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     A(&c.lcount, (size_t)s.T);
     A(&c.lnear, (size_t)s.T);
     A(&c.list, (size_t)c.list_cap);
-    A(&c.tile_e, 8 * (size_t)sys_items(s.T, s.Tp));
     A(&c.facc, 3 * (size_t)N);
     if (p.list_kind == 1) {
         c.vcap = verlet_capacity(N, s.Np, L0, s.T, p, rC);

@@ -115,13 +115,7 @@ __global__ void __launch_bounds__(kPW * 32) k_coulomb_pp_split(EngineDev E, int 
         double en = warp_sum(valid ? (double)ke.s - (double)ke.c : 0.0);
         double wv = warp_sum(valid ? (double)kw.s - (double)kw.c : 0.0);
         double cn = warp_sum(valid ? (double)nc : 0.0);
-        if (lane == 0) {
-            double* te = S.tile_e + 8 * item_index(S, I, 0);
-            te[1] = 0.5 * en;
-            te[2] += 0.5 * wv;
-            te[4] = 0.5 * cn;     // unique pairs
-            te[5] += 0.5 * (double)S.Np * kTile;
-        }
+        if (lane == 0) add_energy(st, 0.0, 0.5 * en, 0.5 * wv, 0, (long long)cn, (long long)S.Np * kTile);
     }
 }
 
@@ -190,12 +184,7 @@ __global__ void __launch_bounds__(kPW * 32) k_coulomb_pp_fp64(EngineDev E, int o
         en = warp_sum(valid ? en : 0.0);
         wv = warp_sum(valid ? wv : 0.0);
         const double cn = warp_sum(valid ? (double)nc : 0.0);
-        if (lane == 0) {
-            double* te = S.tile_e + 8 * item_index(S, I, 0);
-            te[1] = 0.5 * en;
-            te[2] += 0.5 * wv;
-            te[4] = 0.5 * cn;
-        }
+        if (lane == 0) add_energy(st, 0.0, 0.5 * en, 0.5 * wv, 0, (long long)cn, (long long)S.Np * kTile);
     }
 }
 

@@ -418,7 +418,7 @@ __device__ __forceinline__ void push(WarpQueues& Q, int q, bool pred, int& cnt, 
 // tile with the tile itself, a third of its Coulomb-only entries, or the
 // whole list of a neutron tile with the tile itself.
 template <bool kWrap, bool kEnergy>
-__device__ __forceinline__ void force_item(const SysConst& S, int v, WarpQueues& Q) {
+__device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, int v, WarpQueues& Q) {
     const int lane = threadIdx.x & 31;
     const int Pi = proton_items(S.Tp);
     int I, c;                      // c: -1 whole list, 0 near part, 1.. Coulomb-only part c
@@ -426,11 +426,7 @@ __device__ __forceinline__ void force_item(const SysConst& S, int v, WarpQueues&
         const int b = v / kItemGroup;
         I = (b / kPChunks) * kItemGroup + v % kItemGroup;
         c = b % kPChunks;
-        if (I >= S.Tp) {           // past the last proton tile of the group
-            if (kEnergy && lane == 0)
-                for (int k = 0; k < 6; ++k) S.tile_e[8 * v + k] = 0.0;
-            return;
-        }
+        if (I >= S.Tp) return;     // past the last proton tile of the group
     } else {
         I = S.Tp + (v - Pi);
         c = -1;
@@ -441,25 +437,25 @@ __device__ __forceinline__ void force_item(const SysConst& S, int v, WarpQueues&
     long long* facc = S.facc;
 
     PairConsts C;
-    C.rn2 = S.pf.rn2;
-    C.rc2 = S.pf.rc2;
-    C.kq = S.pf.kq;
-    C.A2 = S.pf.A2;
-    C.a = S.pf.a;
-    C.Ssame = S.pf.Ssame;
-    C.Scross = S.pf.Scross;
-    C.bsame = S.pf.bsame;
-    C.bcross = S.pf.bcross;
-    C.kc = S.pf.kc;
-    C.l2a = S.pf.l2a;
-    C.il = S.pf.il;
+    C.rn2 = P.rn2;
+    C.rc2 = P.rc2;
+    C.kq = P.kq;
+    C.A2 = P.A2;
+    C.a = P.a;
+    C.Ssame = P.Ssame;
+    C.Scross = P.Scross;
+    C.bsame = P.bsame;
+    C.bcross = P.bcross;
+    C.kc = P.kc;
+    C.l2a = P.l2a;
+    C.il = P.il;
     // L as an exact FP32 pair; 1/L only picks images (FP32 division)
     const float Lhi = __double2float_rn(L), Llo = __double2float_rn(L - (double)Lhi);
     C.Lhi = Lhi;
     C.Llo = Llo;
     C.iLf = 1.0f / Lhi;
     // source filter radii around I's box: cutoff + skin/2 (+ FP32 margin)
-    const float Rn2 = S.pf.Rn2, Rc2 = S.pf.Rc2;
+    const float Rn2 = P.Rn2, Rc2 = P.Rc2;
 
     const int p = tile_slot0(S, I) + lane;
     const int nv = tile_end(S, I) - tile_slot0(S, I);
@@ -616,20 +612,15 @@ __device__ __forceinline__ void force_item(const SysConst& S, int v, WarpQueues&
         const double wv = warp_sum_f(T.kw.s - T.kw.c);
         const int cn = __reduce_add_sync(0xffffffffu, 2 * T.nn + (valid ? T.nn2 : 0));   // twice the pairs
         const int cc = __reduce_add_sync(0xffffffffu, 2 * T.nc + (valid ? T.nc2 : 0));
-        if (lane == 0) {
-            double* te = S.tile_e + 8 * v;
-            te[0] = en;
-            te[1] = ec;
-            te[2] = wv;
-            te[3] = 0.5 * (double)cn;
-            te[4] = 0.5 * (double)cc;
-            te[5] = (double)T.cand;
-        }
+        if (lane == 0) add_energy(st, en, ec, wv, cn, cc, 2ll * T.cand);
     }
 }
 
-template <bool kEnergy>
-__global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS) k_force_split(EngineDev E, int only) {
+// kSingle: the engine holds one system, whose pair constants come in as a
+// kernel parameter (constant bank: operands without registers).
+template <bool kEnergy, bool kSingle>
+__global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS)
+    k_force_split(EngineDev E, int only, const __grid_constant__ PairF pf) {
     __shared__ WarpQueues qs[kForceWarps];
     const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
     if (g >= E.nitems) return;
@@ -640,8 +631,9 @@ __global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS) k_fo
     const int v = g - S.item_base;
     if (v >= S.n_items) return;
     WarpQueues& Q = qs[threadIdx.x >> 5];
-    if (S.st->need_wrap) force_item<true, kEnergy>(S, v, Q);
-    else force_item<false, kEnergy>(S, v, Q);
+    const PairF& P = kSingle ? pf : S.pf;
+    if (S.st->need_wrap) force_item<true, kEnergy>(S, P, v, Q);
+    else force_item<false, kEnergy>(S, P, v, Q);
 }
 
 // ---------------------------------------------------------------- Verlet
@@ -791,18 +783,7 @@ __device__ __forceinline__ void verlet_tile(const SysConst& S, int I, float (*re
         const double e_n = warp_sum_f(en), e_c = warp_sum_f(ec), w_v = warp_sum_f(wv);
         const int cn = __reduce_add_sync(0xffffffffu, tn), cc = __reduce_add_sync(0xffffffffu, tc);
         const int ca = __reduce_add_sync(0xffffffffu, cnt);
-        if (lane == 0) {
-            double* te = S.tile_e + 8 * item_index(S, I, 0);
-            te[0] = 0.5 * e_n;
-            te[1] = 0.5 * e_c;
-            te[2] = 0.5 * w_v;
-            te[3] = 0.5 * (double)cn;
-            te[4] = 0.5 * (double)cc;
-            te[5] = 0.5 * (double)ca;
-            if (Ip)
-                for (int c = 1; c < kPChunks; ++c)
-                    for (int k = 0; k < 6; ++k) S.tile_e[8 * item_index(S, I, c) + k] = 0.0;
-        }
+        if (lane == 0) add_energy(st, 0.5 * e_n, 0.5 * e_c, 0.5 * w_v, cn, cc, ca);
     }
 }
 
@@ -925,25 +906,27 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fp64(EngineDev E, in
         ec = warp_sum(valid ? ec : 0.0);
         wv = warp_sum(valid ? wv : 0.0);
         const double cn = warp_sum(valid ? (double)nn : 0.0), cc = warp_sum(valid ? (double)nc : 0.0);
-        if (lane == 0) {
-            double* te = S.tile_e + 8 * item_index(S, I, 0);
-            te[0] = 0.5 * en;
-            te[1] = 0.5 * ec;
-            te[2] = 0.5 * wv;
-            te[3] = 0.5 * cn;     // unique pairs
-            te[4] = 0.5 * cc;
-            te[5] = 0.5 * (double)(e1 - e0) * (kTile * kTile);
-            if (Ip)               // the other work items of a proton tile hold nothing here
-                for (int c = 1; c < kPChunks; ++c)
-                    for (int k = 0; k < 6; ++k) S.tile_e[8 * item_index(S, I, c) + k] = 0.0;
-        }
+        if (lane == 0)            // (ordered pairs: twice the pairs)
+            add_energy(st, 0.5 * en, 0.5 * ec, 0.5 * wv, (long long)cn, (long long)cc,
+                       (long long)(e1 - e0) * (kTile * kTile));
     }
 }
 
 }  // namespace
 
+// Clear the energy records before an energy pass.
+__global__ void k_ezero(EngineDev E, int only) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= E.nsys || (only >= 0 && s != only)) return;
+    for (int k = 0; k < 6; ++k) E.sys[s].st->eacc[k] = 0;
+}
+
 void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt) {
     const EngineDev& E = H.dev;
+    if (energy) {
+        k_ezero<<<(E.nsys + 127) / 128, 128, 0, s>>>(E, only);
+        H.count(1);
+    }
     const int nb = (E.ntiles + kForceWarps - 1) / kForceWarps;
     const int nbi = (E.nitems + kForceWarps - 1) / kForceWarps;
     H.rec("force", s);
@@ -952,8 +935,13 @@ void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, in
         else k_force_fp64<false><<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
         H.count(1);
     } else {
-        if (energy) k_force_split<true><<<nbi, kForceWarps * 32, 0, s>>>(E, only);
-        else k_force_split<false><<<nbi, kForceWarps * 32, 0, s>>>(E, only);
+        if (H.single) {
+            if (energy) k_force_split<true, true><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0);
+            else k_force_split<false, true><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0);
+        } else {
+            if (energy) k_force_split<true, false><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0);
+            else k_force_split<false, false><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0);
+        }
         if (H.any_verlet) {
             H.rec("force_verlet", s);
             if (energy) k_force_verlet<true><<<E.ntiles, kVW * 32, 0, s>>>(E, only);

@@ -301,31 +301,16 @@ __global__ void k_kick(EngineDev E) {
     block_sum4(S, v2, 0.0, 0.0, 0.0);
 }
 
-// One warp per system.  energy: also sum the per-tile PE partials.
+// One block per system.  energy: also record the energy pass's totals.
 __global__ void k_finalize(EngineDev E, int energy) {
     const int s = blockIdx.x;
     const SysConst& S = E.sys[s];
     SysState* st = S.st;
     const int lane = threadIdx.x;
     const double v2 = sys_sum(S, 0);
-    double pn = 0, pc = 0, w = 0, cn = 0, cc = 0, ca = 0;
-    if (energy) {
-        for (int t = lane; t < S.n_items; t += kRed) {
-            pn += S.tile_e[8 * t];
-            pc += S.tile_e[8 * t + 1];
-            w += S.tile_e[8 * t + 2];
-            cn += S.tile_e[8 * t + 3];
-            cc += S.tile_e[8 * t + 4];
-            ca += S.tile_e[8 * t + 5];
-        }
-        pn = block_sum(pn);
-        pc = block_sum(pc);
-        w = block_sum(w);
-        cn = block_sum(cn);
-        cc = block_sum(cc);
-        ca = block_sum(ca);
-    }
     if (lane != 0) return;
+    const double u = 1.0 / 4294967296.0;
+    const double pn = (double)st->eacc[0] * u, pc = (double)st->eacc[1] * u, w = (double)st->eacc[2] * u;
     const double Lf = st->L;
     st->L_F = Lf;
     st->t = __dadd_rn(st->t, S.dt);
@@ -347,15 +332,15 @@ __global__ void k_finalize(EngineDev E, int energy) {
         st->e_L = Lf;
         st->e_t = st->t;
         st->e_step = st->step;
-        st->e_pairs_nuc = (int64_t)cn;
-        st->e_pairs_coul = (int64_t)cc;
-        st->e_cand = (int64_t)ca;
+        st->e_pairs_nuc = st->eacc[3] / 2;
+        st->e_pairs_coul = st->eacc[4] / 2;
+        st->e_cand = st->eacc[5] / 2;
         st->have_energy = 1;
     }
 }
 
 // Energies at the current state (md_energy): KE from the block partials of
-// k_vsum(mode 1), PE from the tile partials of an energy force pass.
+// k_vsum(mode 1), PE from the record of an energy force pass.
 __global__ void k_energy_now(EngineDev E, int only, double* out) {
     const int s = blockIdx.x;
     if (only >= 0 && s != only) return;
@@ -363,29 +348,17 @@ __global__ void k_energy_now(EngineDev E, int only, double* out) {
     const SysState* st = S.st;
     const int lane = threadIdx.x;
     const double v2 = sys_sum(S, 0);
-    double pn = 0, pc = 0, w = 0, cn = 0, cc = 0;
-    for (int t = lane; t < S.n_items; t += kRed) {
-        pn += S.tile_e[8 * t];
-        pc += S.tile_e[8 * t + 1];
-        w += S.tile_e[8 * t + 2];
-        cn += S.tile_e[8 * t + 3];
-        cc += S.tile_e[8 * t + 4];
-    }
-    pn = block_sum(pn);
-    pc = block_sum(pc);
-    w = block_sum(w);
-    cn = block_sum(cn);
-    cc = block_sum(cc);
     if (lane == 0) {
+        const double u = 1.0 / 4294967296.0;
         out[0] = 0.5 * S.M * v2;
-        out[1] = pn;
-        out[2] = pc;
-        out[3] = w;
+        out[1] = (double)st->eacc[0] * u;
+        out[2] = (double)st->eacc[1] * u;
+        out[3] = (double)st->eacc[2] * u;
         out[4] = st->L;
         out[5] = st->t;
         out[6] = (double)st->step;
-        out[7] = cn;
-        out[8] = cc;
+        out[7] = (double)(st->eacc[3] / 2);
+        out[8] = (double)(st->eacc[4] / 2);
     }
 }
 

@@ -63,6 +63,10 @@ struct SysState {
     int pad0;
     unsigned long long vtop;     // Verlet list pool slots taken at the last rebuild
     unsigned long long vpairs;   // Verlet list entries written at the last rebuild
+    // energy record of the running force pass: PE_nuc, PE_coul, virial in
+    // 2^-32 MeV fixed point; twice the in-range nuclear / Coulomb pairs and
+    // twice the candidate pairs (cleared before each energy pass)
+    long long eacc[6];
 };
 
 // FP32 constants of the split-precision pair terms, computed on the host
@@ -117,7 +121,6 @@ struct SysConst {
     int* lcount;             // [T] entries per tile
     int* lnear;              // [T] of which near (written from the front of the region)
     int* list;               // [list_cap] tile-pair entries: J | kNucBit
-    double* tile_e;          // [n_items*8] per work item PE_nuc, PE_coul, virial, pair counts
     long long* facc;         // [3N] split precision: forces in 2^-32 MeV/fm fixed point
     // per-particle Verlet lists (list_kind 1): for tile t, lane l's k-th entry
     // is vlist[voff[t] + 32 k + l], k < vcount[32 t + l] <= vwidth[t]; an entry
@@ -172,6 +175,20 @@ __host__ __device__ inline int tile_slot0(const SysConst& s, int t) {
 }
 __host__ __device__ inline int tile_end(const SysConst& s, int t) {
     return t < s.Tp ? min(s.Np, (t + 1) * kTile) : min(s.N, s.Np + (t - s.Tp + 1) * kTile);
+}
+
+// Add a work unit's energies (FP64) and pair counts (twice the pairs) to the
+// system's energy record with integer atomics: the totals do not depend on
+// the order of the additions.
+__device__ inline void add_energy(SysState* st, double pe_nuc, double pe_coul, double vir, long long twice_nn,
+                                  long long twice_nc, long long twice_cand) {
+    const double k = 4294967296.0;
+    atomicAdd((unsigned long long*)&st->eacc[0], (unsigned long long)__double2ll_rn(pe_nuc * k));
+    atomicAdd((unsigned long long*)&st->eacc[1], (unsigned long long)__double2ll_rn(pe_coul * k));
+    atomicAdd((unsigned long long*)&st->eacc[2], (unsigned long long)__double2ll_rn(vir * k));
+    atomicAdd((unsigned long long*)&st->eacc[3], (unsigned long long)twice_nn);
+    atomicAdd((unsigned long long*)&st->eacc[4], (unsigned long long)twice_nc);
+    atomicAdd((unsigned long long*)&st->eacc[5], (unsigned long long)twice_cand);
 }
 
 // error-free a + b = s + e (FP32)
