@@ -173,10 +173,11 @@ constexpr int kQ = 2 * kTile;    // queue capacity
 #define PASTA_FORCE_STAGES 2
 #endif
 #ifndef PASTA_N3_UNROLL
-#define PASTA_N3_UNROLL 2
+#define PASTA_N3_UNROLL 4            // steps unrolled in a rotated block (per-pair wrap: half)
 #endif
 constexpr int kStages = PASTA_FORCE_STAGES;   // source tiles in flight per warp (cp.async)
 constexpr int kN3Unroll = PASTA_N3_UNROLL;    // unrolled steps of a rotated block
+constexpr int kN3UnrollWrap = (PASTA_N3_UNROLL + 1) / 2;   // longer bodies: keep the code in the i-cache
 constexpr double kUnfix = 1.0 / 4294967296.0;  // force accumulators count 2^-32 MeV/fm
 constexpr float kForceMax = 1.0e9f;          // |partial force| beyond this (MeV/fm) is an error
 
@@ -198,9 +199,15 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int kN>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(kN) : "memory"); }
 
+// A lane's sums over the blocks of a work item.  The forces are plain FP32
+// sums of block partials: a block partial carries the rounding of its 32
+// pair terms, and adding a few hundred partials (each a small fraction of the
+// total in the far Coulomb field) adds a relative error of order 1e-7 of the
+// largest partial, far below the 1e-5 force tolerance.  Energies, summed
+// over the whole system, are Kahan-compensated.
 struct Totals {
-    Kahan k0x, k0y, k0z;         // this lane's share of the force on target j = lane mod 16
-    Kahan k1x, k1y, k1z;         // ... and on target j + 16
+    float f0x = 0.f, f0y = 0.f, f0z = 0.f;   // this lane's share of the force on target j = lane mod 16
+    float f1x = 0.f, f1y = 0.f, f1z = 0.f;   // ... and on target j + 16
     Kahan ken, kec, kw;
     int nn = 0, nc = 0;          // unique in-range pairs of the rotated blocks
     int nn2 = 0, nc2 = 0;        // ordered in-range pairs of the tile with itself
@@ -324,8 +331,7 @@ __device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, c
     const float4* ph = Q.dh + 2 * half + j;
     const float4* pl = Q.dl + 2 * half + j;
     const int from = half | ((lane + 1) & 15);
-#pragma unroll kN3Unroll
-    for (int k = 0; k < 16; ++k) {
+    auto step = [&](int k) {
         const float4 q = ph[k];
         const float4 u = kLo ? pl[k] : q;
         const bool sv = kFull || ((half | ((j + k) & 15)) < n);
@@ -340,6 +346,13 @@ __device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, c
         rx = __shfl_sync(0xffffffffu, fmaf(-fr1, dx, rx), from);
         ry = __shfl_sync(0xffffffffu, fmaf(-fr1, dy, ry), from);
         rz = __shfl_sync(0xffffffffu, fmaf(-fr1, dz, rz), from);
+    };
+    if (kWrap) {
+#pragma unroll kN3UnrollWrap
+        for (int k = 0; k < 16; ++k) step(k);
+    } else {
+#pragma unroll kN3Unroll
+        for (int k = 0; k < 16; ++k) step(k);
     }
     if (kFull || (half | j) < n) {
         const int slot = __float_as_int(ph[0].w);
@@ -348,12 +361,12 @@ __device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, c
         red_add(facc + N + slot, to_fix(ry));
         red_add(facc + 2 * N + slot, to_fix(rz));
     }
-    T.k0x.add(f0x);
-    T.k0y.add(f0y);
-    T.k0z.add(f0z);
-    T.k1x.add(f1x);
-    T.k1y.add(f1y);
-    T.k1z.add(f1z);
+    T.f0x += f0x;
+    T.f0y += f0y;
+    T.f0z += f0z;
+    T.f1x += f1x;
+    T.f1y += f1y;
+    T.f1z += f1z;
     if (kEnergy) {
         T.ken.add(e.en);
         T.kec.add(e.ec);
@@ -587,8 +600,8 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
     // Target l = j + 16 (l >> 4): this lane's share plus its partner's
     // (lane l ^ 16 holds the same two targets), plus the tile's own pairs.
     const bool upper = (lane & 16) != 0;
-    const float m0x = T.k0x.s - T.k0x.c, m0y = T.k0y.s - T.k0y.c, m0z = T.k0z.s - T.k0z.c;
-    const float m1x = T.k1x.s - T.k1x.c, m1y = T.k1y.s - T.k1y.c, m1z = T.k1z.s - T.k1z.c;
+    const float m0x = T.f0x, m0y = T.f0y, m0z = T.f0z;
+    const float m1x = T.f1x, m1y = T.f1y, m1z = T.f1z;
     const float ox = __shfl_xor_sync(0xffffffffu, upper ? m0x : m1x, 16);
     const float oy = __shfl_xor_sync(0xffffffffu, upper ? m0y : m1y, 16);
     const float oz = __shfl_xor_sync(0xffffffffu, upper ? m0z : m1z, 16);
