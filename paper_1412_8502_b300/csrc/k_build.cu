@@ -94,6 +94,36 @@ __device__ inline unsigned block_exscan(unsigned v, unsigned* sm /*32*/, unsigne
 
 __device__ inline bool sys_rebuilds(const SysConst& S) { return S.st->rebuild != 0; }
 
+// Order-preserving integer keys: a < b exactly when key(a) < key(b).
+__device__ __forceinline__ unsigned long long dkey(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+    const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ unsigned fkey(float v) {
+    const unsigned b = __float_as_uint(v);
+    return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned k) {
+    return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Bounds lo <= min and hi >= max of v over the valid lanes of the warp from
+// one 32-bit integer reduction each on the high words of the keys (no FP64
+// arithmetic): the bounds are the doubles at the ends of the high-word
+// intervals, within 2^-20 of the true extremes relative to their magnitude.
+// At least one lane must be valid.
+__device__ __forceinline__ void warp_bounds(double v, bool valid, double& lo, double& hi) {
+    const unsigned k = (unsigned)(dkey(v) >> 32);
+    const unsigned kmin = __reduce_min_sync(0xffffffffu, valid ? k : 0xffffffffu);
+    const unsigned kmax = __reduce_max_sync(0xffffffffu, valid ? k : 0u);
+    lo = dkey_inv((unsigned long long)kmin << 32);
+    hi = dkey_inv(((unsigned long long)kmax << 32) | 0xffffffffull);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- decision
@@ -155,13 +185,38 @@ __global__ void k_hist(EngineDev E) {
 constexpr int kScanPer = 8;
 constexpr int kScanChunk = 1024 * kScanPer;
 
+static_assert(kScanPer == 8, "a thread's bins are two 16-byte vectors");
+
+// The 8 bins of a thread from base: two 16-byte loads (bases are multiples
+// of 8 bins; the allocation is 256-byte aligned), element loads at the tail.
+__device__ __forceinline__ void load8(const unsigned* a, long long base, long long n, unsigned (&v)[kScanPer]) {
+    if (base + kScanPer <= n) {
+        const uint4 p = *reinterpret_cast<const uint4*>(a + base);
+        const uint4 q = *reinterpret_cast<const uint4*>(a + base + 4);
+        v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
+        v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+    } else {
+        for (int k = 0; k < kScanPer; ++k) v[k] = (base + k < n) ? a[base + k] : 0u;
+    }
+}
+__device__ __forceinline__ void store8(unsigned* a, long long base, long long n, const unsigned (&v)[kScanPer]) {
+    if (base + kScanPer <= n) {
+        *reinterpret_cast<uint4*>(a + base) = make_uint4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<uint4*>(a + base + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+    } else {
+        for (int k = 0; k < kScanPer; ++k)
+            if (base + k < n) a[base + k] = v[k];
+    }
+}
+
 __global__ void k_scan_reduce(EngineDev E) {
     if (!*E.any_rebuild) return;
     __shared__ unsigned sm[33];
     const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    unsigned v[kScanPer];
+    load8(E.hist, base, E.nbins_total, v);
     unsigned s = 0;
-    for (int k = 0; k < kScanPer; ++k)
-        if (base + k < E.nbins_total) s += E.hist[base + k];
+    for (int k = 0; k < kScanPer; ++k) s += v[k];
     unsigned tot;
     block_exscan(s, sm, &tot);
     if (threadIdx.x == 0) E.blocksum[blockIdx.x] = tot;
@@ -189,18 +244,17 @@ __global__ void k_scan_down(EngineDev E) {
     __shared__ unsigned sm[33];
     const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
     unsigned v[kScanPer];
+    load8(E.hist, base, E.nbins_total, v);
     unsigned s = 0;
-    for (int k = 0; k < kScanPer; ++k) {
-        v[k] = (base + k < E.nbins_total) ? E.hist[base + k] : 0u;
-        s += v[k];
-    }
+    for (int k = 0; k < kScanPer; ++k) s += v[k];
     unsigned run = block_exscan(s, sm, nullptr) + E.blocksum[blockIdx.x];
-    for (int k = 0; k < kScanPer; ++k)
-        if (base + k < E.nbins_total) {
-            E.binstart[base + k] = run;
-            E.cursor[base + k] = run;
-            run += v[k];
-        }
+    unsigned o[kScanPer];
+    for (int k = 0; k < kScanPer; ++k) {
+        o[k] = run;
+        run += v[k];
+    }
+    store8(E.binstart, base, E.nbins_total, o);
+    store8(E.cursor, base, E.nbins_total, o);
 }
 
 // ---------------------------------------------------------------- scatter
@@ -304,8 +358,8 @@ __global__ void k_tiles(EngineDev E) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         xv[a] = valid ? x[a * N + p] : 0.0;
-        const double lo = warp_min(valid ? xv[a] : 1e300);
-        const double hi = warp_max(valid ? xv[a] : -1e300);
+        double lo, hi;
+        warp_bounds(xv[a], valid, lo, hi);
         c[a] = 0.5 * (lo + hi);
         h[a] = 0.5 * (hi - lo);
     }
@@ -429,7 +483,8 @@ __device__ inline int list_entry(const SysConst& S, int I, int J, const float4& 
 }
 
 // Boxes of super-tiles (32 consecutive tiles, compact in Hilbert order):
-// one thread each, union of the member tiles' boxes.
+// one warp each, lane k taking member tile 32 s + k; the union of the member
+// boxes from exact integer min / max reductions of the FP32 box faces.
 __global__ void k_super(EngineDev E) {
     if (!*E.any_rebuild) return;
     const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
@@ -439,16 +494,18 @@ __global__ void k_super(EngineDev E) {
     if (s < 0) return;
     const SysConst& S = E.sys[s];
     if (!sys_rebuilds(S)) return;
-    const int I = g - S.tile_base;           // one warp per tile; lane 0 of every 32nd tile works
-    if (I >= S.T || (I % kTile) != 0 || lane != 0) return;
-    const int t1 = min(S.T, I + kTile);
-    float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
-    for (int t = I; t < t1; ++t)
-        for (int a = 0; a < 3; ++a) {
-            const float c = S.torgf[4 * t + a], h = S.thalf[3 * t + a];
-            lo[a] = fminf(lo[a], c - h);
-            hi[a] = fmaxf(hi[a], c + h);
-        }
+    const int I = g - S.tile_base;           // one warp per tile; the warp of every 32nd tile works
+    if (I >= S.T || (I % kTile) != 0) return;
+    const int t = I + lane;
+    const bool member = t < S.T;
+    float lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float c = member ? S.torgf[4 * t + a] : 0.0f, h = member ? S.thalf[3 * t + a] : 0.0f;
+        lo[a] = fkey_inv(__reduce_min_sync(0xffffffffu, member ? fkey(c - h) : 0xffffffffu));
+        hi[a] = fkey_inv(__reduce_max_sync(0xffffffffu, member ? fkey(c + h) : 0u));
+    }
+    if (lane != 0) return;
     // half extents rounded up, as for tiles
     S.sorg[I / kTile] = make_float4(0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2]), 0.f);
     S.shalf[I / kTile] = make_float4(0.5f * (hi[0] - lo[0]) * (1.0f + 1e-6f) + 1e-4f,
@@ -496,6 +553,7 @@ __global__ void k_lbuild(EngineDev E, int half) {
     int out = 0, outf = 0;         // near entries from the front, Coulomb-only from the back
     const int nsup = (S.T + kTile - 1) / kTile;
     const float R2max = fmaxf(T.R2same, T.R2cross);
+    const bool paired = half && S.list_kind == 0;
     for (int s0 = 0; s0 < nsup; s0 += 32) {
         const int sg = s0 + lane;
         bool pass = false;
@@ -514,10 +572,29 @@ __global__ void k_lbuild(EngineDev E, int half) {
         }
         unsigned sm = __ballot_sync(0xffffffffu, pass);
         while (sm) {
-            const int b = __ffs(sm) - 1;
-            sm &= sm - 1;
-            const int J = (s0 + b) * kTile + lane;
-            const int e = (J < S.T && owns_pair(I, J, half && S.list_kind == 0)) ? list_entry(S, I, J, oI, hI, T) : -1;
+            int J;
+            if (paired) {
+                // Half lists: of two consecutive tiles 2m, 2m + 1 I owns at
+                // most one, so a lane takes the owned tile of a pair and the
+                // warp covers two super-tiles (half-warps) per round.
+                const int b0 = __ffs(sm) - 1;
+                sm &= sm - 1;
+                const int b1 = sm ? __ffs(sm) - 1 : -1;
+                if (b1 >= 0) sm &= sm - 1;
+                const int b = (lane < 16) ? b0 : b1;
+                J = -1;
+                if (b >= 0) {
+                    const int Ja = (s0 + b) * kTile + 2 * (lane & 15);
+                    if (Ja < S.T && owns_pair(I, Ja, 1)) J = Ja;
+                    else if (Ja + 1 < S.T && owns_pair(I, Ja + 1, 1)) J = Ja + 1;
+                }
+            } else {
+                const int b = __ffs(sm) - 1;
+                sm &= sm - 1;
+                J = (s0 + b) * kTile + lane;
+                if (J >= S.T) J = -1;
+            }
+            const int e = J >= 0 ? list_entry(S, I, J, oI, hI, T) : -1;
             const bool near = e >= 0 && (e & kNucBit);
             const unsigned mn = __ballot_sync(0xffffffffu, near);
             const unsigned mf = __ballot_sync(0xffffffffu, e >= 0 && !near);

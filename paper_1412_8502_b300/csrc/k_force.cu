@@ -178,7 +178,7 @@ constexpr int kQ = 2 * kTile;    // queue capacity
 constexpr int kStages = PASTA_FORCE_STAGES;   // source tiles in flight per warp (cp.async)
 constexpr int kN3Unroll = PASTA_N3_UNROLL;    // unrolled steps of a rotated block
 constexpr int kN3UnrollWrap = (PASTA_N3_UNROLL + 1) / 2;   // longer bodies: keep the code in the i-cache
-constexpr double kUnfix = 1.0 / 4294967296.0;  // force accumulators count 2^-32 MeV/fm
+constexpr float kUnfixF = 1.0f / 4294967296.0f;   // force accumulators count 2^-32 MeV/fm
 constexpr float kForceMax = 1.0e9f;          // |partial force| beyond this (MeV/fm) is an error
 
 struct WarpQueues {
@@ -828,13 +828,18 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fix(EngineDev E, int
     const int p = tile_slot0(S, I) + (threadIdx.x & 31);
     if (p >= tile_end(S, I)) return;
     const SysState* st = S.st;
-    float* F = S.f32[out_alt ? (st->cur ^ 1) : st->cur];
     const int N = S.N;
+    // all loads first (the stores below may not be ordered before them)
+    long long v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = S.facc[c * N + p];
+    float* F = S.f32[out_alt ? (st->cur ^ 1) : st->cur];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const long long v = S.facc[c * N + p];
         S.facc[c * N + p] = 0;
-        F[c * N + p] = (float)((double)v * kUnfix);
+        // one rounding of v to FP32 (|v| < 2^53: the same value as rounding
+        // v 2^-32 from FP64), then an exact power-of-two scale
+        F[c * N + p] = __ll2float_rn(v[c]) * kUnfixF;
     }
 }
 

@@ -66,6 +66,20 @@ __device__ inline void block_sum4(const SysConst& S, double a, double b, double 
     }
 }
 
+// Fixed-order block sum of one double into S.blk[blockIdx * 4].
+__device__ inline void block_sum1(const SysConst& S, double a) {
+    __shared__ double sm1[kTilesPerBlock];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    a = warp_sum(a);
+    if (lane == 0) sm1[w] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int k = 0; k < kTilesPerBlock; ++k) r += sm1[k];
+        S.blk[4 * sys_block(S)] = r;
+    }
+}
+
 __device__ inline uint64_t splitmix64(uint64_t seed, uint64_t k) {
     uint64_t z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -298,7 +312,7 @@ __global__ void k_kick(EngineDev E) {
             v2 += v * v;
         }
     }
-    block_sum4(S, v2, 0.0, 0.0, 0.0);
+    block_sum1(S, v2);
 }
 
 // One block per system.  energy: also record the energy pass's totals.
