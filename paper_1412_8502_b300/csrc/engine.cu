@@ -293,6 +293,8 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     c.cl = s.d_cl;
     c.dt = p.dt;
     c.M = 939.0;
+    c.hkick = 0.5 * c.dt / c.M;
+    c.dtf = (float)c.dt;
     c.T_target = T;
     c.skin = p.skin;
     c.a = 110.0;
@@ -421,7 +423,7 @@ int Engine::initialise() {
     return check_errors();
 }
 
-int Engine::initialise_async() {
+int Engine::initialise_async(bool relax) {
     std::vector<unsigned long long> seeds;
     for (SysHost* h : sys) seeds.push_back(h->seed);
     CK(cudaMemcpyAsync(d_seeds_, seeds.data(), sizeof(unsigned long long) * seeds.size(), cudaMemcpyHostToDevice,
@@ -430,13 +432,20 @@ int Engine::initialise_async() {
     CK(cudaGetLastError());
     int rc = refresh(-1);
     if (rc) return rc;
+    return relax ? relax_async(relax_iters()) : MD_OK;
+}
+
+int64_t Engine::relax_iters() const {
     int64_t iters = 0;
-    for (SysHost* h : sys) iters = std::max(iters, h->prm.relax_iters);
-    if (iters > 0) {
-        if (!g_relax_.exec && (rc = capture(g_relax_, 1, false))) return rc;
-        for (int64_t k = 0; k < iters; ++k)
-            if ((rc = run_graph(g_relax_))) return rc;
-    }
+    for (const SysHost* h : sys) iters = std::max(iters, h->prm.relax_iters);
+    return iters;
+}
+
+int Engine::relax_async(int64_t n) {
+    int rc;
+    if (n > 0 && !g_relax_.exec && (rc = capture(g_relax_, 1, false))) return rc;
+    for (int64_t k = 0; k < n; ++k)
+        if ((rc = run_graph(g_relax_))) return rc;
     return MD_OK;
 }
 
@@ -825,6 +834,8 @@ int Engine::set_params(int idx, const md_params& p) {
     if (p.lambda_s == 0.0) h.prm.lambda_s = lambda_thomas_fermi((double)h.Np / (h.L0 * h.L0 * h.L0));
     SysConst& c = h.c;
     c.dt = p.dt;
+    c.hkick = 0.5 * c.dt / c.M;
+    c.dtf = (float)c.dt;
     c.T_target = p.T;
     c.skin = p.skin;
     c.lambda_s = h.prm.lambda_s;

@@ -55,7 +55,12 @@ public:
     // Seed, relax and evaluate forces of all systems (creation path).
     int initialise();
     // Same, only enqueued on the engine's stream (no synchronisation).
-    int initialise_async();
+    // relax = false leaves the relaxation iterations to relax_async.
+    int initialise_async(bool relax = true);
+    // Enqueue n steepest-descent relaxation iterations (serving: in slices).
+    int relax_async(int64_t n);
+    // Relaxation iterations the systems ask for (the largest relax_iters).
+    int64_t relax_iters() const;
     // Release a system's device memory and drop it from the engine.
     void remove_system(int idx);
 

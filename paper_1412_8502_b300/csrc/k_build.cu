@@ -54,12 +54,15 @@ __device__ inline unsigned hilbert_key(unsigned qx, unsigned qy, unsigned qz, in
     return h;
 }
 
+// Bin of a position in [0, L): FP32 arithmetic on the truncated position (a
+// bin choice near a bin face is as good as the other; every later step uses
+// the stored key).
 __device__ inline unsigned sort_key(const SysConst& S, double x, double y, double z, double L) {
     const int n = 1 << S.nbits;
-    const double sc = (double)n / L;
-    const int qx = min(max((int)(x * sc), 0), n - 1);
-    const int qy = min(max((int)(y * sc), 0), n - 1);
-    const int qz = min(max((int)(z * sc), 0), n - 1);
+    const float sc = (float)n / narrow_trunc(L);
+    const int qx = min(max((int)(narrow_trunc(x) * sc), 0), n - 1);
+    const int qy = min(max((int)(narrow_trunc(y) * sc), 0), n - 1);
+    const int qz = min(max((int)(narrow_trunc(z) * sc), 0), n - 1);
     return hilbert_key((unsigned)qx, (unsigned)qy, (unsigned)qz, S.nbits);
 }
 
@@ -353,21 +356,25 @@ __global__ void k_tiles(EngineDev E) {
     const int cn = st->cur_next;
     const int N = S.N;
     const double* x = S.x[cn];
-    double c[3], h[3];
+    double c[3] = {0.0, 0.0, 0.0}, h[3] = {0.0, 0.0, 0.0};
     double xv[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         xv[a] = valid ? x[a * N + p] : 0.0;
         double lo, hi;
         warp_bounds(xv[a], valid, lo, hi);
-        c[a] = 0.5 * (lo + hi);
-        h[a] = 0.5 * (hi - lo);
+        if (lane == 0) {                 // FP64 arithmetic on one lane only
+            c[a] = 0.5 * (lo + hi);
+            h[a] = 0.5 * (hi - lo);
+        }
     }
     const double L = st->L;
     if (lane == 0)
         for (int a = 0; a < 3; ++a) S.torg[3 * t + a] = c[a];
-    __syncwarp();
-    write_xt(S, t, lane, xv, L, valid);
+    // The box is that of the wrapped positions themselves (a Hilbert run of
+    // [0, L)^3 does not wrap), so every position is within h <= L/2 of the
+    // origin and is its own image nearest the origin.
+    store_xt(S, t, lane, xv, valid);
     if (valid) {
         S.disp[p] = 0.0f;
         S.disp[N + p] = 0.0f;

@@ -90,6 +90,9 @@ __device__ inline double u01(uint64_t seed, uint64_t k) {
     return __dmul_rn((double)(splitmix64(seed, k) >> 11), 0x1.0p-53);
 }
 
+__device__ __forceinline__ double to_double(float f) { return widen(f); }
+__device__ __forceinline__ double to_double(double f) { return f; }
+
 template <typename FT>
 __device__ inline const FT* cur_force(const SysConst& S, int cur);
 template <>
@@ -219,6 +222,7 @@ __global__ void k_rescale(EngineDev E, int only) {
         S.v[c][2 * N + p] *= f;
     }
     if (g != 1.0) {
+        const float4 prev = S.xhi[o.t * kTile + (threadIdx.x & 31)];
         double xs[3];
         for (int a = 0; a < 3; ++a) {
             const double x0 = S.x[c][a * N + p];
@@ -226,7 +230,7 @@ __global__ void k_rescale(EngineDev E, int only) {
             S.x[c][a * N + p] = xs[a];
             S.disp[a * N + p] += (float)(xs[a] - x0);
         }
-        write_xt(S, o.t, threadIdx.x & 31, xs, st->L, true);
+        write_xt_moved(S, o.t, threadIdx.x & 31, xs, st->L, narrow_trunc(st->L), prev);
     }
 }
 
@@ -245,22 +249,23 @@ __global__ void k_sd_update(EngineDev E) {
         const int c = st->cur, N = S.N, p = o.p;
         const FT* F = cur_force<FT>(S, c);
         double d[3];
-        for (int a = 0; a < 3; ++a) d[a] = S.relax_gamma * (double)F[a * N + p];
+        for (int a = 0; a < 3; ++a) d[a] = S.relax_gamma * to_double(F[a * N + p]);
         const double m = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         if (m > S.relax_dmax) {
             const double sc = S.relax_dmax / m;
             for (int a = 0; a < 3; ++a) d[a] *= sc;
         }
         const double L = st->L;
+        const float4 prev = S.xhi[o.t * kTile + lane];
         double xs[3];
         for (int a = 0; a < 3; ++a) {
-            xs[a] = wrap_box(S.x[c][a * N + p] + d[a], L);
+            xs[a] = wrap_box_bits(S.x[c][a * N + p] + d[a], L);
             S.x[c][a * N + p] = xs[a];
-            const float dd = S.disp[a * N + p] + (float)d[a];
+            const float dd = S.disp[a * N + p] + narrow_trunc(d[a]);
             S.disp[a * N + p] = dd;
             d2 = fmaf(dd, dd, d2);
         }
-        write_xt(S, o.t, lane, xs, L, true);
+        write_xt_moved(S, o.t, lane, xs, L, narrow_trunc(L), prev);
     }
     d2 = warp_max(d2);
     block_atomic_max(&st->maxdisp2, d2);
@@ -278,18 +283,20 @@ __global__ void k_kick_drift(EngineDev E) {
     if (o.valid) {
         const int c = st->cur, N = S.N, p = o.p;
         const FT* F = cur_force<FT>(S, c);
-        const double h = 0.5 * S.dt / S.M, dt = S.dt, L = st->L;
+        const double h = S.hkick, dt = S.dt, L = st->L;
+        const float4 prev = S.xhi[o.t * kTile + lane];
         double xs[3];
         for (int a = 0; a < 3; ++a) {
-            const double v = S.v[c][a * N + p] + h * (double)F[a * N + p];
+            const double v = fma(h, to_double(F[a * N + p]), S.v[c][a * N + p]);
             S.v[c][a * N + p] = v;
-            xs[a] = wrap_box(S.x[c][a * N + p] + dt * v, L);
+            xs[a] = wrap_box_bits(fma(dt, v, S.x[c][a * N + p]), L);
             S.x[c][a * N + p] = xs[a];
-            const float dd = S.disp[a * N + p] + (float)(dt * v);
+            // displacement estimate in FP32 (the list margin covers its rounding)
+            const float dd = fmaf(S.dtf, narrow_trunc(v), S.disp[a * N + p]);
             S.disp[a * N + p] = dd;
             d2 = fmaf(dd, dd, d2);
         }
-        write_xt(S, o.t, lane, xs, L, true);
+        write_xt_moved(S, o.t, lane, xs, L, narrow_trunc(L), prev);
     }
     d2 = warp_max(d2);
     block_atomic_max(&st->maxdisp2, d2);
@@ -305,11 +312,11 @@ __global__ void k_kick(EngineDev E) {
     if (o.valid) {
         const int c = st->cur, N = S.N, p = o.p;
         const FT* F = cur_force<FT>(S, c);
-        const double h = 0.5 * S.dt / S.M;
+        const double h = S.hkick;
         for (int a = 0; a < 3; ++a) {
-            const double v = S.v[c][a * N + p] + h * (double)F[a * N + p];
+            const double v = fma(h, to_double(F[a * N + p]), S.v[c][a * N + p]);
             S.v[c][a * N + p] = v;
-            v2 += v * v;
+            v2 = fma(v, v, v2);
         }
     }
     block_sum1(S, v2);

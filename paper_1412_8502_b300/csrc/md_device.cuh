@@ -98,6 +98,8 @@ struct SysConst {
     double dt, M, T_target, skin;
     double a, b, c, Lambda, lambda_s, alpha, r_nuc, r_C;
     double r_pp, r_np, relax_gamma, relax_dmax;
+    double hkick;            // dt / (2 M): velocity Verlet half kick per unit force
+    float dtf;               // dt in FP32 (displacement estimates)
     int thermostat_every, rebuild_every, coulomb, energy_every;
     int affine;              // scale positions with the box (option, not the paper)
     int list_kind;           // 0 half tile-pair lists, 1 per-particle Verlet lists
@@ -229,6 +231,53 @@ __device__ inline double min_image(double d, double L, double hL) {
     return d;
 }
 
+// ---- FP64 state without the FP64 pipe.  On this part FP64 arithmetic and
+// every conversion to or from a 64-bit type issue at about 1/64 of the FP32
+// rate, so the exact format work around the FP64 state (widening the FP32
+// forces, splitting positions into FP32 pairs, range tests) is done with
+// integer operations on the IEEE-754 bit patterns.
+
+// Exact (double)f.  Zero and normal f on the integer path; subnormal, inf
+// and NaN through the converter.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned a = b & 0x7fffffffu;
+    const bool normal = (a - 0x00800000u) < 0x7f000000u;
+    if (!normal && a != 0u) return (double)f;
+    const unsigned long long mag = normal ? ((unsigned long long)a << 29) + (896ull << 52) : 0ull;
+    return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) | mag));
+}
+
+// d truncated to FP32 (|result| <= |d|, relative error below 2^-23) for d
+// in the normal FP32 range or zero; other values through the converter.
+__device__ __forceinline__ float narrow_trunc(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned h = (unsigned)(b >> 32);
+    const unsigned e = (h >> 20) & 0x7ffu;
+    if (e == 0u && (b << 1) == 0ull) return __uint_as_float(h & 0x80000000u);
+    if (e - 897u >= 254u) return (float)d;
+    return __uint_as_float((h & 0x80000000u) | ((e - 896u) << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
+}
+
+// x = hi + lo: hi is x truncated to 24 significant bits, lo the remaining
+// 29 bits of the significand rounded to FP32 (|x - hi - lo| <= 2^-48 |x|),
+// from integer operations for 2^-74 <= |x| < 2^127; other x (zero
+// included) through the converter as hi = fp32(x), lo = fp32(x - hi).
+__device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned h = (unsigned)(b >> 32);
+    const unsigned e = (h >> 20) & 0x7ffu;
+    if (e - 949u >= 201u) {
+        hi = (float)x;
+        lo = (float)(x - (double)hi);
+        return;
+    }
+    const unsigned s = h & 0x80000000u;
+    hi = __uint_as_float(s | ((e - 896u) << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
+    // the low 29 bits weigh 2^(e - 1075) each
+    lo = (float)((unsigned)b & 0x1fffffffu) * __uint_as_float(s | ((e - 948u) << 23));
+}
+
 __device__ inline float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -250,32 +299,47 @@ __device__ inline float warp_max(float v) {
     return v;
 }
 
-// Store slot (t, lane)'s position as hi + lo FP32 pair of its image nearest
-// the tile origin (empty slots: far away, zero low part).  h.w carries the
-// particle's slot index (bit pattern of an int; -1 for an empty slot).
-__device__ inline void write_xt(const SysConst& s, int t, int lane, const double* xs, double L, bool valid) {
+// Store slot (t, lane)'s tile-frame position xt as the FP32 pair hi + lo
+// (empty slots: far away, zero low part).  h.w carries the particle's slot
+// index (bit pattern of an int; -1 for an empty slot).
+__device__ inline void store_xt(const SysConst& s, int t, int lane, const double* xt, bool valid) {
     float4 h, l;
     h.w = __int_as_float(valid ? tile_slot0(s, t) + lane : -1);
     l.w = 0.0f;
     if (valid) {
-        const double hL = 0.5 * L;
-        double xt[3];
-        for (int a = 0; a < 3; ++a) {
-            const double o = s.torg[3 * t + a];
-            xt[a] = o + min_image(xs[a] - o, L, hL);
-        }
-        h.x = (float)xt[0];
-        h.y = (float)xt[1];
-        h.z = (float)xt[2];
-        l.x = (float)(xt[0] - (double)h.x);
-        l.y = (float)(xt[1] - (double)h.y);
-        l.z = (float)(xt[2] - (double)h.z);
+        split_hilo(xt[0], h.x, l.x);
+        split_hilo(xt[1], h.y, l.y);
+        split_hilo(xt[2], h.z, l.z);
     } else {
         h.x = h.y = h.z = kPad;
         l.x = l.y = l.z = 0.0f;
     }
     s.xhi[t * kTile + lane] = h;
     s.xlo[t * kTile + lane] = l;
+}
+
+// A particle that moved (by much less than L/2) since its tile-frame
+// position was last stored: its new image is the one next to the previous
+// one, i.e. xs itself unless the particle crossed a face of the box since
+// the last rebuild (then xs - k L, k = +-1, in FP64).  prev: the stored
+// high parts; Lf: L truncated to FP32.
+__device__ inline void write_xt_moved(const SysConst& s, int t, int lane, const double* xs, double L, float Lf,
+                                      const float4& prev) {
+    double xt[3] = {xs[0], xs[1], xs[2]};
+    const float pv[3] = {prev.x, prev.y, prev.z};
+    for (int a = 0; a < 3; ++a) {
+        const float d = narrow_trunc(xs[a]) - pv[a];
+        if (fabsf(d) > 0.5f * Lf) xt[a] = xs[a] - L * (double)rintf(d / Lf);
+    }
+    store_xt(s, t, lane, xt, true);
+}
+
+// xs wrapped into [0, L) (x >= L: x - L; x < 0: x + L, or 0 if that rounds
+// to L), the common in-range case decided on the bit patterns.
+__device__ __forceinline__ double wrap_box_bits(double x, double L) {
+    const long long xb = __double_as_longlong(x);
+    if (xb >= 0 && xb < __double_as_longlong(L)) return x;    // 0 <= x < L (L > 0)
+    return wrap_box(x, L);
 }
 
 // Block-level max of a non-negative float (one value per warp, lane 0

@@ -8,9 +8,13 @@
 // job's completion event and enqueues the job's next slice as soon as the
 // previous one is done, so every job's stream stays busy and the jobs'
 // kernels overlap on the device.  Per-step latencies come from events on the
-// job's stream.  Finished jobs are retired (their memory freed) and waiting
-// ones admitted.  A job's trajectory does not depend on the other jobs: each
-// runs the same deterministic kernels as it would alone.
+// job's stream.  Finished jobs are retired and waiting ones admitted.  A
+// retired job's device memory is released only when the server is idle or
+// when a waiting job needs the room: freeing device memory waits for the
+// whole device, which would drain every other job's queued work and leave
+// the GPU idle until the worker refills it.  A job's trajectory does not
+// depend on the other jobs: each runs the same deterministic kernels as it
+// would alone.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -42,6 +46,7 @@ struct Job {
     cudaEvent_t done = nullptr;
     int state = kInit;
     int64_t slice = 0;
+    int64_t relax_left = 0;      // relaxation iterations not yet enqueued
 };
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
@@ -65,6 +70,7 @@ struct md_server {
     std::condition_variable cv;
     std::deque<Job*> pending;
     std::vector<Job*> active;
+    std::vector<std::pair<Engine*, size_t>> retired;   // engines whose memory is still held
     std::deque<md_result> done;
     int64_t next_id = 0, submitted = 0, finished = 0;
     size_t used = 0;
@@ -75,7 +81,21 @@ struct md_server {
     void run();
     void admit();
     void retire(Job* j, int status);
+    void release_retired();
 };
+
+void md_server::release_retired() {
+    size_t freed = 0;
+    for (auto& e : retired) {
+        delete e.first;
+        freed += e.second;
+    }
+    retired.clear();
+    if (freed) {
+        std::lock_guard<std::mutex> lk(mu);
+        used -= freed;
+    }
+}
 
 void md_server::retire(Job* j, int status) {
     md_result r{};
@@ -96,10 +116,11 @@ void md_server::retire(Job* j, int status) {
     r.step_p99_ms = pct(j->lat_ms, 0.99);
     for (cudaEvent_t e : j->ev) cudaEventDestroy(e);
     if (j->done) cudaEventDestroy(j->done);
-    delete j->eng;
+    // an admitted job's bytes stay in `used` until its engine is released;
+    // a job larger than the budget was never admitted (no engine, no bytes)
+    if (j->eng) retired.emplace_back(j->eng, j->bytes);
     {
         std::lock_guard<std::mutex> lk(mu);
-        used -= j->bytes;
         done.push_back(r);
         finished += 1;
     }
@@ -122,9 +143,13 @@ void md_server::admit() {
                 pending.pop_front();
                 used += f->bytes;
                 j = f;
-            } else {
-                return;   // FIFO: wait for memory to free up
+            } else if (retired.empty()) {
+                return;   // FIFO: wait for running jobs to finish
             }
+        }
+        if (!j) {         // the memory of finished jobs makes the room
+            release_retired();
+            continue;
         }
         if (j->bytes > budget) {
             retire(j, MD_ENOMEM);
@@ -134,7 +159,8 @@ void md_server::admit() {
         Engine* e = new Engine();
         int rc = e->add_system(j->job.N, j->job.Yp, j->job.rho, j->job.T, j->job.seed, prm);
         if (!rc) rc = e->build_tables();
-        if (!rc) rc = e->initialise_async();
+        if (!rc) rc = e->initialise_async(false);   // relaxation follows in slices
+        j->relax_left = e->relax_iters();
         j->eng = e;
         if (rc) {
             retire(j, rc);
@@ -152,6 +178,7 @@ void md_server::admit() {
 void md_server::run() {
     cudaSetDevice(device);
     for (;;) {
+        if (active.empty() && !retired.empty()) release_retired();   // the device is idle
         {
             std::unique_lock<std::mutex> lk(mu);
             cv.wait(lk, [&] { return stop || !pending.empty() || !active.empty(); });
@@ -183,6 +210,20 @@ void md_server::run() {
                 }
                 j->state = kReady;
             }
+            if (j->relax_left > 0 && !stop) {     // creation: the next slice of relaxation
+                const int64_t k = std::min(slice_steps, j->relax_left);
+                int rc = j->eng->relax_async(k);
+                if (rc == MD_OK && cudaEventRecord(j->done, j->eng->stream()) != cudaSuccess) rc = MD_ECUDA;
+                if (rc != MD_OK) {
+                    retire(j, rc);
+                    continue;
+                }
+                j->relax_left -= k;
+                j->state = kInit;
+                progressed = true;
+                keep.push_back(j);
+                continue;
+            }
             const int64_t left = j->job.steps - j->done_steps;
             if (left <= 0 || stop) {
                 retire(j, stop && left > 0 ? MD_ETIMEOUT : MD_OK);
@@ -203,6 +244,7 @@ void md_server::run() {
         active.swap(keep);
         if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
+    release_retired();
 }
 
 extern "C" {
