@@ -559,7 +559,7 @@ __global__ void k_lbuild(EngineDev E, int half) {
     int* lst = S.list + (long long)I * S.T;
     int out = 0, outf = 0;         // near entries from the front, Coulomb-only from the back
     const int nsup = (S.T + kTile - 1) / kTile;
-    const float R2max = fmaxf(T.R2same, T.R2cross);
+    const bool Ip = I < S.Tp;
     const bool paired = half && S.list_kind == 0;
     for (int s0 = 0; s0 < nsup; s0 += 32) {
         const int sg = s0 + lane;
@@ -575,7 +575,9 @@ __global__ void k_lbuild(EngineDev E, int half) {
                 const float gap = fmaxf(fabsf(d) - hI[a] - hh[a], 0.0f);
                 d2 = fmaf(gap, gap, d2);
             }
-            pass = d2 < R2max;
+            // proton-proton pairs reach to the Coulomb range, all others to
+            // the nuclear range (super-tiles hold proton tiles first)
+            pass = d2 < ((Ip && sg * kTile < S.Tp) ? T.R2same : T.R2cross);
         }
         unsigned sm = __ballot_sync(0xffffffffu, pass);
         while (sm) {

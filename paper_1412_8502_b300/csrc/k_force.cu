@@ -22,10 +22,11 @@
 // atomics, so the result does not depend on their order; a second kernel
 // turns them into FP32 forces and clears them.
 //
-// Precision: positions are exact FP32 pairs hi + lo of the image nearest the
-// tile origin; periodic shifts of sources use an error-free two-sum, so every
-// separation dx = (hi_i - hi_j) + (lo_i - lo_j) carries only the rounding of
-// its final sum, whatever the box size.  Pair arithmetic is FP32; far
+// Precision: positions are FP32 pairs hi + lo of the image nearest the tile
+// origin (hi rounded to 24 bits, lo the rounded remainder: 48 significant
+// bits); periodic shifts of sources use an error-free two-sum, so a
+// separation dx = (hi_i - hi_j) + (lo_i - lo_j) carries FP32 rounding of
+// order 2^-24 |dx|, whatever the box size.  Pair arithmetic is FP32; far
 // Coulomb-only pairs (beyond r_nuc + skin/2 of the target box) use the hi
 // part only, an error below 1e-4 fm at r > 12 fm.  Energies are combined in
 // FP64.

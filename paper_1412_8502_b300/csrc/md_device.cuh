@@ -10,10 +10,11 @@
 // order: protons occupy sorted slots [0, Np), neutrons [Np, N).  Proton tile
 // t covers slots [32 t, 32 t + 32) ∩ [0, Np); neutron tile Tp + u covers
 // [Np + 32 u, ...) ∩ [Np, N).  Positions and velocities are FP64 (x[a*N + p]
-// is axis a of sorted slot p).  The force kernel reads each position as an
-// exact pair of FP32 numbers, xhi + xlo, of the periodic image nearest its
-// tile's origin O_t (FP64, fixed at the last pair-list rebuild), refreshed
-// every step: xhi[32 t + lane] = fp32(xt), xlo = fp32(xt - xhi).
+// is axis a of sorted slot p).  The force kernel reads each position as a
+// pair of FP32 numbers, xhi + xlo, of the periodic image nearest its tile's
+// origin O_t (FP64, fixed at the last pair-list rebuild), refreshed every
+// step: xhi[32 t + lane] = xt rounded to 24 significant bits, xlo = the
+// remainder rounded to FP32 (|xt - xhi - xlo| <= 2^-49 |xt|).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -259,23 +260,27 @@ __device__ __forceinline__ float narrow_trunc(double d) {
     return __uint_as_float((h & 0x80000000u) | ((e - 896u) << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
 }
 
-// x = hi + lo: hi is x truncated to 24 significant bits, lo the remaining
-// 29 bits of the significand rounded to FP32 (|x - hi - lo| <= 2^-48 |x|),
-// from integer operations for 2^-74 <= |x| < 2^127; other x (zero
-// included) through the converter as hi = fp32(x), lo = fp32(x - hi).
+// x = hi + lo: hi is x rounded to 24 significant bits (to nearest, ties
+// away from zero, so |x - hi| <= ulp(hi)/2), lo the remainder rounded to
+// FP32 (|x - hi - lo| <= 2^-49 |x|), from integer operations for
+// 2^-74 <= |x| < 2^126; other x (zero included) through the converter as
+// hi = fp32(x), lo = fp32(x - hi).
 __device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned h = (unsigned)(b >> 32);
-    const unsigned e = (h >> 20) & 0x7ffu;
-    if (e - 949u >= 201u) {
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    if (e - 949u >= 200u) {
         hi = (float)x;
         lo = (float)(x - (double)hi);
         return;
     }
-    const unsigned s = h & 0x80000000u;
-    hi = __uint_as_float(s | ((e - 896u) << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
-    // the low 29 bits weigh 2^(e - 1075) each
-    lo = (float)((unsigned)b & 0x1fffffffu) * __uint_as_float(s | ((e - 948u) << 23));
+    const unsigned s = (unsigned)(b >> 32) & 0x80000000u;
+    // adding half a unit of the 24-bit significand rounds it (a carry may
+    // step the exponent, which is the correct rounded value)
+    const unsigned long long r = b + (1ull << 28);
+    hi = __uint_as_float(s | ((((unsigned)(r >> 52) & 0x7ffu) - 896u) << 23) | ((unsigned)(r >> 29) & 0x7fffffu));
+    // x - hi in units of 2^(e - 1075), the weight of the last bit of x
+    const int low = (int)((unsigned)b & 0x1fffffffu) - (int)(((unsigned)b & 0x10000000u) << 1);
+    lo = (float)low * __uint_as_float(s | ((e - 948u) << 23));
 }
 
 __device__ inline float warp_sum(float v) {
