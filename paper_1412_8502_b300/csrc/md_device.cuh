@@ -215,6 +215,7 @@ __device__ __forceinline__ void apply_shift(int shk, float Lhi, float Llo, float
 }
 
 // Wrap into [0, L): one period at most (displacements per step << L).
+static __device__ __noinline__ double wrap_box_slow(double x, double L);
 __device__ inline double wrap_box(double x, double L) {
     if (x >= L) {
         x -= L;
@@ -226,6 +227,9 @@ __device__ inline double wrap_box(double x, double L) {
 }
 
 // Nearest image of a difference with |d| < 1.5 L, comparison form.
+static __device__ __noinline__ double wrap_box_slow(double x, double L) { return wrap_box(x, L); }
+static __device__ __noinline__ double image_shift(double x, double L, float k) { return x - L * (double)k; }
+
 __device__ inline double min_image(double d, double L, double hL) {
     if (d > hL) d -= L;
     else if (d < -hL) d += L;
@@ -238,13 +242,23 @@ __device__ inline double min_image(double d, double L, double hL) {
 // forces, splitting positions into FP32 pairs, range tests) is done with
 // integer operations on the IEEE-754 bit patterns.
 
+// The rare cases below go through these out-of-line converters: inlined,
+// the compiler predicates them into the common path, where their FP64
+// instructions issue for every particle.
+static __device__ __noinline__ double widen_slow(float f) { return (double)f; }
+static __device__ __noinline__ float narrow_slow(double d) { return (float)d; }
+static __device__ __noinline__ float2 split_slow(double x) {
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
+
 // Exact (double)f.  Zero and normal f on the integer path; subnormal, inf
 // and NaN through the converter.
 __device__ __forceinline__ double widen(float f) {
     const unsigned b = __float_as_uint(f);
     const unsigned a = b & 0x7fffffffu;
     const bool normal = (a - 0x00800000u) < 0x7f000000u;
-    if (!normal && a != 0u) return (double)f;
+    if (!normal && a != 0u) return widen_slow(f);
     const unsigned long long mag = normal ? ((unsigned long long)a << 29) + (896ull << 52) : 0ull;
     return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) | mag));
 }
@@ -256,7 +270,7 @@ __device__ __forceinline__ float narrow_trunc(double d) {
     const unsigned h = (unsigned)(b >> 32);
     const unsigned e = (h >> 20) & 0x7ffu;
     if (e == 0u && (b << 1) == 0ull) return __uint_as_float(h & 0x80000000u);
-    if (e - 897u >= 254u) return (float)d;
+    if (e - 897u >= 254u) return narrow_slow(d);
     return __uint_as_float((h & 0x80000000u) | ((e - 896u) << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
 }
 
@@ -269,8 +283,9 @@ __device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
     if (e - 949u >= 200u) {
-        hi = (float)x;
-        lo = (float)(x - (double)hi);
+        const float2 q = split_slow(x);
+        hi = q.x;
+        lo = q.y;
         return;
     }
     const unsigned s = (unsigned)(b >> 32) & 0x80000000u;
@@ -334,7 +349,7 @@ __device__ inline void write_xt_moved(const SysConst& s, int t, int lane, const 
     const float pv[3] = {prev.x, prev.y, prev.z};
     for (int a = 0; a < 3; ++a) {
         const float d = narrow_trunc(xs[a]) - pv[a];
-        if (fabsf(d) > 0.5f * Lf) xt[a] = xs[a] - L * (double)rintf(d / Lf);
+        if (fabsf(d) > 0.5f * Lf) xt[a] = image_shift(xs[a], L, rintf(d / Lf));
     }
     store_xt(s, t, lane, xt, true);
 }
@@ -344,7 +359,7 @@ __device__ inline void write_xt_moved(const SysConst& s, int t, int lane, const 
 __device__ __forceinline__ double wrap_box_bits(double x, double L) {
     const long long xb = __double_as_longlong(x);
     if (xb >= 0 && xb < __double_as_longlong(L)) return x;    // 0 <= x < L (L > 0)
-    return wrap_box(x, L);
+    return wrap_box_slow(x, L);
 }
 
 // Block-level max of a non-negative float (one value per warp, lane 0
