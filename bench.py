@@ -34,6 +34,7 @@ sys.path.insert(0, str(ROOT))
 
 MEASURED = ROOT / "MEASURED_PEAKS.json"
 TRAFFIC = ROOT / "profiles" / "force_split_409600_traffic.json"
+PIPES = ROOT / "profiles" / "force_split_204800_pipes.json"
 FORCE_SRC = ROOT / "paper_1412_8502_b300" / "csrc" / "k_force.cu"
 
 WORKLOADS = {
@@ -126,6 +127,22 @@ def force_traffic():
     d = json.loads(TRAFFIC.read_text())
     sha = hashlib.sha256(FORCE_SRC.read_bytes()).hexdigest()[:16]
     return d.get("dram_bytes_per_launch") if d.get("k_force_sha") == sha else None
+
+
+def force_pipes():
+    """Issue and pipe utilisation of the force kernel from the committed ncu
+    summary, if the force kernel source is unchanged since it was taken."""
+    if not PIPES.exists():
+        return None
+    d = json.loads(PIPES.read_text())
+    sha = hashlib.sha256(FORCE_SRC.read_bytes()).hexdigest()[:16]
+    if d.get("k_force_sha") != sha:
+        return None
+    keys = ("issue_active", "fma_pipe_active", "alu_pipe_active", "lsu_pipe_active", "xu_pipe_active",
+            "fp64_pipe_active")
+    out = {k: d[k] for k in keys if k in d}
+    out["source"] = "ncu, " + d.get("workload", "")
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -256,6 +273,7 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "kernel": "k_force_split", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": (achieved / fp32_peak) if achieved else None,
                      "traffic": force_traffic(),
+                     "issue": force_pipes(),
                      "peak_note": "FP32 FMA issue peak 148 SM x 128 lanes x 2 flop x 2032 MHz (derived; "
                                   "MEASURED_PEAKS has no FP32 figure)",
                      "algorithmic": {"pairs_nuc_per_step": pairs_nuc / K, "pairs_coul_per_step": pairs_coul / K,
@@ -295,9 +313,10 @@ def run_gpu(args):
 
 def cell_build_roofline(kt, rebuilds, N, info, peaks):
     """Spatial sort + tile build (hist, scan, scatter, move, tiles) per
-    rebuild: algorithmic bytes / CUDA-event time (the kernels' early exits on
-    steps without a rebuild are included in the time, conservatively)."""
-    names = ("hist", "scan", "scatter", "move", "tiles")
+    rebuild: algorithmic bytes / CUDA-event time.  In the step graph these
+    kernels sit in a conditional node that runs only on rebuild steps; its
+    event interval ("cell_build") is the time."""
+    names = ("cell_build",) if "cell_build" in kt else ("hist", "scan", "scatter", "move", "tiles")
     ms = sum(kt.get(k, (0, 0.0))[1] for k in names)
     if rebuilds <= 0 or ms <= 0:
         return None
@@ -343,11 +362,12 @@ def run_batch(steps):
     p.r_C = 0.0                 # and the Coulomb cutoff from each box (min(40, L0/2))
     b.step(3)
     torch.cuda.synchronize()
+    l0 = b.systems[0].info()["launches"]
     t0 = time.perf_counter()
     b.step(steps)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
-    launches = b.systems[0].info()["launches"]
+    launches = (b.systems[0].info()["launches"] - l0) / steps
     b.close()
     ts = 0.0
     for j in jobs:
@@ -361,7 +381,7 @@ def run_batch(steps):
         s.close()
     return {"systems": len(jobs), "nucleons": ntot, "steps": steps, "tuned_skin_fm": tuned_skin,
             "batched": ntot * steps / tb, "serial": ntot * steps / ts, "speedup": ts / tb,
-            "unit": "nucleon-steps/s", "graph_nodes_per_step": 17,
+            "unit": "nucleon-steps/s", "kernel_launches_per_step": launches,
             "note": "15 systems (Yp x T sweep), N from {4000,12800,25600,51200}, rho log-uniform "
                     "[0.00125, 0.08]; batched = one graph launch per step for all; serial = one system at a time"}
 

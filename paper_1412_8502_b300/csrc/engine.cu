@@ -107,6 +107,7 @@ const char* last_error_cstr() { return g_err.c_str(); }
 
 Engine::Engine() {
     cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&aux_stream_, cudaStreamNonBlocking);
     stream_ = own_stream_;
     H_.owner = this;
     H_.rec_fn = rec_cb;
@@ -123,11 +124,12 @@ Engine::~Engine() {
     sys.clear();
     free_tables();
     if (own_stream_) cudaStreamDestroy(own_stream_);
+    if (aux_stream_) cudaStreamDestroy(aux_stream_);
 }
 
 void Engine::free_tables() {
     void* ptrs[] = {d_sys_, d_tile_sys_, d_item_sys_, d_hist_, d_binstart_, d_cursor_, d_blocksum_, d_any_, d_out_,
-                    d_clock_, d_seeds_};
+                    d_clock_, d_seeds_, d_cond_runs_};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d_sys_ = nullptr;
@@ -135,6 +137,7 @@ void Engine::free_tables() {
     d_item_sys_ = nullptr;
     d_hist_ = d_binstart_ = d_cursor_ = d_blocksum_ = nullptr;
     d_any_ = nullptr;
+    d_cond_runs_ = nullptr;
     d_out_ = d_clock_ = nullptr;
     d_seeds_ = nullptr;
     table_bytes_ = 0;
@@ -386,6 +389,7 @@ int Engine::build_tables() {
     if ((rc = A(&d_cursor_, sizeof(unsigned) * bins))) return rc;
     if ((rc = A(&d_blocksum_, sizeof(unsigned) * (nscan + 1)))) return rc;
     if ((rc = A(&d_any_, sizeof(int)))) return rc;
+    if ((rc = A(&d_cond_runs_, sizeof(unsigned long long)))) return rc;
     if ((rc = A(&d_out_, sizeof(double) * 16))) return rc;
     if ((rc = A(&d_clock_, sizeof(double) * 8))) return rc;
     if ((rc = A(&d_seeds_, sizeof(unsigned long long) * std::max(n, 1)))) return rc;
@@ -407,6 +411,7 @@ int Engine::build_tables() {
     E.cursor = d_cursor_;
     E.blocksum = d_blocksum_;
     E.any_rebuild = d_any_;
+    E.cond_runs = d_cond_runs_;
     H_.precision = precision;
     H_.any_pp = false;
     H_.any_verlet = false;
@@ -450,40 +455,100 @@ int Engine::relax_async(int64_t n) {
 }
 
 // ------------------------------------------------------------------ graphs
+// A step (kind 0) or relaxation iteration (kind 1) as one graph: kick-drift
+// (or the steepest-descent update) and the rebuild decision, the rebuild
+// kernels in two conditional (IF) nodes on handles that the decision kernel
+// sets (on steps without a rebuild they are not launched), then the forces
+// and the closing kick.  The plain segments are captured into the graph from
+// its current frontier; the conditional nodes are added between them and
+// their bodies captured on a second stream.  Timing events (not allowed
+// inside conditional bodies) bracket each conditional node.
 int Engine::capture(GraphRec& g, int kind, bool energy) {
     g = GraphRec();
     capturing_ = true;
     capture_nodes_ = 0;
+    cond_nodes_ = 0;
     cur_rec_ = &g;
     cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        if (kind == 0) {
-            launch_kick_drift(H_, stream_);
-            launch_rebuild(H_, stream_, 0, -1);
-            launch_force(H_, stream_, energy, -1, 0);
-            launch_kick_finalize(H_, stream_, energy);
-        } else {
-            launch_sd_update(H_, stream_);
-            launch_rebuild(H_, stream_, 0, -1);
-            launch_force(H_, stream_, false, -1, 0);
-        }
+    int rc = build_step_graph(graph, kind, energy);
+    capturing_ = false;
+    cur_rec_ = nullptr;
+    if (rc != MD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(MD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    g.nodes = capture_nodes_;
+    g.cond_nodes = cond_nodes_;
+    return MD_OK;
+}
+
+int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h[2];     // one per conditional node
+    for (int k = 0; k < 2; ++k) CK(cudaGraphConditionalHandleCreate(&h[k], graph, 0, cudaGraphCondAssignDefault));
+    std::vector<cudaGraphNode_t> front;
+    int rc;
+    // segment: launches captured into `graph` after the frontier, which then moves
+    auto segment = [&](auto&& launches) -> int {
+        CK(cudaStreamBeginCaptureToGraph(stream_, graph, front.empty() ? nullptr : front.data(), nullptr,
+                                         front.size(), cudaStreamCaptureModeThreadLocal));
+        launches();
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        cudaError_t e = cudaStreamGetCaptureInfo(stream_, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+        std::vector<cudaGraphNode_t> next(deps, deps + (e == cudaSuccess ? nd : 0));
+        cudaGraph_t out = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(stream_, &out);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(MD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        front.swap(next);
+        return MD_OK;
+    };
+    // conditional node after the frontier; its body captured on the second stream
+    auto conditional = [&](int part) -> int {
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h[part];
+        p.conditional.type = cudaGraphCondTypeIf;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, graph, front.empty() ? nullptr : front.data(), nullptr, front.size(), &p));
+        CK(cudaStreamBeginCaptureToGraph(aux_stream_, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal));
+        const int n0 = capture_nodes_;
+        if (part == 0) launch_cell_build(H_, aux_stream_, false);
+        else launch_list_build(H_, aux_stream_, false);
+        cond_nodes_ += capture_nodes_ - n0;
+        capture_nodes_ = n0;
+        cudaGraph_t body = nullptr;
+        CK(cudaStreamEndCapture(aux_stream_, &body));
+        front.assign(1, node);
+        return MD_OK;
+    };
+    if ((rc = segment([&] {
+             if (kind == 0) launch_kick_drift(H_, stream_);
+             else launch_sd_update(H_, stream_);
+             launch_decide(H_, stream_, 0, -1, h[0], h[1], true);
+             H_.rec("cell_build", stream_);
+         })))
+        return rc;
+    if ((rc = conditional(0))) return rc;
+    if ((rc = segment([&] { H_.rec("lists", stream_); }))) return rc;
+    if ((rc = conditional(1))) return rc;
+    return segment([&] {
+        launch_force(H_, stream_, kind == 0 && energy, -1, 0);
+        if (kind == 0) launch_kick_finalize(H_, stream_, energy);
         if (timing_) {
             cudaEvent_t ev;
             cudaEventCreate(&ev);
             cudaEventRecordWithFlags(ev, stream_, cudaEventRecordExternal);
-            g.events.push_back(ev);
+            cur_rec_->events.push_back(ev);
         }
-        e = cudaStreamEndCapture(stream_, &graph);
-    }
-    capturing_ = false;
-    cur_rec_ = nullptr;
-    if (e != cudaSuccess) return fail(MD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&g.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(MD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    g.nodes = capture_nodes_;
-    return MD_OK;
+    });
 }
 
 int Engine::run_graph(GraphRec& g) {
@@ -956,7 +1021,10 @@ int Engine::info(int idx, md_info_t* out) {
     out->tiles = h.T;
     out->rebuilds = st.n_rebuilds;
     out->list_entries = st.list_total;
-    out->launches = launches;
+    unsigned long long cond_runs = 0;
+    CK(cudaMemcpyAsync(&cond_runs, d_cond_runs_, sizeof(cond_runs), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    out->launches = launches + (int64_t)cond_runs * cond_nodes_;
     out->device_bytes = (int64_t)(h.bytes + (sys.size() == 1 ? table_bytes_ : 0));
     out->need_wrap = st.need_wrap;
     out->sort_bits = h.nbits;

@@ -38,7 +38,8 @@ struct SysHost {
 
 struct GraphRec {
     cudaGraphExec_t exec = nullptr;
-    int nodes = 0;
+    int nodes = 0;                      // kernels launched on every replay
+    int cond_nodes = 0;                 // kernels of the conditional rebuild bodies
     std::vector<std::string> names;     // timing mode: one per event interval
     std::vector<cudaEvent_t> events;
 };
@@ -124,7 +125,11 @@ private:
     bool timing_ = false;
     bool capturing_ = false;
     int capture_nodes_ = 0;
+    int cond_nodes_ = 0;                    // kernels per run of the conditional rebuild bodies
     GraphRec* cur_rec_ = nullptr;
+    cudaStream_t aux_stream_ = nullptr;     // captures the bodies of conditional nodes
+    unsigned long long* d_cond_runs_ = nullptr;
+    int build_step_graph(cudaGraph_t& graph, int kind, bool energy);
     std::map<std::string, std::pair<int64_t, double>> ktimes_;
     std::vector<std::string> korder_;
 };

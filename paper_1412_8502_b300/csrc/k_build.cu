@@ -131,7 +131,12 @@ __device__ __forceinline__ void warp_bounds(double v, bool valid, double& lo, do
 
 // ---------------------------------------------------------------- decision
 // One thread per system.  forced_only: rebuild only systems that asked.
-__global__ void k_decide(EngineDev E, int forced_only, int only) {
+// set_cond: the kernel runs inside a step graph whose rebuild kernels sit in
+// two conditional (IF) nodes, on handles cond_cell and cond_list (a handle
+// drives one node); it sets both, so the rebuild kernels are not launched at
+// all on steps without a rebuild.
+__global__ void k_decide(EngineDev E, int forced_only, int only, cudaGraphConditionalHandle cond_cell,
+                         cudaGraphConditionalHandle cond_list, int set_cond) {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -159,7 +164,14 @@ __global__ void k_decide(EngineDev E, int forced_only, int only) {
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) *E.any_rebuild = any;
+    if (threadIdx.x == 0) {
+        *E.any_rebuild = any;
+        if (set_cond) {
+            cudaGraphSetConditional(cond_cell, any ? 1u : 0u);
+            cudaGraphSetConditional(cond_list, any ? 1u : 0u);
+            if (any) *E.cond_runs += 1ull;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- histogram
@@ -818,33 +830,55 @@ __global__ void k_lwrite(EngineDev E, int only) {
 }
 
 // ---------------------------------------------------------------- launchers
-void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int only) {
+void launch_decide(const EngineHost& H, cudaStream_t s, int forced_only, int only,
+                   cudaGraphConditionalHandle cond_cell, cudaGraphConditionalHandle cond_list, bool set_cond) {
+    H.rec("decide", s);
+    k_decide<<<1, 1024, 0, s>>>(H.dev, forced_only, only, cond_cell, cond_list, set_cond ? 1 : 0);
+    H.count(1);
+}
+
+// Spatial sort and tiles (the cell build).  rec: per-kernel timing events
+// (not inside conditional graph nodes, which hold kernels only).
+void launch_cell_build(const EngineHost& H, cudaStream_t s, bool rec) {
     const EngineDev& E = H.dev;
     const int nb = (E.ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
     const int nscan = (int)((E.nbins_total + kScanChunk - 1) / kScanChunk);
-    H.rec("decide", s);
-    k_decide<<<1, 1024, 0, s>>>(E, forced_only, only);
-    H.rec("hist", s);
+    if (rec) H.rec("hist", s);
     k_hist<<<nb, kBlock, 0, s>>>(E);
-    H.rec("scan", s);
+    if (rec) H.rec("scan", s);
     k_scan_reduce<<<nscan, 1024, 0, s>>>(E);
     k_scan_top<<<1, 1024, 0, s>>>(E, nscan);
     k_scan_down<<<nscan, 1024, 0, s>>>(E);
-    H.rec("scatter", s);
+    if (rec) H.rec("scatter", s);
     k_scatter<<<nb, kBlock, 0, s>>>(E);
-    H.rec("move", s);
+    if (rec) H.rec("move", s);
     k_move<<<nb, kBlock, 0, s>>>(E);
-    H.rec("tiles", s);
+    if (rec) H.rec("tiles", s);
     k_tiles<<<nb, kBlock, 0, s>>>(E);
-    H.rec("lists", s);
+    H.count(7);
+}
+
+// Super-tile boxes and tile-pair lists (+ per-particle Verlet lists).
+void launch_list_build(const EngineHost& H, cudaStream_t s, bool rec) {
+    const EngineDev& E = H.dev;
+    const int nb = (E.ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
+    if (rec) H.rec("lists", s);
     k_super<<<nb, kBlock, 0, s>>>(E);
     k_lbuild<<<nb, kBlock, 0, s>>>(E, H.precision == 0 ? 1 : 0);
-    H.count(10);
+    H.count(2);
     if (H.any_verlet) {
-        H.rec("verlet_lists", s);
+        if (rec) H.rec("verlet_lists", s);
         k_vbuild<<<E.ntiles, kVB * 32, 0, s>>>(E);
         H.count(1);
     }
+}
+
+// Decision and rebuild launched directly (outside a step graph): the rebuild
+// kernels run and return at once unless a system rebuilds.
+void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int only) {
+    launch_decide(H, s, forced_only, only, 0, 0, false);
+    launch_cell_build(H, s, true);
+    launch_list_build(H, s, true);
 }
 
 // phase 0: count and scan (host then checks capacity); phase 1: write.

@@ -45,6 +45,10 @@ struct EngineHost {
 };
 
 void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int only);
+void launch_decide(const EngineHost& H, cudaStream_t s, int forced_only, int only,
+                   cudaGraphConditionalHandle cond_cell, cudaGraphConditionalHandle cond_list, bool set_cond);
+void launch_cell_build(const EngineHost& H, cudaStream_t s, bool rec);
+void launch_list_build(const EngineHost& H, cudaStream_t s, bool rec);
 void launch_cluster_lists(const EngineHost& H, cudaStream_t s, int phase, int only);
 void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt);
 void launch_coulomb_pp(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt);

@@ -152,6 +152,7 @@ struct EngineDev {
     unsigned* cursor;        // [nbins_total] scatter cursors
     unsigned* blocksum;      // [scan blocks]
     int* any_rebuild;        // set when any system rebuilds this step
+    unsigned long long* cond_runs;   // step-graph rebuilds run through the conditional node
 };
 
 // Force work items of a system.  A proton tile's list holds its near
