@@ -17,6 +17,7 @@
 // remainder rounded to FP32 (|xt - xhi - xlo| <= 2^-49 |xt|).
 #pragma once
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace pasta {
@@ -216,8 +217,8 @@ __device__ __forceinline__ void apply_shift(int shk, float Lhi, float Llo, float
 }
 
 // Wrap into [0, L): one period at most (displacements per step << L).
-static __device__ __noinline__ double wrap_box_slow(double x, double L);
-__device__ inline double wrap_box(double x, double L) {
+static __host__ __device__ __noinline__ double wrap_box_slow(double x, double L);
+__host__ __device__ inline double wrap_box(double x, double L) {
     if (x >= L) {
         x -= L;
     } else if (x < 0.0) {
@@ -228,7 +229,7 @@ __device__ inline double wrap_box(double x, double L) {
 }
 
 // Nearest image of a difference with |d| < 1.5 L, comparison form.
-static __device__ __noinline__ double wrap_box_slow(double x, double L) { return wrap_box(x, L); }
+static __host__ __device__ __noinline__ double wrap_box_slow(double x, double L) { return wrap_box(x, L); }
 static __device__ __noinline__ double image_shift(double x, double L, float k) { return x - L * (double)k; }
 
 __device__ inline double min_image(double d, double L, double hL) {
@@ -243,36 +244,75 @@ __device__ inline double min_image(double d, double L, double hL) {
 // forces, splitting positions into FP32 pairs, range tests) is done with
 // integer operations on the IEEE-754 bit patterns.
 
+// Bit patterns of FP32/FP64 values (device intrinsics; memcpy on the host,
+// where the helpers below are tested against the hardware conversions).
+__host__ __device__ __forceinline__ unsigned f_bits(float f) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    unsigned u;
+    memcpy(&u, &f, sizeof u);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ float f_from(unsigned u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    memcpy(&f, &u, sizeof f);
+    return f;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned long long d_bits(double d) {
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(d);
+#else
+    unsigned long long u;
+    memcpy(&u, &d, sizeof u);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ double d_from(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double d;
+    memcpy(&d, &u, sizeof d);
+    return d;
+#endif
+}
+
 // The rare cases below go through these out-of-line converters: inlined,
 // the compiler predicates them into the common path, where their FP64
 // instructions issue for every particle.
-static __device__ __noinline__ double widen_slow(float f) { return (double)f; }
-static __device__ __noinline__ float narrow_slow(double d) { return (float)d; }
-static __device__ __noinline__ float2 split_slow(double x) {
+static __host__ __device__ __noinline__ double widen_slow(float f) { return (double)f; }
+static __host__ __device__ __noinline__ float narrow_slow(double d) { return (float)d; }
+static __host__ __device__ __noinline__ float2 split_slow(double x) {
     const float hi = (float)x;
     return make_float2(hi, (float)(x - (double)hi));
 }
 
 // Exact (double)f.  Zero and normal f on the integer path; subnormal, inf
 // and NaN through the converter.
-__device__ __forceinline__ double widen(float f) {
-    const unsigned b = __float_as_uint(f);
+__host__ __device__ __forceinline__ double widen(float f) {
+    const unsigned b = f_bits(f);
     const unsigned a = b & 0x7fffffffu;
     const bool normal = (a - 0x00800000u) < 0x7f000000u;
     if (!normal && a != 0u) return widen_slow(f);
     const unsigned long long mag = normal ? ((unsigned long long)a << 29) + (896ull << 52) : 0ull;
-    return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) | mag));
+    return d_from(((unsigned long long)(b & 0x80000000u) << 32) | mag);
 }
 
 // d truncated to FP32 (|result| <= |d|, relative error below 2^-23) for d
 // in the normal FP32 range or zero; other values through the converter.
-__device__ __forceinline__ float narrow_trunc(double d) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+__host__ __device__ __forceinline__ float narrow_trunc(double d) {
+    const unsigned long long b = d_bits(d);
     const unsigned h = (unsigned)(b >> 32);
     const unsigned e = (h >> 20) & 0x7ffu;
-    if (e == 0u && (b << 1) == 0ull) return __uint_as_float(h & 0x80000000u);
+    if (e == 0u && (b << 1) == 0ull) return f_from(h & 0x80000000u);
     if (e - 897u >= 254u) return narrow_slow(d);
-    return __uint_as_float((h & 0x80000000u) | ((e - 896u) << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
+    return f_from((h & 0x80000000u) | ((e - 896u) << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
 }
 
 // x = hi + lo: hi is x rounded to 24 significant bits (to nearest, ties
@@ -280,8 +320,8 @@ __device__ __forceinline__ float narrow_trunc(double d) {
 // FP32 (|x - hi - lo| <= 2^-49 |x|), from integer operations for
 // 2^-74 <= |x| < 2^126; other x (zero included) through the converter as
 // hi = fp32(x), lo = fp32(x - hi).
-__device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+__host__ __device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
+    const unsigned long long b = d_bits(x);
     const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
     if (e - 949u >= 200u) {
         const float2 q = split_slow(x);
@@ -293,10 +333,10 @@ __device__ __forceinline__ void split_hilo(double x, float& hi, float& lo) {
     // adding half a unit of the 24-bit significand rounds it (a carry may
     // step the exponent, which is the correct rounded value)
     const unsigned long long r = b + (1ull << 28);
-    hi = __uint_as_float(s | ((((unsigned)(r >> 52) & 0x7ffu) - 896u) << 23) | ((unsigned)(r >> 29) & 0x7fffffu));
+    hi = f_from(s | ((((unsigned)(r >> 52) & 0x7ffu) - 896u) << 23) | ((unsigned)(r >> 29) & 0x7fffffu));
     // x - hi in units of 2^(e - 1075), the weight of the last bit of x
     const int low = (int)((unsigned)b & 0x1fffffffu) - (int)(((unsigned)b & 0x10000000u) << 1);
-    lo = (float)low * __uint_as_float(s | ((e - 948u) << 23));
+    lo = (float)low * f_from(s | ((e - 948u) << 23));
 }
 
 __device__ inline float warp_sum(float v) {
@@ -357,9 +397,9 @@ __device__ inline void write_xt_moved(const SysConst& s, int t, int lane, const 
 
 // xs wrapped into [0, L) (x >= L: x - L; x < 0: x + L, or 0 if that rounds
 // to L), the common in-range case decided on the bit patterns.
-__device__ __forceinline__ double wrap_box_bits(double x, double L) {
-    const long long xb = __double_as_longlong(x);
-    if (xb >= 0 && xb < __double_as_longlong(L)) return x;    // 0 <= x < L (L > 0)
+__host__ __device__ __forceinline__ double wrap_box_bits(double x, double L) {
+    const long long xb = (long long)d_bits(x);
+    if (xb >= 0 && xb < (long long)d_bits(L)) return x;       // 0 <= x < L (L > 0)
     return wrap_box_slow(x, L);
 }
 
