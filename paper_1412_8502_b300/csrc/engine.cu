@@ -36,8 +36,10 @@ static PairF pair_consts(const SysConst& c) {
     f.kc = (float)(-1.0 / (c.lambda_s * ln2));
     f.l2a = (float)std::log2(c.alpha);
     f.il = (float)(1.0 / c.lambda_s);
-    const float half = 0.5f * (float)c.skin + 2e-3f;
-    const float Rn = (float)c.r_nuc + half, Rc = (float)(c.coulomb == 1 ? c.r_C : 0.0) + half;
+    // the force pass tests sources against the box of its targets' current
+    // positions, so the radii are the cutoffs plus a rounding margin (no skin)
+    const float margin = 2e-3f;
+    const float Rn = (float)c.r_nuc + margin, Rc = (float)(c.coulomb == 1 ? c.r_C : 0.0) + margin;
     f.Rn2 = Rn * Rn;
     f.Rc2 = Rc * Rc;
     return f;

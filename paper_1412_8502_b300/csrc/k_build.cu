@@ -106,13 +106,6 @@ __device__ __forceinline__ double dkey_inv(unsigned long long k) {
     const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
     return __longlong_as_double((long long)b);
 }
-__device__ __forceinline__ unsigned fkey(float v) {
-    const unsigned b = __float_as_uint(v);
-    return (b >> 31) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float fkey_inv(unsigned k) {
-    return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
-}
 
 // Bounds lo <= min and hi >= max of v over the valid lanes of the warp from
 // one 32-bit integer reduction each on the high words of the keys (no FP64

@@ -490,8 +490,27 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
         X.h1 = X.ok1 ? S.xhi[I * kTile + j + 16] : a0;
         X.l1 = X.ok1 ? S.xlo[I * kTile + j + 16] : b0;
     }
-    const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
-    const float hIx = S.thalf[3 * I], hIy = S.thalf[3 * I + 1], hIz = S.thalf[3 * I + 2];
+    // Box of the targets' current positions (high parts; a lane on an empty
+    // slot sits on a real particle of the tile), widened by 1e-3 fm for the
+    // low parts and FP32 rounding; sources are tested against it with the
+    // bare cutoffs (the rebuild-time box would need the skin on top).
+    float4 oI;
+    float hIx, hIy, hIz;
+    {
+        const float a0[3] = {X.h0.x, X.h0.y, X.h0.z}, a1[3] = {X.h1.x, X.h1.y, X.h1.z};
+        float c[3], hh[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float lo = fkey_inv(__reduce_min_sync(0xffffffffu, fkey(fminf(a0[a], a1[a]))));
+            const float hi = fkey_inv(__reduce_max_sync(0xffffffffu, fkey(fmaxf(a0[a], a1[a]))));
+            c[a] = 0.5f * (lo + hi);
+            hh[a] = 0.5f * (hi - lo) + 1e-3f;
+        }
+        oI = make_float4(c[0], c[1], c[2], 0.0f);
+        hIx = hh[0];
+        hIy = hh[1];
+        hIz = hh[2];
+    }
     const bool Ip = I < S.Tp;
     const int cls0 = (Ip && S.coulomb == 1) ? kPPNuc : kNucSame;
     const int* lst = S.list + (long long)I * S.T;

@@ -83,7 +83,7 @@ struct PairF {
     float kc;                // -1/(lambda ln 2)
     float l2a;               // log2(alpha)
     float il;                // 1/lambda
-    float Rn2, Rc2;          // source filter radii^2: cutoff + skin/2 + 2e-3 fm
+    float Rn2, Rc2;          // source filter radii^2 around the targets' current box: cutoff + 2e-3 fm
 };
 
 // Per-system constants and device pointers.
@@ -281,6 +281,16 @@ __host__ __device__ __forceinline__ double d_from(unsigned long long u) {
     memcpy(&d, &u, sizeof d);
     return d;
 #endif
+}
+
+// Order-preserving 32-bit key of a float (a < b exactly when key(a) < key(b))
+// for integer warp min / max reductions.
+__device__ __forceinline__ unsigned fkey(float v) {
+    const unsigned b = __float_as_uint(v);
+    return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned k) {
+    return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
 }
 
 // The rare cases below go through these out-of-line converters: inlined,
