@@ -190,6 +190,7 @@ struct WarpQueues {
     float4 sh[kStages][kTile];   // staged source tiles (high parts)
     float4 sl[kStages][kTile];   // staged source tiles (low parts)
     int sJ[kStages];             // staged tile index | shift code << 24 | nuclear flag
+    float4 box[4];               // half-tile boxes of the targets: centre A, half A, centre B, half B
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -490,26 +491,35 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
         X.h1 = X.ok1 ? S.xhi[I * kTile + j + 16] : a0;
         X.l1 = X.ok1 ? S.xlo[I * kTile + j + 16] : b0;
     }
-    // Box of the targets' current positions (high parts; a lane on an empty
+    // Boxes of the targets' current positions, one per half tile (targets
+    // j = 0..15 in .x of the lanes' pairs, j + 16 in .y; a lane on an empty
     // slot sits on a real particle of the tile), widened by 1e-3 fm for the
-    // low parts and FP32 rounding; sources are tested against it with the
-    // bare cutoffs (the rebuild-time box would need the skin on top).
-    float4 oI;
-    float hIx, hIy, hIz;
+    // low parts and FP32 rounding.  A source is kept when it is within the
+    // bare cutoff of either box: the union of the two regions is smaller than
+    // the region around the tile's single box wherever the tile is not
+    // box-shaped, and the rebuild-time box would need the skin on top.
+    // (kept in shared memory: registers are the scarce resource here)
     {
         const float a0[3] = {X.h0.x, X.h0.y, X.h0.z}, a1[3] = {X.h1.x, X.h1.y, X.h1.z};
-        float c[3], hh[3];
+        float cA[3], hA[3], cB[3], hB[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float lo = fkey_inv(__reduce_min_sync(0xffffffffu, fkey(fminf(a0[a], a1[a]))));
-            const float hi = fkey_inv(__reduce_max_sync(0xffffffffu, fkey(fmaxf(a0[a], a1[a]))));
-            c[a] = 0.5f * (lo + hi);
-            hh[a] = 0.5f * (hi - lo) + 1e-3f;
+            const float la = fkey_inv(__reduce_min_sync(0xffffffffu, fkey(a0[a])));
+            const float ua = fkey_inv(__reduce_max_sync(0xffffffffu, fkey(a0[a])));
+            const float lb = fkey_inv(__reduce_min_sync(0xffffffffu, fkey(a1[a])));
+            const float ub = fkey_inv(__reduce_max_sync(0xffffffffu, fkey(a1[a])));
+            cA[a] = 0.5f * (la + ua);
+            hA[a] = 0.5f * (ua - la) + 1e-3f;
+            cB[a] = 0.5f * (lb + ub);
+            hB[a] = 0.5f * (ub - lb) + 1e-3f;
         }
-        oI = make_float4(c[0], c[1], c[2], 0.0f);
-        hIx = hh[0];
-        hIy = hh[1];
-        hIz = hh[2];
+        if (lane == 0) {
+            Q.box[0] = make_float4(cA[0], cA[1], cA[2], 0.0f);
+            Q.box[1] = make_float4(hA[0], hA[1], hA[2], 0.0f);
+            Q.box[2] = make_float4(cB[0], cB[1], cB[2], 0.0f);
+            Q.box[3] = make_float4(hB[0], hB[1], hB[2], 0.0f);
+        }
+        __syncwarp();
     }
     const bool Ip = I < S.Tp;
     const int cls0 = (Ip && S.coulomb == 1) ? kPPNuc : kNucSame;
@@ -585,17 +595,25 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
         __syncwarp();
         const bool src_ok = h.x != kPad;
         if (shk != kShiftNone) apply_shift(shk, Lhi, Llo, h, l);
-        // distance of the source to I's box (small boxes: nearest image)
-        float ux = h.x - oI.x, uy = h.y - oI.y, uz = h.z - oI.z;
-        if (kWrap) {
-            ux = fmaf(-Lhi, rintf(ux * C.iLf), ux);
-            uy = fmaf(-Lhi, rintf(uy * C.iLf), uy);
-            uz = fmaf(-Lhi, rintf(uz * C.iLf), uz);
+        // squared distance of the source to the nearer half-tile box (small
+        // boxes: nearest image)
+        float d2h[2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float4 cc4 = Q.box[2 * b], hh4 = Q.box[2 * b + 1];
+            const float cc[3] = {cc4.x, cc4.y, cc4.z}, hh[3] = {hh4.x, hh4.y, hh4.z};
+            float ux = h.x - cc[0], uy = h.y - cc[1], uz = h.z - cc[2];
+            if (kWrap) {
+                ux = fmaf(-Lhi, rintf(ux * C.iLf), ux);
+                uy = fmaf(-Lhi, rintf(uy * C.iLf), uy);
+                uz = fmaf(-Lhi, rintf(uz * C.iLf), uz);
+            }
+            const float gx = fmaxf(fabsf(ux) - hh[0], 0.0f);
+            const float gy = fmaxf(fabsf(uy) - hh[1], 0.0f);
+            const float gz = fmaxf(fabsf(uz) - hh[2], 0.0f);
+            d2h[b] = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
         }
-        const float gx = fmaxf(fabsf(ux) - hIx, 0.0f);
-        const float gy = fmaxf(fabsf(uy) - hIy, 0.0f);
-        const float gz = fmaxf(fabsf(uz) - hIz, 0.0f);
-        const float d2 = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
+        const float d2 = fminf(d2h[0], d2h[1]);
         if (farc) {                // Coulomb-only entry: every source goes to PPC or nowhere
             push(Q, 1, src_ok && d2 < Rc2, c1, lane, h, l);
             if (c1 >= kTile) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, X, C, T, facc, N);
