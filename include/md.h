@@ -224,10 +224,13 @@ MD_API int md_set_state(md_system* s, const md_state_view* view);
 
 MD_API int md_get_info(const md_system* s, md_info_t* info);
 
-/* Per-kernel device timing.  When on, md_step records CUDA events around
- * every kernel of each step; md_kernel_times returns, for up to `max`
- * kernels, the name, launch count and summed milliseconds since the last
- * reset, and the number of kernels available in *n. */
+/* Per-kernel device timing.  on = 1: md_step records CUDA events around
+ * every kernel of each step; on = 2: only around the cell build, the list
+ * build, the force pass and the closing kick (fewer event nodes in the step
+ * graph); 0: off (MD_EINVAL for other values).  Each call resets the sums.
+ * md_kernel_times returns, for up to `max` timed intervals, the name of the
+ * kernel that opens it, the count and the summed milliseconds, and the number
+ * of intervals available in *n. */
 MD_API int md_set_timing(md_system* s, int on);
 MD_API int md_kernel_times(md_system* s, int max, const char** names, int64_t* launches,
                     double* ms, int* n);

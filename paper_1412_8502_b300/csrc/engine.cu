@@ -162,18 +162,29 @@ size_t Engine::device_bytes() const {
 
 void Engine::set_stream(cudaStream_t s) { stream_ = s ? s : own_stream_; }
 
-void Engine::set_timing(bool on) {
-    if (on != timing_) {
+void Engine::set_timing(int level) {
+    if (level != timing_level_) {
         cudaStreamSynchronize(stream_);
         drop_graphs();
-        timing_ = on;
+        timing_level_ = level;
+        timing_ = level != 0;
     }
     ktimes_.clear();
     korder_.clear();
 }
 
+// Level 2 records events only at the start of these kernels (and at the end
+// of the step): fewer event nodes in the step graph.
+static bool key_kernel(const char* name) {
+    static const char* keys[] = {"cell_build", "lists", "force", "force_verlet", "force_fix", "coulomb_pp", "kick"};
+    for (const char* k : keys)
+        if (std::strcmp(k, name) == 0) return true;
+    return false;
+}
+
 void Engine::on_rec(const char* name, cudaStream_t s) {
     if (!(capturing_ && timing_ && cur_rec_)) return;
+    if (timing_level_ == 2 && !key_kernel(name)) return;
     cudaEvent_t e;
     cudaEventCreate(&e);
     cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);

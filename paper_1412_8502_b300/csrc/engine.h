@@ -87,7 +87,7 @@ public:
 
     void set_stream(cudaStream_t s);
     cudaStream_t stream() const { return stream_; }
-    void set_timing(bool on);
+    void set_timing(int level);     // 0 off, 1 every kernel, 2 key kernels only
     int kernel_times(int max, const char** names, int64_t* launches, double* ms, int* n);
 
     std::vector<SysHost*> sys;
@@ -123,6 +123,7 @@ private:
 
     GraphRec g_step_[2], g_relax_;
     bool timing_ = false;
+    int timing_level_ = 0;
     bool capturing_ = false;
     int capture_nodes_ = 0;
     int cond_nodes_ = 0;                    // kernels per run of the conditional rebuild bodies

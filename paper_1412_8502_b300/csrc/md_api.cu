@@ -179,7 +179,8 @@ int md_get_info(const md_system* s, md_info_t* info) {
 
 int md_set_timing(md_system* s, int on) {
     GUARD(s);
-    s->eng->set_timing(on != 0);
+    if (on < 0 || on > 2) return fail(MD_EINVAL, "timing level must be 0, 1 or 2");
+    s->eng->set_timing(on);
     return MD_OK;
 }
 

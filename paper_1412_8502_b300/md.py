@@ -267,8 +267,9 @@ def md_set_stream(h, stream) -> None:
     _ck(LIB.md_set_stream(h, ctypes.c_void_p(ptr or 0)), "md_set_stream")
 
 
-def md_set_timing(h, on: bool) -> None:
-    _ck(LIB.md_set_timing(h, 1 if on else 0), "md_set_timing")
+def md_set_timing(h, on) -> None:
+    """on: False/0 off, True/1 every kernel, 2 key kernels only."""
+    _ck(LIB.md_set_timing(h, int(on)), "md_set_timing")
 
 
 def md_kernel_times(h) -> dict:
