@@ -163,6 +163,8 @@ def run_gpu(args):
         p.skin = 4.0
     if args.skin is not None:
         p.skin = args.skin
+    if args.plain_graph:                # profiling: ncu does not look inside graphs with conditional nodes
+        p.cond_graph = 0
     sys_ = md.System(N, W["Yp"], W["rho"], W["T"], replicas.replica_seed(W["seed"], rank), p)
     stream = torch.cuda.Stream()
     sys_.set_stream(stream)
@@ -273,6 +275,7 @@ def run_gpu(args):
         "data": "synthetic: seeded uniform positions + 500 steepest-descent iterations, Maxwell velocities",
         "config": {"workload": W["desc"], "N": N, "Yp": W["Yp"], "T_MeV": W["T"], "rho_start": W["rho"],
                    "lists": "half tile-pair lists" if args.lists == "tiles" else "per-particle Verlet lists",
+                   "graph": "plain nodes (profiling)" if args.plain_graph else "rebuild in conditional nodes",
                    "skin_fm": p.skin,
                    "xi_dot": W["xi"], "window": "first steps of the expansion (densest, slowest)",
                    "clusters": "one cluster analysis inside the timed region",
@@ -532,6 +535,8 @@ def main():
     ap.add_argument("--skin", type=float, default=None, help="pair-list skin / Verlet delta r, fm")
     ap.add_argument("--timing", default="key", choices=["key", "full"],
                     help="CUDA events inside the timed region: around the key kernels (default) or every kernel")
+    ap.add_argument("--plain-graph", action="store_true",
+                    help="rebuild kernels as plain graph nodes instead of conditional ones (for kernel profilers)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")

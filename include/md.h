@@ -93,6 +93,12 @@ typedef struct {
                                 as a multiple of the expected neighbour count at
                                 the initial density (default 2).  A rebuild that
                                 needs more makes md_step return MD_ENOMEM. */
+    int32_t cond_graph;      /* 1 (default): the rebuild kernels of a step sit in
+                                conditional graph nodes and are not launched on
+                                steps without a rebuild; 0: plain graph nodes
+                                that return at once on such steps (profilers
+                                that cannot look inside graphs with conditional
+                                nodes).  Results are the same. */
 } md_params;
 
 typedef struct {

@@ -500,8 +500,10 @@ int Engine::capture(GraphRec& g, int kind, bool energy) {
 
 int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
     CK(cudaGraphCreate(&graph, 0));
-    cudaGraphConditionalHandle h[2];     // one per conditional node
-    for (int k = 0; k < 2; ++k) CK(cudaGraphConditionalHandleCreate(&h[k], graph, 0, cudaGraphCondAssignDefault));
+    // one handle per conditional node (a graph may not hold a handle without its node)
+    cudaGraphConditionalHandle h[2] = {0, 0};
+    if (sys.empty() || sys[0]->prm.cond_graph != 0)
+        for (int k = 0; k < 2; ++k) CK(cudaGraphConditionalHandleCreate(&h[k], graph, 0, cudaGraphCondAssignDefault));
     std::vector<cudaGraphNode_t> front;
     int rc;
     // segment: launches captured into `graph` after the frontier, which then moves
@@ -542,16 +544,31 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
         front.assign(1, node);
         return MD_OK;
     };
-    if ((rc = segment([&] {
-             if (kind == 0) launch_kick_drift(H_, stream_);
-             else launch_sd_update(H_, stream_);
-             launch_decide(H_, stream_, 0, -1, h[0], h[1], true);
-             H_.rec("cell_build", stream_);
-         })))
-        return rc;
-    if ((rc = conditional(0))) return rc;
-    if ((rc = segment([&] { H_.rec("lists", stream_); }))) return rc;
-    if ((rc = conditional(1))) return rc;
+    const bool cond = sys.empty() || sys[0]->prm.cond_graph != 0;
+    if (!cond) {
+        // plain nodes: the rebuild kernels return at once unless a system rebuilds
+        rc = segment([&] {
+            if (kind == 0) launch_kick_drift(H_, stream_);
+            else launch_sd_update(H_, stream_);
+            launch_decide(H_, stream_, 0, -1, 0, 0, false);
+            H_.rec("cell_build", stream_);
+            launch_cell_build(H_, stream_, false);
+            H_.rec("lists", stream_);
+            launch_list_build(H_, stream_, false);
+        });
+        if (rc) return rc;
+    } else {
+        if ((rc = segment([&] {
+                 if (kind == 0) launch_kick_drift(H_, stream_);
+                 else launch_sd_update(H_, stream_);
+                 launch_decide(H_, stream_, 0, -1, h[0], h[1], true);
+                 H_.rec("cell_build", stream_);
+             })))
+            return rc;
+        if ((rc = conditional(0))) return rc;
+        if ((rc = segment([&] { H_.rec("lists", stream_); }))) return rc;
+        if ((rc = conditional(1))) return rc;
+    }
     return segment([&] {
         launch_force(H_, stream_, kind == 0 && energy, -1, 0);
         if (kind == 0) launch_kick_finalize(H_, stream_, energy);
@@ -904,6 +921,10 @@ int Engine::set_params(int idx, const md_params& p) {
         if (sys.size() > 1) return fail(MD_EINVAL, "precision is shared by all systems of a batch");
         precision = p.precision;
         H_.precision = precision;
+        cudaStreamSynchronize(stream_);
+        drop_graphs();
+    }
+    if ((h.prm.cond_graph != 0) != (p.cond_graph != 0)) {   // graph layout changes
         cudaStreamSynchronize(stream_);
         drop_graphs();
     }

@@ -38,7 +38,7 @@ class md_params(ctypes.Structure):
                 ("precision", _I32), ("coulomb", _I32), ("r_pp", _D), ("r_np", _D),
                 ("relax_iters", _I64), ("relax_gamma", _D), ("relax_dmax", _D),
                 ("energy_every", _I64), ("sort_bits", _I32), ("affine", _I32), ("list_kind", _I32),
-                ("verlet_pool", _D)]
+                ("verlet_pool", _D), ("cond_graph", _I32)]
 
 
 class md_energy_t(ctypes.Structure):

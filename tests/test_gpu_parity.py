@@ -254,6 +254,23 @@ def test_rerun_is_bitwise_identical(md):
         assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
+def test_plain_and_conditional_step_graphs_agree_bitwise(md):
+    """The rebuild kernels in conditional graph nodes (default) or as plain
+    nodes that return at once without a rebuild: the same kernels run on
+    the same data, so trajectories (through several rebuilds) are identical."""
+    x, t, L = CONFIGS["cfg1_liquid_2000"]()
+    out = []
+    for cond in (1, 0):
+        s, v = load(md, x, t, L, 0, cond_graph=cond)
+        s.step(30, 7.5e-5)
+        g = s.state()
+        out.append((g["x"].copy(), g["v"].copy(), s.forces(), s.info()["rebuilds"]))
+        s.close()
+    assert out[0][3] == out[1][3] and out[0][3] >= 3
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
+
+
 def test_set_state_resume_matches_uninterrupted(md):
     s1 = make(md, 1500, 0.3, 0.08, T=1.0, seed=8, precision=1, relax=10, thermostat_every=0)
     st0 = s1.state()
