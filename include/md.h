@@ -258,9 +258,9 @@ MD_API const char* md_last_error(void);
 
 /* Cluster analysis (same rules and results as md_clusters) on positions the
  * caller already holds in device memory, for callers that cannot allocate
- * device memory: code running inside another application's memory pool,
- * work enqueued while a CUDA graph is being captured, or loops that must not
- * stall on the allocator.  The paper has no counterpart; this is a service of
+ * device memory: code running inside another application's memory pool
+ * (a foreign allocation breaks its accounting), or loops that must not stall
+ * on the allocator.  The paper has no counterpart; this is a service of
  * the library.  It calls no cudaMalloc, cudaFree or allocating routine: its
  * working memory is one fixed file-scope device array, held by every GPU that
  * loads the library until the process exits.

@@ -4,9 +4,8 @@
 // Some callers hold their positions in device memory they manage themselves
 // and may not call cudaMalloc at all: code that runs inside another
 // application's memory pool or arena (where a foreign allocation breaks the
-// host's accounting or fragments its pool), work enqueued while a CUDA graph
-// is being captured (an allocation there is illegal or becomes part of the
-// graph), or real-time loops that must not stall on the allocator.  For them
+// host's accounting or fragments its pool), or real-time loops that must not
+// stall on the allocator (cudaMalloc can wait on the device).  For them
 // this entry point runs the same distance-linkage analysis as md_clusters on
 // caller-provided device buffers, and all its working memory is one
 // file-scope __device__ array of fixed size that every GPU loading the library
