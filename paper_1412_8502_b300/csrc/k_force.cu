@@ -358,7 +358,7 @@ __device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, c
 #pragma unroll kN3Unroll
         for (int k = 0; k < 16; ++k) step(k);
     }
-    if (kFull || (half | j) < n) {
+    if ((half | j) < n) {
         const int slot = __float_as_int(ph[0].w);
         T.bad |= !(fabsf(rx) < kForceMax && fabsf(ry) < kForceMax && fabsf(rz) < kForceMax);
         red_add(facc + slot, to_fix(rx));
@@ -384,7 +384,11 @@ __device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, c
 template <int kClass, bool kLo, bool kWrap, bool kEnergy>
 __device__ __forceinline__ void n3_any(const WarpQueues& Q, int n, int lane, const Targets& X, const PairConsts& C,
                                        Totals& T, long long* facc, int N) {
-    if (n == kTile) n3_block<kClass, kLo, kWrap, kEnergy, true>(Q, n, lane, X, C, T, facc, N);
+    // Without per-pair wrapping the unused slots of a partial block hold a
+    // far pad position (drain), whose pair terms vanish exactly (2^-huge = +0,
+    // out of range): the full-block code serves every block, which keeps the
+    // instruction footprint of the pass small.
+    if (n == kTile || !kWrap) n3_block<kClass, kLo, kWrap, kEnergy, true>(Q, n, lane, X, C, T, facc, N);
     else n3_block<kClass, kLo, kWrap, kEnergy, false>(Q, n, lane, X, C, T, facc, N);
 }
 
@@ -395,8 +399,11 @@ __device__ __forceinline__ void drain(WarpQueues& Q, int q, int cls, int& cnt, i
     __syncwarp();
     const int n = min(cnt, kTile);
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    // unused slots: zeros with per-pair wrapping (the partial-block code masks
+    // them), else a pad 1e9 fm away (all terms underflow to zero)
+    const float4 pad = kWrap ? zero : make_float4(kPad, kPad, kPad, 0.f);
     const int half = lane & 16, j = lane & 15;
-    const float4 h = lane < n ? Q.h[q][lane] : zero;
+    const float4 h = lane < n ? Q.h[q][lane] : pad;
     Q.dh[2 * half + j] = h;
     Q.dh[2 * half + 16 + j] = h;
     if (q != 1) {
