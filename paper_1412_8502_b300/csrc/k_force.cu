@@ -323,11 +323,13 @@ struct Targets {
 // one lane down within the half after every step: after 16 steps lane l holds
 // the whole reaction on source 16h + j.  One source load and one rotation
 // serve two pairs.
+// cross: unlike species (b - c), chosen at run time so that like and unlike
+// nuclear blocks share one instance of the code.
 template <int kClass, bool kLo, bool kWrap, bool kEnergy, bool kFull>
 __device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, const Targets& X,
-                                         const PairConsts& C, Totals& T, long long* facc, int N) {
-    const float S = (kClass == kNucCross) ? C.Scross : C.Ssame;
-    const float bS = (kClass == kNucCross) ? C.bcross : C.bsame;
+                                         const PairConsts& C, Totals& T, long long* facc, int N, bool cross) {
+    const float S = cross ? C.Scross : C.Ssame;
+    const float bS = cross ? C.bcross : C.bsame;
     float f0x = 0.f, f0y = 0.f, f0z = 0.f, f1x = 0.f, f1y = 0.f, f1z = 0.f;
     EAcc e{0.f, 0.f, 0.f, 0.f, 0.f};
     float rx = 0.0f, ry = 0.0f, rz = 0.0f;
@@ -383,13 +385,13 @@ __device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, c
 
 template <int kClass, bool kLo, bool kWrap, bool kEnergy>
 __device__ __forceinline__ void n3_any(const WarpQueues& Q, int n, int lane, const Targets& X, const PairConsts& C,
-                                       Totals& T, long long* facc, int N) {
+                                       Totals& T, long long* facc, int N, bool cross = false) {
     // Without per-pair wrapping the unused slots of a partial block hold a
     // far pad position (drain), whose pair terms vanish exactly (2^-huge = +0,
     // out of range): the full-block code serves every block, which keeps the
     // instruction footprint of the pass small.
-    if (n == kTile || !kWrap) n3_block<kClass, kLo, kWrap, kEnergy, true>(Q, n, lane, X, C, T, facc, N);
-    else n3_block<kClass, kLo, kWrap, kEnergy, false>(Q, n, lane, X, C, T, facc, N);
+    if (n == kTile || !kWrap) n3_block<kClass, kLo, kWrap, kEnergy, true>(Q, n, lane, X, C, T, facc, N, cross);
+    else n3_block<kClass, kLo, kWrap, kEnergy, false>(Q, n, lane, X, C, T, facc, N, cross);
 }
 
 // Evaluate the first min(cnt, 32) entries of queue q, shift the rest down.
@@ -422,8 +424,7 @@ __device__ __forceinline__ void drain(WarpQueues& Q, int q, int cls, int& cnt, i
     switch (cls) {
         case kPPNuc: n3_any<kPPNuc, true, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N); break;
         case kPPCoul: n3_any<kPPCoul, false, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N); break;
-        case kNucCross: n3_any<kNucCross, true, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N); break;
-        default: n3_any<kNucSame, true, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N); break;
+        default: n3_any<kNucSame, true, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N, cls == kNucCross); break;
     }
 }
 
