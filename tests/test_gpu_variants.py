@@ -72,3 +72,32 @@ def test_affine_option_trajectory_fp64(md):
     s0, _ = load(md, x, t, L, 1, T=1.0, thermostat_every=0, affine=0)
     s0.step(40, xi)
     assert np.abs(min_img(s0.state()["x"] - g["x"], r["L"])).max() > 1e-3
+
+
+def test_coulomb_cutoff_truncation_effect(md):
+    """The default Coulomb term stops at r_C = 40 fm (a reading of Sec. II.A);
+    the paper sums every proton pair at its nearest image.  On one 51,200-
+    nucleon state (L0 = 86.2 fm, density 0.080 fm^-3) the two differ by an
+    energy offset and a small force change (measured on B300: force relative
+    L2 7.9e-4, PE_coul 19.48 vs 20.66 MeV per proton); the test records both
+    and bounds them, so the reading's effect on the physics is known."""
+    p = md.md_params_default()
+    p.relax_iters = 100
+    s = md.System(51200, 0.30, 0.080, 1.0, 2, p)
+    assert abs(s.params.r_C - 40.0) < 1e-12
+    F40, e40 = s.forces(), s.energy()
+    q = s.params
+    q.coulomb = 2
+    s.params = q
+    Fall, eall = s.forces(), s.energy()
+    s.close()
+    dF = rel_l2(F40, Fall)
+    n_p = int(np.floor(0.30 * 51200 + 0.5))
+    dE = (eall["PE_coul"] - e40["PE_coul"]) / n_p
+    print(f"r_C = 40 fm vs all pairs: force rel L2 {dF:.2e}, PE_coul {e40['PE_coul'] / n_p:.4f} vs "
+          f"{eall['PE_coul'] / n_p:.4f} MeV per proton (difference {dE:.4f})")
+    assert dF < 1e-2
+    assert 0.0 < dE < 0.1 * abs(eall["PE_coul"]) / n_p
+    # the nuclear term is the same; with the all-pairs Coulomb kernel the
+    # proton pairs' nuclear part is summed in another grouping (FP32 partials)
+    assert abs(e40["PE_nuc"] - eall["PE_nuc"]) <= 1e-8 * abs(eall["PE_nuc"])
