@@ -278,7 +278,6 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     A(&c.slot, (size_t)N);
     A(&c.xhi, (size_t)s.T * kTile);
     A(&c.xlo, (size_t)s.T * kTile);
-    A(&c.torg, 3 * (size_t)s.T);
     A(&c.torgf, 4 * (size_t)s.T);
     A(&c.thalf, 3 * (size_t)s.T);
     A(&c.sorg, (size_t)(s.T + kTile - 1) / kTile);

@@ -361,21 +361,24 @@ __global__ void k_tiles(EngineDev E) {
     const int cn = st->cur_next;
     const int N = S.N;
     const double* x = S.x[cn];
-    double c[3] = {0.0, 0.0, 0.0}, h[3] = {0.0, 0.0, 0.0};
+    // FP32 box from the FP64 bounds: the lower bound truncated (positions are
+    // >= 0), the upper one truncated and stepped one unit up; no FP64
+    // arithmetic (FP64 instructions occupy the narrow FP64 unit even with
+    // one active lane).  FP32 rounding of the centre and half extents
+    // (< 1e-4 fm below 2000 fm) is covered by the list build's margin.
+    float c[3], h[3];
     double xv[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         xv[a] = valid ? x[a * N + p] : 0.0;
         double lo, hi;
         warp_bounds(xv[a], valid, lo, hi);
-        if (lane == 0) {                 // FP64 arithmetic on one lane only
-            c[a] = 0.5 * (lo + hi);
-            h[a] = 0.5 * (hi - lo);
-        }
+        const float lf = narrow_trunc(lo);
+        const float hf = __uint_as_float(__float_as_uint(narrow_trunc(hi)) + 1u);
+        c[a] = 0.5f * (lf + hf);
+        h[a] = 0.5f * (hf - lf);
     }
     const double L = st->L;
-    if (lane == 0)
-        for (int a = 0; a < 3; ++a) S.torg[3 * t + a] = c[a];
     // The box is that of the wrapped positions themselves (a Hilbert run of
     // [0, L)^3 does not wrap), so every position is within h <= L/2 of the
     // origin and is its own image nearest the origin.
@@ -386,15 +389,15 @@ __global__ void k_tiles(EngineDev E) {
         S.disp[2 * N + p] = 0.0f;
     }
     if (lane == 0) {
-        const float hm = (float)fmax(h[0], fmax(h[1], h[2]));
+        const float hm = fmaxf(h[0], fmaxf(h[1], h[2]));
         for (int a = 0; a < 3; ++a) {
             // round the FP32 box up so the FP32 range test stays conservative
-            S.thalf[3 * t + a] = (float)h[a] * (1.0f + 1e-6f) + 1e-6f;
-            S.torgf[4 * t + a] = (float)c[a];
+            S.thalf[3 * t + a] = h[a] * (1.0f + 1e-6f) + 1e-6f;
+            S.torgf[4 * t + a] = c[a];
         }
         S.torgf[4 * t + 3] = hm;
         s_hm[w] = hm;
-        s_hs[w] = (float)((h[0] + h[1] + h[2]) / 3.0);
+        s_hs[w] = (h[0] + h[1] + h[2]) * (1.0f / 3.0f);
         if (t == 0) {
             st->last_build = st->step;
             st->n_rebuilds += 1;

@@ -12,7 +12,7 @@
 // [Np + 32 u, ...) ∩ [Np, N).  Positions and velocities are FP64 (x[a*N + p]
 // is axis a of sorted slot p).  The force kernel reads each position as a
 // pair of FP32 numbers, xhi + xlo, of the periodic image nearest its tile's
-// origin O_t (FP64, fixed at the last pair-list rebuild), refreshed every
+// origin O_t (fixed at the last pair-list rebuild), refreshed every
 // step: xhi[32 t + lane] = xt rounded to 24 significant bits, xlo = the
 // remainder rounded to FP32 (|xt - xhi - xlo| <= 2^-49 |xt|).
 #pragma once
@@ -117,7 +117,6 @@ struct SysConst {
     int* slot;               // [N] scatter scratch
     float4* xhi;             // [T*32] FP32 high part of the tile-frame position
     float4* xlo;             // [T*32] FP32 low part (xhi + xlo = position)
-    double* torg;            // [T*3] FP64 tile origins
     float* torgf;            // [T*4] FP32 origin (x,y,z) and max half-extent
     float* thalf;            // [T*3] tile half-extents at rebuild
     float4* sorg;            // [ceil(T/32)] super-tile (32 tiles) box centre
