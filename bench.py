@@ -163,6 +163,8 @@ def run_gpu(args):
         p.skin = 4.0
     if args.skin is not None:
         p.skin = args.skin
+    if args.sort_bits is not None:
+        p.sort_bits = args.sort_bits
     if args.plain_graph:                # profiling: ncu does not look inside graphs with conditional nodes
         p.cond_graph = 0
     sys_ = md.System(N, W["Yp"], W["rho"], W["T"], replicas.replica_seed(W["seed"], rank), p)
@@ -535,6 +537,7 @@ def main():
     ap.add_argument("--skin", type=float, default=None, help="pair-list skin / Verlet delta r, fm")
     ap.add_argument("--timing", default="key", choices=["key", "full"],
                     help="CUDA events inside the timed region: around the key kernels (default) or every kernel")
+    ap.add_argument("--sort-bits", type=int, default=None, help="spatial-sort bits per axis (default: from N)")
     ap.add_argument("--plain-graph", action="store_true",
                     help="rebuild kernels as plain graph nodes instead of conditional ones (for kernel profilers)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
