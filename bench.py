@@ -466,6 +466,7 @@ def run_serve(n_jobs, steps, rate, seed=5):
             "step_p50_ms": lat[len(lat) // 2] if lat else None, "step_p99_ms": p99,
             "wait_ms_max": max(r["wait_ms"] for r in ok) if ok else None,
             "job_N": [j["N"] for j in jobs],
+            "job_step_p99_ms": {int(r["N"]): round(r["step_p99_ms"], 3) for r in ok},
             "note": "N log-uniform in [2000, %d], Yp/T from the sweep, rho 0.080 -> U[0.005,0.02] over the job's "
                     "steps; p50 = median over jobs of each job's median step latency, p99 = max over jobs of "
                     "each job's 99th percentile; serial = the same arrival trace served one job at a time "

@@ -107,8 +107,8 @@ int fail(int code, const std::string& msg) {
 }
 const char* last_error_cstr() { return g_err.c_str(); }
 
-Engine::Engine() {
-    cudaStreamCreateWithFlags(&own_stream_, cudaStreamNonBlocking);
+Engine::Engine(int priority) {
+    cudaStreamCreateWithPriority(&own_stream_, cudaStreamNonBlocking, priority);
     cudaStreamCreateWithFlags(&aux_stream_, cudaStreamNonBlocking);
     stream_ = own_stream_;
     H_.owner = this;

@@ -46,7 +46,9 @@ struct GraphRec {
 
 class Engine {
 public:
-    Engine();
+    // priority: of the engine's own stream (CUDA stream priority; 0 = default,
+    // lower values are scheduled first where the device supports it)
+    explicit Engine(int priority = 0);
     ~Engine();
 
     // Allocate and register a system; returns MD_OK or an error code.

@@ -156,7 +156,15 @@ void md_server::admit() {
             continue;
         }
         j->t_admit = Clock::now();
-        Engine* e = new Engine();
+        // Stream priority by job size: a small job's short kernels are
+        // scheduled ahead of the large jobs' long force passes as SMs free up,
+        // which bounds its step latency without slowing the large jobs much.
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);   // lo: least urgent, hi: most urgent
+        int prio = lo;
+        if (j->job.N < 20000) prio = hi;
+        else if (j->job.N < 100000) prio = (lo + hi) / 2;
+        Engine* e = new Engine(prio);
         int rc = e->add_system(j->job.N, j->job.Yp, j->job.rho, j->job.T, j->job.seed, prm);
         if (!rc) rc = e->build_tables();
         if (!rc) rc = e->initialise_async(false);   // relaxation follows in slices
