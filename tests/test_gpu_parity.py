@@ -93,7 +93,7 @@ def cfg_relaxed(N, Yp, rho, seed, iters=40):
 
 
 CONFIGS = {
-    "cfg1_liquid_2000": lambda: cfg_liquid(2000, 0.30, 0.080, 3),
+    "liquid_2000": lambda: cfg_liquid(2000, 0.30, 0.080, 3),
     "liquid_8000_yp04": lambda: cfg_liquid(8000, 0.40, 0.080, 4),
     "drops_3000_dilute": lambda: cfg_drops(3000, 0.30, 0.005, 5),
     "relaxed_1500": lambda: cfg_relaxed(1500, 0.30, 0.080, 6),
@@ -258,7 +258,7 @@ def test_plain_and_conditional_step_graphs_agree_bitwise(md):
     """The rebuild kernels in conditional graph nodes (default) or as plain
     nodes that return at once without a rebuild: the same kernels run on
     the same data, so trajectories (through several rebuilds) are identical."""
-    x, t, L = CONFIGS["cfg1_liquid_2000"]()
+    x, t, L = CONFIGS["liquid_2000"]()
     out = []
     for cond in (1, 0):
         s, v = load(md, x, t, L, 0, cond_graph=cond)
@@ -297,7 +297,7 @@ def _check_clusters(s, x, t, L):
     assert st["A_mean"] == sto[2] and st["Z_mean"] == sto[3] and st["n_big"] == sto[4]
 
 
-@pytest.mark.parametrize("name", ["drops_3000_dilute", "cfg1_liquid_2000", "liquid_4096_yp005"])
+@pytest.mark.parametrize("name", ["drops_3000_dilute", "liquid_2000", "liquid_4096_yp005"])
 def test_clusters_bit_exact(md, name):
     x, t, L = CONFIGS[name]()
     s, _ = load(md, x, t, L, 0)
