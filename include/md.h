@@ -115,12 +115,15 @@ typedef struct {
                             (md_step_energy only) */
 } md_energy_t;
 
-/* State exchange (md_get_state / md_set_state).  The caller owns x, v
+/* State exchange (md_get_state / md_set_state).  The caller owns x, v, f
  * ([N][3] doubles, original order) and type ([N], 1 = proton); any of the
- * three pointers may be NULL on md_get_state to skip that array.
+ * four pointers may be NULL on md_get_state to skip that array.
  * L(t) = L_base * (1 + xi_dot * (t - t_base)) is Eq. (3) re-based at t_base.
- * L_F is the box side the cached forces were evaluated with (the forces
- * that the next half-kick uses). */
+ * f are the cached forces (MeV/fm) that the next half-kick of velocity
+ * Verlet uses, evaluated at x with box side L_F: (x, v, f, L_F) is the whole
+ * integrator state, so a state saved with f and loaded with f continues
+ * without a fresh force evaluation (in split precision the forces are FP32
+ * values, which round-trip exactly through doubles). */
 typedef struct {
     int64_t N, Np;
     double* x;
@@ -128,6 +131,7 @@ typedef struct {
     int8_t* type;
     double L, L_base, t, t_base, xi_dot, L_F;
     int64_t step;
+    double* f;
 } md_state_view;
 
 typedef struct {
@@ -224,8 +228,10 @@ MD_API int md_clusters_mste(md_system* s, int32_t* labels, int64_t* hist_A, int6
 /* Copy the state to the caller (md_state_view above). */
 MD_API int md_get_state(md_system* s, md_state_view* view);
 /* Replace x, v (and the clock fields) from the caller; N and Np must match,
- * x is wrapped into [0, L).  Forces are re-evaluated at the new state.  Used
- * for resume and for parity checks. */
+ * x is wrapped into [0, L).  With f == NULL the forces are re-evaluated at
+ * the new state (box side L); otherwise f (evaluated with box side L_F, as
+ * md_get_state returns them) become the cached forces and no force pass
+ * runs.  Used for resume and for parity checks. */
 MD_API int md_set_state(md_system* s, const md_state_view* view);
 
 MD_API int md_get_info(const md_system* s, md_info_t* info);

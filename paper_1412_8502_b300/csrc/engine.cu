@@ -830,13 +830,17 @@ int Engine::clusters_mste(int idx, int32_t* labels, int64_t* hA, int64_t* hZ, md
 
 int Engine::get_state(int idx, md_state_view* v) {
     SysHost& h = *sys[idx];
+    int rc;
+    if (v->f && h.dirty && (rc = refresh(idx))) return rc;
     double* dx = h.d_stage;
     double* dv = h.d_stage + 3 * h.N;
-    launch_gather(H_, stream_, idx, v->x ? dx : nullptr, v->v ? dv : nullptr, nullptr,
+    double* df = h.d_stage + 6 * h.N;
+    launch_gather(H_, stream_, idx, v->x ? dx : nullptr, v->v ? dv : nullptr, v->f ? df : nullptr,
                   v->type ? h.d_stage_t : nullptr);
     CK(cudaGetLastError());
     if (v->x) CK(cudaMemcpyAsync(v->x, dx, sizeof(double) * 3 * h.N, cudaMemcpyDeviceToHost, stream_));
     if (v->v) CK(cudaMemcpyAsync(v->v, dv, sizeof(double) * 3 * h.N, cudaMemcpyDeviceToHost, stream_));
+    if (v->f) CK(cudaMemcpyAsync(v->f, df, sizeof(double) * 3 * h.N, cudaMemcpyDeviceToHost, stream_));
     if (v->type) CK(cudaMemcpyAsync(v->type, h.d_stage_t, h.N, cudaMemcpyDeviceToHost, stream_));
     SysState st;
     CK(cudaMemcpyAsync(&st, h.d_st, sizeof(st), cudaMemcpyDeviceToHost, stream_));
@@ -863,15 +867,26 @@ int Engine::set_state(int idx, const md_state_view* v) {
         for (int64_t i = 0; i < h.N; ++i)
             if (v->type[i] != (i < h.Np ? 1 : 0)) return fail(MD_EINVAL, "type must list protons first");
     }
+    if (v->f && !(v->L_F > 0.0)) return fail(MD_EINVAL, "L_F must be > 0 when forces are given");
     double clock[8] = {v->L, v->L_base > 0 ? v->L_base : v->L, v->t, v->t_base, v->xi_dot, (double)v->step,
-                       v->L, 0.0};
+                       v->f ? v->L_F : v->L, 0.0};
     CK(cudaMemcpyAsync(h.d_stage, v->x, sizeof(double) * 3 * h.N, cudaMemcpyHostToDevice, stream_));
     CK(cudaMemcpyAsync(h.d_stage + 3 * h.N, v->v, sizeof(double) * 3 * h.N, cudaMemcpyHostToDevice, stream_));
+    if (v->f)
+        CK(cudaMemcpyAsync(h.d_stage + 6 * h.N, v->f, sizeof(double) * 3 * h.N, cudaMemcpyHostToDevice, stream_));
     CK(cudaMemcpyAsync(d_clock_, clock, sizeof(clock), cudaMemcpyHostToDevice, stream_));
     launch_set_clock(H_, stream_, idx, d_clock_);
     launch_scatter_state(H_, stream_, idx, h.d_stage, h.d_stage + 3 * h.N);
-    int rc = refresh(idx);
-    if (rc) return rc;
+    int rc;
+    if (v->f) {
+        // the caller's forces: sort into tiles, then place them by particle id
+        launch_rebuild(H_, stream_, 1, idx);
+        launch_scatter_forces(H_, stream_, idx, h.d_stage + 6 * h.N);
+        CK(cudaGetLastError());
+        h.dirty = false;
+    } else if ((rc = refresh(idx))) {
+        return rc;
+    }
     h.host_step = v->step;
     h.xi = v->xi_dot;
     return check_errors();

@@ -418,6 +418,20 @@ __global__ void k_scatter_state(EngineDev E, int only, const double* ix, const d
     S.id[0][p] = p;
 }
 
+// Load caller forces (AoS, original order) into the cached force array of
+// the current slot order (after the rebuild that follows a loaded state):
+// slot p holds particle id[p].
+template <typename FT>
+__global__ void k_scatter_forces(EngineDev E, int only, const double* f) {
+    Slot o;
+    if (!slot_of(E, only, o) || !o.valid) return;
+    const SysConst& S = E.sys[o.s];
+    const int c = S.st->cur, N = S.N, p = o.p;
+    const int i = S.id[c][p];
+    FT* F = const_cast<FT*>(cur_force<FT>(S, c));
+    for (int a = 0; a < 3; ++a) F[a * N + p] = (FT)f[3 * i + a];
+}
+
 // Clock and bookkeeping of a loaded state: d_clock = {L, L_base, t, t_base,
 // xi_dot, step, L_F}.  Slot order becomes the identity; forces are stale.
 __global__ void k_set_clock(EngineDev E, int only, const double* c) {
@@ -527,6 +541,13 @@ void launch_set_rate(const EngineHost& H, cudaStream_t s, int only, double xi_do
 void launch_scatter_state(const EngineHost& H, cudaStream_t s, int only, const double* ix, const double* iv) {
     const EngineDev& E = H.dev;
     k_scatter_state<<<nblk(E), kBlock, 0, s>>>(E, only, ix, iv);
+    H.count(1);
+}
+
+void launch_scatter_forces(const EngineHost& H, cudaStream_t s, int only, const double* iforce) {
+    const EngineDev& E = H.dev;
+    if (H.precision == 1) k_scatter_forces<double><<<nblk(E), kBlock, 0, s>>>(E, only, iforce);
+    else k_scatter_forces<float><<<nblk(E), kBlock, 0, s>>>(E, only, iforce);
     H.count(1);
 }
 

@@ -60,6 +60,7 @@ void launch_energy_now(const EngineHost& H, cudaStream_t s, int only, double* d_
 void launch_gather(const EngineHost& H, cudaStream_t s, int only, double* ox, double* ov, double* of,
                    int8_t* otype);
 void launch_scatter_state(const EngineHost& H, cudaStream_t s, int only, const double* ix, const double* iv);
+void launch_scatter_forces(const EngineHost& H, cudaStream_t s, int only, const double* iforce);
 void launch_set_clock(const EngineHost& H, cudaStream_t s, int only, const double* d_clock);
 void launch_set_rate(const EngineHost& H, cudaStream_t s, int only, double xi_dot);
 void launch_clusters(const EngineHost& H, cudaStream_t s, int only, int Np, int N, int Tp, int T,

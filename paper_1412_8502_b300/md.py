@@ -50,7 +50,7 @@ class md_energy_t(ctypes.Structure):
 class md_state_view(ctypes.Structure):
     _fields_ = [("N", _I64), ("Np", _I64), ("x", ctypes.POINTER(_D)), ("v", ctypes.POINTER(_D)),
                 ("type", ctypes.POINTER(ctypes.c_int8)), ("L", _D), ("L_base", _D), ("t", _D),
-                ("t_base", _D), ("xi_dot", _D), ("L_F", _D), ("step", _I64)]
+                ("t_base", _D), ("xi_dot", _D), ("L_F", _D), ("step", _I64), ("f", ctypes.POINTER(_D))]
 
 
 class md_cluster_stats(ctypes.Structure):
@@ -198,40 +198,79 @@ def md_get_info(h) -> dict:
     return {k: getattr(i, k) for k, _ in md_info_t._fields_}
 
 
-def md_get_state(h, N: int, x=True, v=True, type=True, out=None) -> dict:
-    """State in original particle order.  `out` may supply preallocated
-    (x, v) arrays (e.g. pinned host memory) of shape (N, 3)."""
+def _state_array(a, N, what):
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.shape == (N, 3) and a.flags.c_contiguous):
+        raise ValueError(f"{what} must be a C-contiguous float64 array of shape ({N}, 3)")
+    return a
+
+
+def md_get_state(h, N: int, x=True, v=True, type=True, out=None, f=False) -> dict:
+    """State in original particle order.  f: also the cached forces (the
+    ones the next half-kick uses, evaluated with box side L_F).  `out` may
+    supply preallocated (x, v) or (x, v, f) arrays (e.g. pinned host memory)
+    of shape (N, 3)."""
+    fs = None
     if out is not None:
-        xs, vs = out
+        xs, vs = _state_array(out[0], N, "x"), _state_array(out[1], N, "v")
+        if len(out) > 2 and out[2] is not None:
+            fs = _state_array(out[2], N, "f")
     else:
         xs = np.empty((N, 3)) if x else None
         vs = np.empty((N, 3)) if v else None
+        fs = np.empty((N, 3)) if f else None
     ts = np.empty(N, dtype=np.int8) if type else None
     view = md_state_view()
     view.x = _dp(xs) if xs is not None else None
     view.v = _dp(vs) if vs is not None else None
+    view.f = _dp(fs) if fs is not None else None
     view.type = ts.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)) if ts is not None else None
     _ck(LIB.md_get_state(h, ctypes.byref(view)), "md_get_state")
-    return dict(x=xs, v=vs, type=ts, N=view.N, Np=view.Np, L=view.L, L_base=view.L_base, t=view.t,
+    return dict(x=xs, v=vs, f=fs, type=ts, N=view.N, Np=view.Np, L=view.L, L_base=view.L_base, t=view.t,
                 t_base=view.t_base, xi_dot=view.xi_dot, L_F=view.L_F, step=view.step)
 
 
-def md_set_state(h, x, v, L, L_base=None, t=0.0, t_base=0.0, xi_dot=0.0, step=0, Np=None) -> None:
+def md_set_state(h, x, v, L, L_base=None, t=0.0, t_base=0.0, xi_dot=0.0, step=0, Np=None, f=None,
+                 L_F=None) -> None:
+    """Load x, v (and the clock).  With f (forces as md_get_state returns
+    them, evaluated with box side L_F) the forces are restored instead of
+    re-evaluated."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     v = np.ascontiguousarray(v, dtype=np.float64)
     N = x.shape[0]
+    if f is not None:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.shape != (N, 3):
+            raise ValueError(f"f must have shape ({N}, 3)")
     if Np is None:
         Np = md_get_info(h)["Np"]
     view = md_state_view(N=N, Np=Np, x=_dp(x), v=_dp(v), type=None, L=float(L),
                          L_base=float(L if L_base is None else L_base), t=float(t), t_base=float(t_base),
-                         xi_dot=float(xi_dot), L_F=float(L), step=int(step))
+                         xi_dot=float(xi_dot), L_F=float(L if L_F is None else L_F), step=int(step),
+                         f=_dp(f) if f is not None else None)
     _ck(LIB.md_set_state(h, ctypes.byref(view)), "md_set_state")
 
 
-def md_clusters(h, N: int, Np: int, labels=True, fn="md_clusters"):
-    lab = np.empty(N, dtype=np.int32) if labels else None
-    hA = np.zeros(N + 1, dtype=np.int64)
-    hZ = np.zeros(Np + 1, dtype=np.int64)
+def _out_array(a, n, dt, what):
+    if not (isinstance(a, np.ndarray) and a.dtype == dt and a.shape == (n,) and a.flags.c_contiguous
+            and a.flags.writeable):
+        raise ValueError(f"{what} must be a writeable C-contiguous {np.dtype(dt).name}[{n}] array")
+    return a
+
+
+def md_clusters(h, N: int, Np: int, labels=True, fn="md_clusters", out=None):
+    """Labels (int32[N], or None when labels is False), hist_A (int64[N+1]),
+    hist_Z (int64[Np+1]) and the statistics.  out: optional (labels or None,
+    hist_A, hist_Z) arrays to fill instead of new ones (e.g. page-locked
+    buffers reused across calls); they are returned."""
+    if out is not None:
+        lab, hA, hZ = out
+        lab = _out_array(lab, N, np.int32, "labels") if labels else None
+        hA = _out_array(hA, N + 1, np.int64, "hist_A")
+        hZ = _out_array(hZ, Np + 1, np.int64, "hist_Z")
+    else:
+        lab = np.empty(N, dtype=np.int32) if labels else None
+        hA = np.zeros(N + 1, dtype=np.int64)
+        hZ = np.zeros(Np + 1, dtype=np.int64)
     st = md_cluster_stats()
     _ck(getattr(LIB, fn)(h, lab.ctypes.data_as(ctypes.POINTER(_I32)) if lab is not None else None,
                          hA.ctypes.data_as(ctypes.POINTER(_I64)), hZ.ctypes.data_as(ctypes.POINTER(_I64)),
@@ -239,8 +278,8 @@ def md_clusters(h, N: int, Np: int, labels=True, fn="md_clusters"):
     return lab, hA, hZ, {k: getattr(st, k) for k, _ in md_cluster_stats._fields_}
 
 
-def md_clusters_mste(h, N: int, Np: int, labels=True):
-    return md_clusters(h, N, Np, labels, fn="md_clusters_mste")
+def md_clusters_mste(h, N: int, Np: int, labels=True, out=None):
+    return md_clusters(h, N, Np, labels, fn="md_clusters_mste", out=out)
 
 
 def md_clusters_noalloc(d_x, N, Np, L, r_pp, r_np, d_labels, d_hist_A, d_hist_Z, d_counts, stream=None) -> None:
@@ -393,17 +432,17 @@ class System:
     def step_energy(self):
         return md_step_energy(self.h)
 
-    def state(self, out=None):
-        return md_get_state(self.h, self.N, out=out)
+    def state(self, out=None, f=False):
+        return md_get_state(self.h, self.N, out=out, f=f)
 
     def set_state(self, x, v, L, **kw):
         md_set_state(self.h, x, v, L, Np=self.Np, **kw)
 
-    def clusters(self, labels=True):
-        return md_clusters(self.h, self.N, self.Np, labels)
+    def clusters(self, labels=True, out=None):
+        return md_clusters(self.h, self.N, self.Np, labels, out=out)
 
-    def clusters_mste(self, labels=True):
-        return md_clusters_mste(self.h, self.N, self.Np, labels)
+    def clusters_mste(self, labels=True, out=None):
+        return md_clusters_mste(self.h, self.N, self.Np, labels, out=out)
 
     def info(self):
         return md_get_info(self.h)

@@ -57,3 +57,33 @@ def test_no_device_is_an_error_not_a_fallback(lib_path):
     assert md.LIB.md_batch_create(0, None, None, ctypes.byref(h)) == md.MD_EINVAL
     sv = ctypes.c_void_p()
     assert md.LIB.md_server_create(1 << 30, None, ctypes.byref(sv)) == md.MD_ENODEV
+
+
+def test_cluster_output_buffers_are_checked(lib_path):
+    """Caller-supplied cluster output arrays: wrong size, dtype or layout is
+    rejected before the library is called."""
+    import numpy as np
+    from paper_1412_8502_b300 import md
+    N, Np = 10, 4
+    good = (np.empty(N, np.int32), np.empty(N + 1, np.int64), np.empty(Np + 1, np.int64))
+    bad = [(good[0], np.empty(N, np.int64), good[2]),                  # hist_A one short
+           (good[0], good[1], np.empty(Np + 1, np.int32)),               # hist_Z wrong dtype
+           (np.empty(2 * N, np.int32)[::2], good[1], good[2]),           # labels not contiguous
+           (good[0], good[1], np.empty((Np + 1, 1), np.int64))]          # hist_Z 2-D
+    for out in bad:
+        with pytest.raises(ValueError):
+            md.md_clusters(None, N, Np, True, out=out)
+
+
+def test_state_arrays_are_checked(lib_path):
+    """Caller-supplied state arrays of the wrong shape or dtype are rejected
+    before the library is called."""
+    import numpy as np
+    from paper_1412_8502_b300 import md
+    N = 8
+    ok = np.empty((N, 3))
+    for out in [(np.empty((N, 2)), ok), (ok, np.empty((N, 3), np.float32)), (ok, ok, np.empty((N + 1, 3)))]:
+        with pytest.raises(ValueError):
+            md.md_get_state(None, N, out=out)
+    with pytest.raises(ValueError):
+        md.md_set_state(None, ok, ok, 10.0, Np=2, f=np.empty((N, 2)))

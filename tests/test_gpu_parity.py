@@ -317,6 +317,13 @@ def test_clusters_after_dynamics_and_edges(md):
     ts = np.array([1, 1, 1, 1, 1, 0, 0, 0], np.int8)
     s2, _ = load(md, xs, ts, L, 0)
     _check_clusters(s2, xs, ts, L)
+    # caller-supplied output arrays: same results, filled in place (twice)
+    lab, hA, hZ, st = s.clusters()
+    out = (np.full(s.N, -7, np.int32), np.full(s.N + 1, 9, np.int64), np.full(s.Np + 1, 9, np.int64))
+    for _ in range(2):
+        lab2, hA2, hZ2, st2 = s.clusters(out=out)
+        assert lab2 is out[0] and hA2 is out[1] and hZ2 is out[2]
+        assert np.array_equal(lab, lab2) and np.array_equal(hA, hA2) and np.array_equal(hZ, hZ2) and st == st2
 
 
 # --------------------------------------------------------------- full size
@@ -341,3 +348,37 @@ def test_full_size_sampled_forces(md, N, Yp, T, seed):
     assert info["rebuilds"] >= 2
     e = s.energy()
     assert np.isfinite(e["KE"] + e["PE_nuc"] + e["PE_coul"])
+
+
+# --------------------------------------------------------------- state round trip
+@pytest.mark.parametrize("precision", [0, 1])
+def test_state_round_trip_with_forces(md, precision):
+    """md_get_state with f returns the cached forces; md_set_state with them
+    restores them bit for bit (no fresh force pass), and the restored system
+    continues the trajectory of the original one (differences only from the
+    FP32 summation order of the re-sorted tiles)."""
+    x, t, L = CONFIGS["liquid_2000"]()
+    s, _ = load(md, x, t, L, precision)
+    xi = 7.5e-5
+    s.step(7, xi)
+    g = s.state(f=True)
+    assert np.array_equal(g["f"], s.forces())
+    s2 = make(md, len(x), float(t.sum()) / len(x), len(x) / L ** 3, precision=precision)
+    kw = dict(L_base=g["L_base"], t=g["t"], t_base=g["t_base"], xi_dot=g["xi_dot"], step=g["step"])
+    s2.set_state(g["x"], g["v"], g["L"], f=g["f"], L_F=g["L_F"], **kw)
+    g2 = s2.state(f=True)
+    assert np.array_equal(g2["f"], g["f"]) and np.array_equal(s2.forces(), g["f"])
+    assert g2["L_F"] == g["L_F"] and g2["L"] == g["L"] and g2["step"] == g["step"]
+    assert np.array_equal(g2["x"], g["x"]) and np.array_equal(g2["v"], g["v"])
+    s.step(5, xi)
+    s2.step(5, xi)
+    a, b = s.state(), s2.state()
+    tol = 1e-12 if precision == 1 else 1e-6
+    assert rel_l2(b["x"], a["x"]) < tol and rel_l2(b["v"], a["v"]) < tol
+    # without f the forces are re-evaluated at the loaded positions, with the
+    # loaded box side (here L_F, the side the saved forces were evaluated with)
+    s3 = make(md, len(x), float(t.sum()) / len(x), len(x) / L ** 3, precision=precision)
+    s3.set_state(g["x"], g["v"], g["L_F"])
+    assert rel_l2(s3.forces(), g["f"]) < (1e-12 if precision == 1 else 1e-5)
+    for q in (s, s2, s3):
+        q.close()
