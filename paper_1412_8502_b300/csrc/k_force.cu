@@ -31,7 +31,8 @@
 // part only, an error below 1e-4 fm at r > 12 fm.  Energies are combined in
 // FP64.
 //
-// FP64 validation mode: full lists, one FP64 thread per target, no sharing.
+// FP64 validation mode: full lists, one FP64 lane per target and list
+// entry stride, no sharing; an FP32 screen passes the pairs near a cutoff.
 //
 // Single-exponential nuclear term: with g = exp(-r^2/(2 Lambda)),
 // exp(-r^2/Lambda) = g^2, so one ex2 serves both Gaussians of Eq. (1).
@@ -892,11 +893,24 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fix(EngineDev E, int
 }
 
 // ---------------------------------------------------------------- FP64
-// Validation mode: FP64 positions, per-pair nearest image, FP64 exp/sqrt.
+// Validation mode: FP64 positions, per-pair nearest image, FP64 exp/sqrt,
+// full lists (each pair evaluated for both particles, no sharing).  One
+// block of kFW warps per target tile: warp w takes list entries w, w + kFW,
+// ..., lane l target l of the tile; the warps' partial sums are added in
+// warp order (deterministic).  A pair first passes an FP32 screen on the
+// tile-frame hi + lo positions against the largest cutoff that applies plus
+// a band far wider than the FP32 error of the screen (2e-3 relative +
+// 1e-3 fm^2), so only pairs that may lie inside a cutoff reach the FP64
+// arithmetic, whose own comparisons decide.
+constexpr int kFW = 16;
+
 template <bool kEnergy>
-__global__ void __launch_bounds__(kForceWarps * 32) k_force_fp64(EngineDev E, int only, int out_alt) {
-    __shared__ double sb[kForceWarps][3][kTile];
-    const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(kFW * 32) k_force_fp64(EngineDev E, int only, int out_alt) {
+    __shared__ double sb[kFW][3][kTile];
+    __shared__ float4 sh[kFW][kTile], sl[kFW][kTile];
+    __shared__ double red[kFW][3][kTile];
+    __shared__ double ered[kFW][5];
+    const int g = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (g >= E.ntiles) return;
     const int s = E.tile_sys[g];
@@ -906,75 +920,119 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fp64(EngineDev E, in
     if (I >= S.T) return;
     SysState* st = S.st;
     const double L = st->L, hL = 0.5 * L;
+    const float Lhi = __double2float_rn(L), Llo = __double2float_rn(L - (double)Lhi), iLf = 1.0f / Lhi;
     const int N = S.N;
     const double* x = S.x[st->cur];
     const int p = tile_slot0(S, I) + lane;
     const bool valid = p < tile_end(S, I);
-    const double xi = valid ? x[p] : 1e30, yi = valid ? x[N + p] : 1e30, zi = valid ? x[2 * N + p] : 1e30;
+    const double xi = valid ? x[p] : 0.0, yi = valid ? x[N + p] : 0.0, zi = valid ? x[2 * N + p] : 0.0;
+    const float4 hi = S.xhi[I * kTile + lane], lo = S.xlo[I * kTile + lane];
     const bool Ip = I < S.Tp;
     const double rn2 = S.r_nuc * S.r_nuc, rc2 = S.r_C * S.r_C;
-    const double A2 = 2.0 * S.a / S.Lambda;
+    const double A2 = 2.0 * S.a / S.Lambda, i2L = 1.0 / (2.0 * S.Lambda), iLam = 1.0 / S.Lambda;
+    const double il = 1.0 / S.lambda_s;
+    const float lim_n = (float)rn2 * (1.0f + 2e-3f) + 1e-3f;
+    const float lim_c = (float)fmax(rn2, rc2) * (1.0f + 2e-3f) + 1e-3f;
     double fx = 0, fy = 0, fz = 0, en = 0, ec = 0, wv = 0;
     int nn = 0, nc = 0;
     const int* lst = S.list + (long long)I * S.T;
-    const int e0 = 0, e1 = S.lcount[I], nnear = S.lnear[I];
-    for (int e = e0; e < e1; ++e) {
+    const int e1 = S.lcount[I], nnear = S.lnear[I];
+    for (int e = w; e < e1; e += kFW) {
         const int J = lst[list_pos(S, e, nnear)] & kJMask;
         const int q = tile_slot0(S, J) + lane;
-        const bool qv = q < tile_end(S, J);
+        const int nq = tile_end(S, J) - tile_slot0(S, J);
+        const bool qv = lane < nq;
         __syncwarp();
-        sb[w][0][lane] = qv ? x[q] : -1e30;
-        sb[w][1][lane] = qv ? x[N + q] : -1e30;
-        sb[w][2][lane] = qv ? x[2 * N + q] : -1e30;
+        sb[w][0][lane] = qv ? x[q] : 0.0;
+        sb[w][1][lane] = qv ? x[N + q] : 0.0;
+        sb[w][2][lane] = qv ? x[2 * N + q] : 0.0;
+        sh[w][lane] = S.xhi[J * kTile + lane];
+        sl[w][lane] = S.xlo[J * kTile + lane];
         __syncwarp();
         const bool Jp = J < S.Tp;
         const bool pp = Ip && Jp && S.coulomb == 1;
         const double bc = (Ip == Jp) ? (S.b + S.c) : (S.b - S.c);
-        for (int k = 0; k < kTile; ++k) {
-            if (J == I && k == lane) continue;
-            const double dx = min_image(xi - sb[w][0][k], L, hL);
-            const double dy = min_image(yi - sb[w][1][k], L, hL);
-            const double dz = min_image(zi - sb[w][2][k], L, hL);
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            double gg = 0.0;
-            if (r2 < rn2) {
-                const double g1 = exp(-r2 / (2.0 * S.Lambda));
-                gg += g1 * (A2 * g1 + bc / S.Lambda);
-                if (kEnergy) {
-                    en += g1 * (S.a * g1 + bc);
-                    nn += 1;
+        const float lim = pp ? lim_c : lim_n;
+        if (valid) {
+            for (int k = 0; k < nq; ++k) {
+                if (J == I && k == lane) continue;
+                // FP32 screen (nearest image per pair)
+                const float4 qh = sh[w][k], ql = sl[w][k];
+                float ux = (hi.x - qh.x) + (lo.x - ql.x), uy = (hi.y - qh.y) + (lo.y - ql.y);
+                float uz = (hi.z - qh.z) + (lo.z - ql.z);
+                const float kx = rintf(ux * iLf), ky = rintf(uy * iLf), kz = rintf(uz * iLf);
+                ux = fmaf(-Llo, kx, fmaf(-Lhi, kx, ux));
+                uy = fmaf(-Llo, ky, fmaf(-Lhi, ky, uy));
+                uz = fmaf(-Llo, kz, fmaf(-Lhi, kz, uz));
+                if (fmaf(uz, uz, fmaf(uy, uy, ux * ux)) >= lim) continue;
+                const double dx = min_image(xi - sb[w][0][k], L, hL);
+                const double dy = min_image(yi - sb[w][1][k], L, hL);
+                const double dz = min_image(zi - sb[w][2][k], L, hL);
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                double gg = 0.0;
+                if (r2 < rn2) {
+                    const double g1 = exp(-r2 * i2L);
+                    gg += g1 * (A2 * g1 + bc * iLam);
+                    if (kEnergy) {
+                        en += g1 * (S.a * g1 + bc);
+                        nn += 1;
+                    }
                 }
-            }
-            if (pp && r2 < rc2) {
-                const double r = sqrt(r2);
-                const double ea = S.alpha * exp(-r / S.lambda_s);
-                gg += ea * (1.0 / (r2 * r) + 1.0 / (S.lambda_s * r2));
-                if (kEnergy) {
-                    ec += ea / r;
-                    nc += 1;
+                if (pp && r2 < rc2) {
+                    const double r = sqrt(r2);
+                    const double ir = 1.0 / r;
+                    const double ea = S.alpha * exp(-r * il);
+                    gg += ea * ir * ir * (ir + il);
+                    if (kEnergy) {
+                        ec += ea * ir;
+                        nc += 1;
+                    }
                 }
+                fx += gg * dx;
+                fy += gg * dy;
+                fz += gg * dz;
+                if (kEnergy) wv += gg * r2;
             }
-            fx += gg * dx;
-            fy += gg * dy;
-            fz += gg * dz;
-            if (kEnergy) wv += gg * r2;
         }
     }
-    double* F = S.f64[out_alt ? (st->cur ^ 1) : st->cur];
-    if (valid) {
-        F[p] = fx;
-        F[N + p] = fy;
-        F[2 * N + p] = fz;
-        if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&st->error, 1);
-    }
+    red[w][0][lane] = fx;
+    red[w][1][lane] = fy;
+    red[w][2][lane] = fz;
     if (kEnergy) {
-        en = warp_sum(valid ? en : 0.0);
-        ec = warp_sum(valid ? ec : 0.0);
-        wv = warp_sum(valid ? wv : 0.0);
-        const double cn = warp_sum(valid ? (double)nn : 0.0), cc = warp_sum(valid ? (double)nc : 0.0);
-        if (lane == 0)            // (ordered pairs: twice the pairs)
-            add_energy(st, 0.5 * en, 0.5 * ec, 0.5 * wv, (long long)cn, (long long)cc,
-                       (long long)(e1 - e0) * (kTile * kTile));
+        const double a0 = warp_sum(valid ? en : 0.0), a1 = warp_sum(valid ? ec : 0.0);
+        const double a2 = warp_sum(valid ? wv : 0.0);
+        const double a3 = warp_sum(valid ? (double)nn : 0.0), a4 = warp_sum(valid ? (double)nc : 0.0);
+        if (lane == 0) {
+            ered[w][0] = a0;
+            ered[w][1] = a1;
+            ered[w][2] = a2;
+            ered[w][3] = a3;
+            ered[w][4] = a4;
+        }
+    }
+    __syncthreads();
+    if (w == 0) {
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int k = 0; k < kFW; ++k) {
+            sx += red[k][0][lane];
+            sy += red[k][1][lane];
+            sz += red[k][2][lane];
+        }
+        double* F = S.f64[out_alt ? (st->cur ^ 1) : st->cur];
+        if (valid) {
+            F[p] = sx;
+            F[N + p] = sy;
+            F[2 * N + p] = sz;
+            if (!isfinite(sx) || !isfinite(sy) || !isfinite(sz)) atomicOr(&st->error, 1);
+        }
+        if (kEnergy && lane == 0) {
+            double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int k = 0; k < kFW; ++k)
+                for (int c = 0; c < 5; ++c) t[c] += ered[k][c];
+            // ordered pairs: twice the pairs
+            add_energy(st, 0.5 * t[0], 0.5 * t[1], 0.5 * t[2], (long long)t[3], (long long)t[4],
+                       (long long)e1 * (kTile * kTile));
+        }
     }
 }
 
@@ -997,8 +1055,8 @@ void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, in
     const int nbi = (E.nitems + kForceWarps - 1) / kForceWarps;
     H.rec("force", s);
     if (H.precision == 1) {
-        if (energy) k_force_fp64<true><<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
-        else k_force_fp64<false><<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
+        if (energy) k_force_fp64<true><<<E.ntiles, kFW * 32, 0, s>>>(E, only, out_alt);
+        else k_force_fp64<false><<<E.ntiles, kFW * 32, 0, s>>>(E, only, out_alt);
         H.count(1);
     } else {
         if (H.single) {
