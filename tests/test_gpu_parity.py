@@ -98,6 +98,10 @@ CONFIGS = {
     "drops_3000_dilute": lambda: cfg_drops(3000, 0.30, 0.005, 5),
     "relaxed_1500": lambda: cfg_relaxed(1500, 0.30, 0.080, 6),
     "liquid_4096_yp005": lambda: cfg_liquid(4096, 0.05, 0.030, 7),
+    # the late expansion: drops in a 464 fm box (coordinates as large as at
+    # the end of the 409,600 run's schedule, where the FP32 screens and the
+    # hi + lo separations work on the largest magnitudes)
+    "drops_20000_L464": lambda: cfg_drops(20000, 0.40, 0.0002, 8),
 }
 
 
@@ -297,7 +301,7 @@ def _check_clusters(s, x, t, L):
     assert st["A_mean"] == sto[2] and st["Z_mean"] == sto[3] and st["n_big"] == sto[4]
 
 
-@pytest.mark.parametrize("name", ["drops_3000_dilute", "liquid_2000", "liquid_4096_yp005"])
+@pytest.mark.parametrize("name", ["drops_3000_dilute", "liquid_2000", "liquid_4096_yp005", "drops_20000_L464"])
 def test_clusters_bit_exact(md, name):
     x, t, L = CONFIGS[name]()
     s, _ = load(md, x, t, L, 0)
