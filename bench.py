@@ -302,6 +302,9 @@ def run_gpu(args):
                                      "force_ms_per_launch": force_ms / max(force_n, 1),
                                      "candidate_pairs_per_step": cand / K,
                                      "candidate_efficiency": (pairs_nuc + pairs_coul) / max(cand, 1)}},
+        "force_code": {"variant": info["force_code"], "tuner_trials": info["force_trials"],
+                       "note": "split force-pass code in use: 4 long unrolled loops, 2 compact; chosen on the device "
+                               "by timing both every 500 steps (bitwise the same results)"},
         "tiles": {"count": info["tiles"], "list_entries": info["list_entries"], "rebuilds": info["rebuilds"],
                   "halfext_mean_fm": info["tile_halfext_mean"], "halfext_max_fm": info["tile_halfext_max"],
                   "need_wrap": info["need_wrap"]},
@@ -530,7 +533,8 @@ def run_full(args):
                          "E_per_nucleon_MeV": round((en["KE"] + en["PE_nuc"] + en["PE_coul"]) / N, 5),
                          "n_clusters": cst["n_clusters"], "n_big": cst["n_big"],
                          "A_mean": round(cst["A_mean"], 2), "Z_mean": round(cst["Z_mean"], 2),
-                         "m_free_n": round(cst["m_free_n"], 5), "rebuilds": info["rebuilds"]})
+                         "m_free_n": round(cst["m_free_n"], 5), "rebuilds": info["rebuilds"],
+                         "force_code": info["force_code"]})
     s.close()
     tot_ms = sum(r["ms_per_step"] * chunk for r in rows)
     first, last = rows[0], rows[-1]

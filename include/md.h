@@ -99,6 +99,13 @@ typedef struct {
                                 that return at once on such steps (profilers
                                 that cannot look inside graphs with conditional
                                 nodes).  Results are the same. */
+    int32_t force_unroll;    /* split force-pass code: 4 = long unrolled loops
+                                (fastest where the far Coulomb field dominates:
+                                dense states); 2 = compact (fits the instruction
+                                cache where several pair classes run at once:
+                                clustered, dilute states); 0 (default) = chosen
+                                on the device every 500 steps by timing 4 force
+                                passes of each.  Results are bitwise the same. */
 } md_params;
 
 typedef struct {
@@ -158,6 +165,11 @@ typedef struct {
     int64_t verlet_slots;    /* list_kind 1: pool slots used (entries + padding of
                                 the per-tile blocks) / available */
     int64_t verlet_capacity;
+    int32_t force_code;      /* code variant of the split force pass now in use:
+                                4 long unrolled loops, 2 compact (md_params
+                                force_unroll; 0 there: the device tuner's choice) */
+    int32_t pad0;
+    int64_t force_trials;    /* trials the device tuner has completed */
 } md_info_t;
 
 /* Fill the defaults listed above. */

@@ -131,7 +131,7 @@ Engine::~Engine() {
 
 void Engine::free_tables() {
     void* ptrs[] = {d_sys_, d_tile_sys_, d_item_sys_, d_hist_, d_binstart_, d_cursor_, d_blocksum_, d_any_, d_out_,
-                    d_clock_, d_seeds_, d_cond_runs_};
+                    d_clock_, d_seeds_, d_cond_runs_, d_tune_};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d_sys_ = nullptr;
@@ -140,6 +140,7 @@ void Engine::free_tables() {
     d_hist_ = d_binstart_ = d_cursor_ = d_blocksum_ = nullptr;
     d_any_ = nullptr;
     d_cond_runs_ = nullptr;
+    d_tune_ = nullptr;
     d_out_ = d_clock_ = nullptr;
     d_seeds_ = nullptr;
     table_bytes_ = 0;
@@ -223,6 +224,8 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
     if (p.coulomb < 0 || p.coulomb > 2) return fail(MD_EINVAL, "coulomb must be 0, 1 or 2");
     if (p.affine != 0 && p.affine != 1) return fail(MD_EINVAL, "affine must be 0 or 1");
+    if (p.force_unroll != 0 && p.force_unroll != 2 && p.force_unroll != 4)
+        return fail(MD_EINVAL, "force_unroll must be 0, 2 or 4");
     if (p.list_kind != 0 && p.list_kind != 1) return fail(MD_EINVAL, "list_kind must be 0 or 1");
     if (p.list_kind == 1 && p.precision != MD_PREC_SPLIT)
         return fail(MD_EINVAL, "Verlet lists (list_kind 1) need split precision");
@@ -330,6 +333,7 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     c.coulomb = p.coulomb;
     c.energy_every = (int)p.energy_every;
     c.list_kind = p.list_kind;
+    c.force_unroll = p.force_unroll;
     c.pf = pair_consts(c);
 
     SysState st{};
@@ -402,6 +406,7 @@ int Engine::build_tables() {
     if ((rc = A(&d_blocksum_, sizeof(unsigned) * (nscan + 1)))) return rc;
     if ((rc = A(&d_any_, sizeof(int)))) return rc;
     if ((rc = A(&d_cond_runs_, sizeof(unsigned long long)))) return rc;
+    if ((rc = A(&d_tune_, sizeof(ForceTune)))) return rc;
     if ((rc = A(&d_out_, sizeof(double) * 16))) return rc;
     if ((rc = A(&d_clock_, sizeof(double) * 8))) return rc;
     if ((rc = A(&d_seeds_, sizeof(unsigned long long) * std::max(n, 1)))) return rc;
@@ -424,6 +429,7 @@ int Engine::build_tables() {
     E.blocksum = d_blocksum_;
     E.any_rebuild = d_any_;
     E.cond_runs = d_cond_runs_;
+    E.tune = d_tune_;
     H_.precision = precision;
     H_.any_pp = false;
     H_.any_verlet = false;
@@ -900,6 +906,8 @@ int Engine::set_params(int idx, const md_params& p) {
     if (!(p.dt > 0.0) || !(p.r_nuc > 0.0) || !(p.skin > 0.0) || !(p.lambda_s >= 0.0))
         return fail(MD_EINVAL, "dt, r_nuc, skin must be > 0 and lambda_s >= 0");
     if (p.affine != 0 && p.affine != 1) return fail(MD_EINVAL, "affine must be 0 or 1");
+    if (p.force_unroll != 0 && p.force_unroll != 2 && p.force_unroll != 4)
+        return fail(MD_EINVAL, "force_unroll must be 0, 2 or 4");
     if (p.precision != MD_PREC_SPLIT && p.precision != MD_PREC_FP64) return fail(MD_EINVAL, "bad precision");
     if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
     if (p.list_kind != 0 && p.list_kind != 1) return fail(MD_EINVAL, "list_kind must be 0 or 1");
@@ -966,6 +974,7 @@ int Engine::set_params(int idx, const md_params& p) {
     c.coulomb = p.coulomb;
     c.energy_every = (int)p.energy_every;
     c.list_kind = p.list_kind;
+    c.force_unroll = p.force_unroll;
     c.pf = pair_consts(c);
     if (pp_changed || lists_changed) {
         cudaStreamSynchronize(stream_);
@@ -1081,6 +1090,11 @@ int Engine::info(int idx, md_info_t* out) {
     out->verlet_entries = h.c.list_kind == 1 ? (int64_t)st.vpairs : 0;
     out->verlet_slots = h.c.list_kind == 1 ? (int64_t)st.vtop : 0;
     out->verlet_capacity = h.c.list_kind == 1 ? (int64_t)h.c.vcap : 0;
+    ForceTune tu{};
+    CK(cudaMemcpyAsync(&tu, d_tune_, sizeof(tu), cudaMemcpyDeviceToHost, stream_));
+    CK(cudaStreamSynchronize(stream_));
+    out->force_code = h.c.force_unroll != 0 ? h.c.force_unroll : (tu.cur == 1 ? 2 : 4);
+    out->force_trials = tu.trials;
     return MD_OK;
 }
 

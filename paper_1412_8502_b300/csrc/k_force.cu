@@ -55,6 +55,22 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 
 enum PairClass { kPPNuc = 0, kPPCoul = 1, kNucCross = 2, kNucSame = 3 };
 
+// Two code variants of the split force pass, chosen per system and step:
+// long unrolled loops (kULong: rotated blocks 4 steps, the tile with itself
+// 8 sources) and a compact one (kUCompact: 2 and 2).  Where the far Coulomb
+// field dominates (dense states), one block kind runs on most warps and the
+// long loops issue best; where nuclear pairs are a large part of the work
+// (clustered, dilute states), warps of one SM run several block kinds at a
+// time, and the long variant's code no longer fits the instruction cache
+// (ncu: 6 "no instruction" stalls per issue at rho = 0.00125 against 0.3 in
+// the dense state).  Both variants do the same arithmetic in the same order.
+#ifndef PASTA_N3_UNROLL
+#define PASTA_N3_UNROLL 4            // steps unrolled in a rotated block, long variant
+#endif
+constexpr int kULong = PASTA_N3_UNROLL;
+constexpr int kUCompact = 2;
+__host__ __device__ constexpr int self_unroll(int kU) { return kU == kULong ? 8 : 2; }
+
 struct PairConsts {
     float rn2, rc2;          // squared cutoffs
     float kq;                // -1/(2 Lambda ln 2): g = 2^(r2 kq)
@@ -143,13 +159,13 @@ __device__ __forceinline__ void one_pair(const float4& q, const float4& u, const
 
 // The tile against itself: all lanes take source k in turn (broadcast), for
 // all 32 sources (compile-time trip count) or the first n (ragged tiles).
-template <int kClass, bool kLo, bool kWrap, bool kEnergy>
+template <int kClass, bool kLo, bool kWrap, bool kEnergy, int kU>
 __device__ __forceinline__ void pair_block(const float4* __restrict__ qh, const float4* __restrict__ ql, int n,
                                            const float4& hi, const float4& lo, const PairConsts& C, Acc& acc) {
     const float S = (kClass == kNucCross) ? C.Scross : C.Ssame;
     const float bS = (kClass == kNucCross) ? C.bcross : C.bsame;
     if (n == kTile) {
-#pragma unroll 8
+#pragma unroll self_unroll(kU)
         for (int k = 0; k < kTile; ++k)
             one_pair<kClass, kLo, kWrap, kEnergy>(qh[k], kLo ? ql[k] : qh[k], hi, lo, C, S, bS, acc);
     } else {
@@ -174,12 +190,7 @@ constexpr int kQ = 2 * kTile;    // queue capacity
 #ifndef PASTA_FORCE_STAGES
 #define PASTA_FORCE_STAGES 2
 #endif
-#ifndef PASTA_N3_UNROLL
-#define PASTA_N3_UNROLL 4            // steps unrolled in a rotated block (per-pair wrap: half)
-#endif
 constexpr int kStages = PASTA_FORCE_STAGES;   // source tiles in flight per warp (cp.async)
-constexpr int kN3Unroll = PASTA_N3_UNROLL;    // unrolled steps of a rotated block
-constexpr int kN3UnrollWrap = (PASTA_N3_UNROLL + 1) / 2;   // longer bodies: keep the code in the i-cache
 constexpr float kUnfixF = 1.0f / 4294967296.0f;   // force accumulators count 2^-32 MeV/fm
 constexpr float kForceMax = 1.0e9f;          // |partial force| beyond this (MeV/fm) is an error
 
@@ -326,7 +337,7 @@ struct Targets {
 // serve two pairs.
 // cross: unlike species (b - c), chosen at run time so that like and unlike
 // nuclear blocks share one instance of the code.
-template <int kClass, bool kLo, bool kWrap, bool kEnergy, bool kFull>
+template <int kClass, bool kLo, bool kWrap, bool kEnergy, bool kFull, int kU>
 __device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, const Targets& X,
                                          const PairConsts& C, Totals& T, long long* facc, int N, bool cross) {
     const float S = cross ? C.Scross : C.Ssame;
@@ -354,11 +365,11 @@ __device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, c
         ry = __shfl_sync(0xffffffffu, fmaf(-fr1, dy, ry), from);
         rz = __shfl_sync(0xffffffffu, fmaf(-fr1, dz, rz), from);
     };
-    if (kWrap) {
-#pragma unroll kN3UnrollWrap
+    if (kWrap) {                 // longer bodies: half the unrolling
+#pragma unroll (kU + 1) / 2
         for (int k = 0; k < 16; ++k) step(k);
     } else {
-#pragma unroll kN3Unroll
+#pragma unroll kU
         for (int k = 0; k < 16; ++k) step(k);
     }
     if ((half | j) < n) {
@@ -384,19 +395,19 @@ __device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, c
     T.cand += n * kTile;
 }
 
-template <int kClass, bool kLo, bool kWrap, bool kEnergy>
+template <int kClass, bool kLo, bool kWrap, bool kEnergy, int kU>
 __device__ __forceinline__ void n3_any(const WarpQueues& Q, int n, int lane, const Targets& X, const PairConsts& C,
                                        Totals& T, long long* facc, int N, bool cross = false) {
     // Without per-pair wrapping the unused slots of a partial block hold a
     // far pad position (drain), whose pair terms vanish exactly (2^-huge = +0,
     // out of range): the full-block code serves every block, which keeps the
     // instruction footprint of the pass small.
-    if (n == kTile || !kWrap) n3_block<kClass, kLo, kWrap, kEnergy, true>(Q, n, lane, X, C, T, facc, N, cross);
-    else n3_block<kClass, kLo, kWrap, kEnergy, false>(Q, n, lane, X, C, T, facc, N, cross);
+    if (n == kTile || !kWrap) n3_block<kClass, kLo, kWrap, kEnergy, true, kU>(Q, n, lane, X, C, T, facc, N, cross);
+    else n3_block<kClass, kLo, kWrap, kEnergy, false, kU>(Q, n, lane, X, C, T, facc, N, cross);
 }
 
 // Evaluate the first min(cnt, 32) entries of queue q, shift the rest down.
-template <bool kWrap, bool kEnergy>
+template <bool kWrap, bool kEnergy, int kU>
 __device__ __forceinline__ void drain(WarpQueues& Q, int q, int cls, int& cnt, int lane, const Targets& X,
                                       const PairConsts& C, Totals& T, long long* facc, int N) {
     __syncwarp();
@@ -423,9 +434,9 @@ __device__ __forceinline__ void drain(WarpQueues& Q, int q, int cls, int& cnt, i
     cnt = rest;
     __syncwarp();
     switch (cls) {
-        case kPPNuc: n3_any<kPPNuc, true, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N); break;
-        case kPPCoul: n3_any<kPPCoul, false, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N); break;
-        default: n3_any<kNucSame, true, kWrap, kEnergy>(Q, n, lane, X, C, T, facc, N, cls == kNucCross); break;
+        case kPPNuc: n3_any<kPPNuc, true, kWrap, kEnergy, kU>(Q, n, lane, X, C, T, facc, N); break;
+        case kPPCoul: n3_any<kPPCoul, false, kWrap, kEnergy, kU>(Q, n, lane, X, C, T, facc, N); break;
+        default: n3_any<kNucSame, true, kWrap, kEnergy, kU>(Q, n, lane, X, C, T, facc, N, cls == kNucCross); break;
     }
 }
 
@@ -443,7 +454,7 @@ __device__ __forceinline__ void push(WarpQueues& Q, int q, bool pred, int& cnt, 
 // Work item v of a system (see item_index): the near entries of a proton
 // tile with the tile itself, a third of its Coulomb-only entries, or the
 // whole list of a neutron tile with the tile itself.
-template <bool kWrap, bool kEnergy>
+template <bool kWrap, bool kEnergy, int kU>
 __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, int v, WarpQueues& Q) {
     const int lane = threadIdx.x & 31;
     const int Pi = proton_items(S.Tp);
@@ -572,8 +583,8 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
         Q.dl[lane] = ls;
         __syncwarp();
         Acc a{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (cls0 == kPPNuc) pair_block<kPPNuc, true, kWrap, kEnergy>(Q.dh, Q.dl, nv, hs, ls, C, a);
-        else pair_block<kNucSame, true, kWrap, kEnergy>(Q.dh, Q.dl, nv, hs, ls, C, a);
+        if (cls0 == kPPNuc) pair_block<kPPNuc, true, kWrap, kEnergy, kU>(Q.dh, Q.dl, nv, hs, ls, C, a);
+        else pair_block<kNucSame, true, kWrap, kEnergy, kU>(Q.dh, Q.dl, nv, hs, ls, C, a);
         sfx = a.fx;
         sfy = a.fy;
         sfz = a.fz;
@@ -625,26 +636,26 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
         const float d2 = fminf(d2h[0], d2h[1]);
         if (farc) {                // Coulomb-only entry: every source goes to PPC or nowhere
             push(Q, 1, src_ok && d2 < Rc2, c1, lane, h, l);
-            if (c1 >= kTile) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, X, C, T, facc, N);
+            if (c1 >= kTile) drain<kWrap, kEnergy, kU>(Q, 1, kPPCoul, c1, lane, X, C, T, facc, N);
         } else if (Ip && Jp && S.coulomb == 1) {
             const bool nuc = src_ok && d2 < Rn2;
             push(Q, 0, nuc, c0, lane, h, l);
             push(Q, 1, src_ok && !nuc && d2 < Rc2, c1, lane, h, l);
-            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, kPPNuc, c0, lane, X, C, T, facc, N);
-            if (c1 >= kTile) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, X, C, T, facc, N);
+            if (c0 >= kTile) drain<kWrap, kEnergy, kU>(Q, 0, kPPNuc, c0, lane, X, C, T, facc, N);
+            if (c1 >= kTile) drain<kWrap, kEnergy, kU>(Q, 1, kPPCoul, c1, lane, X, C, T, facc, N);
         } else if (Ip != Jp) {
             push(Q, 2, src_ok && d2 < Rn2, c2, lane, h, l);
-            if (c2 >= kTile) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, X, C, T, facc, N);
+            if (c2 >= kTile) drain<kWrap, kEnergy, kU>(Q, 2, kNucCross, c2, lane, X, C, T, facc, N);
         } else {
             push(Q, 0, src_ok && d2 < Rn2, c0, lane, h, l);
-            if (c0 >= kTile) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, X, C, T, facc, N);
+            if (c0 >= kTile) drain<kWrap, kEnergy, kU>(Q, 0, cls0, c0, lane, X, C, T, facc, N);
         }
     }
     cp_async_wait<0>();
     // flush the partial queues (< 32 entries each)
-    if (c0 > 0) drain<kWrap, kEnergy>(Q, 0, cls0, c0, lane, X, C, T, facc, N);
-    if (c1 > 0) drain<kWrap, kEnergy>(Q, 1, kPPCoul, c1, lane, X, C, T, facc, N);
-    if (c2 > 0) drain<kWrap, kEnergy>(Q, 2, kNucCross, c2, lane, X, C, T, facc, N);
+    if (c0 > 0) drain<kWrap, kEnergy, kU>(Q, 0, cls0, c0, lane, X, C, T, facc, N);
+    if (c1 > 0) drain<kWrap, kEnergy, kU>(Q, 1, kPPCoul, c1, lane, X, C, T, facc, N);
+    if (c2 > 0) drain<kWrap, kEnergy, kU>(Q, 2, kNucCross, c2, lane, X, C, T, facc, N);
 
     // Target l = j + 16 (l >> 4): this lane's share plus its partner's
     // (lane l ^ 16 holds the same two targets), plus the tile's own pairs.
@@ -679,23 +690,33 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
 }
 
 // kSingle: the engine holds one system, whose pair constants come in as a
-// kernel parameter (constant bank: operands without registers).
+// kernel parameter (constant bank: operands without registers).  The code
+// variant comes from the system's force_unroll, or (0) from the device
+// tuner; block 0 records the start of the pass for the tuner.
 template <bool kEnergy, bool kSingle>
 __global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS)
     k_force_split(EngineDev E, int only, const __grid_constant__ PairF pf) {
     __shared__ WarpQueues qs[kForceWarps];
+    ForceTune* tu = E.tune;
+    if (blockIdx.x == 0 && threadIdx.x == 0) tu->t_start = global_ns();   // k_force_fix takes the end
     const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
-    if (g >= E.nitems) return;
-    const int s = E.item_sys[g];
-    if (s < 0 || (only >= 0 && s != only)) return;
-    const SysConst& S = E.sys[s];
-    if (S.list_kind != 0) return;          // per-particle lists: k_force_verlet
-    const int v = g - S.item_base;
-    if (v >= S.n_items) return;
-    WarpQueues& Q = qs[threadIdx.x >> 5];
-    const PairF& P = kSingle ? pf : S.pf;
-    if (S.st->need_wrap) force_item<true, kEnergy>(S, P, v, Q);
-    else force_item<false, kEnergy>(S, P, v, Q);
+    const int s = g < E.nitems ? E.item_sys[g] : -1;
+    if (s >= 0 && (only < 0 || s == only)) {
+        const SysConst& S = E.sys[s];
+        const int v = g - S.item_base;
+        if (S.list_kind == 0 && v < S.n_items) {       // per-particle lists: k_force_verlet
+            WarpQueues& Q = qs[threadIdx.x >> 5];
+            const PairF& P = kSingle ? pf : S.pf;
+            const bool compact = S.force_unroll == kUCompact || (S.force_unroll == 0 && tu->cur == 1);
+            if (S.st->need_wrap) {
+                if (compact) force_item<true, kEnergy, kUCompact>(S, P, v, Q);
+                else force_item<true, kEnergy, kULong>(S, P, v, Q);
+            } else {
+                if (compact) force_item<false, kEnergy, kUCompact>(S, P, v, Q);
+                else force_item<false, kEnergy, kULong>(S, P, v, Q);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------- Verlet
@@ -867,6 +888,8 @@ __global__ void __launch_bounds__(kVW * 32) k_force_verlet(EngineDev E, int only
 // Fixed-point accumulators -> FP32 forces (rounded once), and back to zero
 // for the next pass.  One warp per tile, one lane per particle.
 __global__ void __launch_bounds__(kForceWarps * 32) k_force_fix(EngineDev E, int only, int out_alt) {
+    // duration of the force pass that this launch follows (device tuner)
+    if (blockIdx.x == 0 && threadIdx.x == 0) E.tune->t_last = global_ns() - E.tune->t_start;
     const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
     if (g >= E.ntiles) return;
     const int s = E.tile_sys[g];

@@ -323,6 +323,31 @@ __global__ void k_kick(EngineDev E) {
 }
 
 // One block per system.  energy: also record the energy pass's totals.
+// Force-pass code variant (ForceTune): account the pass of the step just
+// taken (variant tu->cur), then advance the trial: kTuneSteps passes of the
+// long variant, kTuneSteps of the compact one, keep the faster.
+__device__ inline void tune_step(ForceTune* tu, long long step, bool active) {
+    if (!active) return;
+    if (tu->phase != 0) {
+        tu->acc[tu->cur] += (double)tu->t_last;
+        tu->n[tu->cur] += 1;
+        if (tu->phase == 1 && tu->n[0] >= kTuneSteps) {
+            tu->phase = 2;
+            tu->cur = 1;
+        } else if (tu->phase == 2 && tu->n[1] >= kTuneSteps) {
+            tu->cur = tu->acc[1] < tu->acc[0] ? 1 : 0;
+            tu->phase = 0;
+            tu->trials += 1;
+            tu->next_step = step + kTuneEvery;
+        }
+    } else if (step >= tu->next_step) {
+        tu->phase = 1;
+        tu->cur = 0;
+        tu->n[0] = tu->n[1] = 0;
+        tu->acc[0] = tu->acc[1] = 0.0;
+    }
+}
+
 __global__ void k_finalize(EngineDev E, int energy) {
     const int s = blockIdx.x;
     const SysConst& S = E.sys[s];
@@ -358,6 +383,7 @@ __global__ void k_finalize(EngineDev E, int energy) {
         st->e_cand = st->eacc[5] / 2;
         st->have_energy = 1;
     }
+    if (s == 0 && E.tune) tune_step(E.tune, st->step, S.force_unroll == 0 && S.list_kind == 0);
 }
 
 // Energies at the current state (md_energy): KE from the block partials of

@@ -69,6 +69,7 @@ void md_params_default(md_params* p) {
     p->list_kind = 0;
     p->verlet_pool = 2.0;
     p->cond_graph = 1;
+    p->force_unroll = 0;
 }
 
 double md_lambda_thomas_fermi(double n_e) { return pasta::lambda_thomas_fermi(n_e); }

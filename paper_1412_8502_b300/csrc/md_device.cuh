@@ -105,6 +105,7 @@ struct SysConst {
     int thermostat_every, rebuild_every, coulomb, energy_every;
     int affine;              // scale positions with the box (option, not the paper)
     int list_kind;           // 0 half tile-pair lists, 1 per-particle Verlet lists
+    int force_unroll;        // split force-pass code variant: 0 automatic, 2 compact, 4 long
     PairF pf;
     // state arrays (index [cur] is current)
     double* x[2];
@@ -139,6 +140,31 @@ struct SysConst {
 };
 
 // Global tables of an engine.
+// Choice between the two code variants of the split force pass, made on
+// the device by timing (the variants give bitwise the same results): every
+// kTuneEvery steps kTuneSteps force passes run with each variant, their
+// durations (%globaltimer at the start of the force kernel's block 0 to the
+// start of the k_force_fix launch that follows it) are summed, and the
+// faster variant is kept until the next trial.
+constexpr int kTuneEvery = 500;
+constexpr int kTuneSteps = 4;
+struct ForceTune {
+    unsigned long long t_start;  // start of the running force pass, ns
+    unsigned long long t_last;   // duration of the last force pass, ns
+    int cur;                     // variant of the next pass: 0 long, 1 compact
+    int phase;                   // 0 idle, 1 timing the long, 2 timing the compact variant
+    int trials;                  // trials completed
+    int n[2];
+    long long next_step;         // step of system 0 at which the next trial starts
+    double acc[2];               // summed durations per variant, ns
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 struct EngineDev {
     const SysConst* sys;     // [nsys]
     const int* tile_sys;     // [ntiles] global tile -> system (-1: padding)
@@ -153,6 +179,7 @@ struct EngineDev {
     unsigned* blocksum;      // [scan blocks]
     int* any_rebuild;        // set when any system rebuilds this step
     unsigned long long* cond_runs;   // step-graph rebuilds run through the conditional node
+    ForceTune* tune;                 // force-pass code variant (automatic choice)
 };
 
 // Force work items of a system.  A proton tile's list holds its near

@@ -38,7 +38,7 @@ class md_params(ctypes.Structure):
                 ("precision", _I32), ("coulomb", _I32), ("r_pp", _D), ("r_np", _D),
                 ("relax_iters", _I64), ("relax_gamma", _D), ("relax_dmax", _D),
                 ("energy_every", _I64), ("sort_bits", _I32), ("affine", _I32), ("list_kind", _I32),
-                ("verlet_pool", _D), ("cond_graph", _I32)]
+                ("verlet_pool", _D), ("cond_graph", _I32), ("force_unroll", _I32)]
 
 
 class md_energy_t(ctypes.Structure):
@@ -62,7 +62,8 @@ class md_info_t(ctypes.Structure):
     _fields_ = [("N", _I64), ("Np", _I64), ("tiles", _I64), ("rebuilds", _I64),
                 ("list_entries", _I64), ("launches", _I64), ("device_bytes", _I64),
                 ("need_wrap", _I32), ("sort_bits", _I32), ("tile_halfext_mean", _D), ("tile_halfext_max", _D),
-                ("verlet_entries", _I64), ("verlet_slots", _I64), ("verlet_capacity", _I64)]
+                ("verlet_entries", _I64), ("verlet_slots", _I64), ("verlet_capacity", _I64),
+                ("force_code", _I32), ("pad0", _I32), ("force_trials", _I64)]
 
 
 class md_job(ctypes.Structure):

@@ -386,3 +386,43 @@ def test_state_round_trip_with_forces(md, precision):
     assert rel_l2(s3.forces(), g["f"]) < (1e-12 if precision == 1 else 1e-5)
     for q in (s, s2, s3):
         q.close()
+
+
+# --------------------------------------------------------------- code variants
+@pytest.mark.parametrize("name", ["liquid_2000", "drops_3000_dilute", "liquid_4096_yp005"])
+def test_force_code_variants_agree_bitwise(md, name):
+    """The long and the compact code variants of the split force pass do the
+    same arithmetic in the same order: identical forces, energies and pair
+    counts, before and after steps (the automatic choice, force_unroll = 0,
+    switches between them by the pair mix of the last energy record)."""
+    x, t, L = CONFIGS[name]()
+    outs = []
+    for fu in (4, 2, 0):
+        s, _ = load(md, x, t, L, 0, force_unroll=fu, energy_every=1)
+        F0, e0 = s.forces(), s.energy()
+        s.step(12, 7.5e-5)
+        outs.append((F0, e0, s.state(f=True), s.step_energy()))
+        s.close()
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and o[1] == outs[0][1]
+        for k in ("x", "v", "f"):
+            assert np.array_equal(o[2][k], outs[0][2][k])
+        assert o[3] == outs[0][3]
+
+
+def test_force_code_tuner_reports_its_choice(md):
+    """force_unroll = 0: the device tuner times both variants every 500 steps
+    and reports the one in use; a fixed force_unroll is reported as set."""
+    x, t, L = CONFIGS["liquid_2000"]()
+    s, _ = load(md, x, t, L, 0)
+    s.step(10, 0.0)
+    info = s.info()
+    assert info["force_trials"] == 1 and info["force_code"] in (2, 4)
+    s.close()
+    for fu in (2, 4):
+        s, _ = load(md, x, t, L, 0, force_unroll=fu)
+        s.step(10, 0.0)
+        assert s.info()["force_code"] == fu and s.info()["force_trials"] == 0
+        s.close()
+    with pytest.raises(md.MDError):
+        load(md, x, t, L, 0, force_unroll=3)
