@@ -104,8 +104,9 @@ typedef struct {
                                 dense states); 2 = compact (fits the instruction
                                 cache where several pair classes run at once:
                                 clustered, dilute states); 0 (default) = chosen
-                                on the device every 500 steps by timing 4 force
-                                passes of each.  Results are bitwise the same. */
+                                on the device every 500 steps (from step 500 on;
+                                the long one before) by timing 4 force passes of
+                                each.  Results are bitwise the same. */
 } md_params;
 
 typedef struct {

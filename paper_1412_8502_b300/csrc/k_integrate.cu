@@ -338,9 +338,9 @@ __device__ inline void tune_step(ForceTune* tu, long long step, bool active) {
             tu->cur = tu->acc[1] < tu->acc[0] ? 1 : 0;
             tu->phase = 0;
             tu->trials += 1;
-            tu->next_step = step + kTuneEvery;
+            tu->last_step = step;
         }
-    } else if (step >= tu->next_step) {
+    } else if (step >= tu->last_step + kTuneEvery) {
         tu->phase = 1;
         tu->cur = 0;
         tu->n[0] = tu->n[1] = 0;

@@ -145,7 +145,8 @@ struct SysConst {
 // kTuneEvery steps kTuneSteps force passes run with each variant, their
 // durations (%globaltimer at the start of the force kernel's block 0 to the
 // start of the k_force_fix launch that follows it) are summed, and the
-// faster variant is kept until the next trial.
+// faster variant is kept until the next trial.  The first trial comes at
+// step kTuneEvery: until then the long variant runs (systems start dense).
 constexpr int kTuneEvery = 500;
 constexpr int kTuneSteps = 4;
 struct ForceTune {
@@ -155,7 +156,7 @@ struct ForceTune {
     int phase;                   // 0 idle, 1 timing the long, 2 timing the compact variant
     int trials;                  // trials completed
     int n[2];
-    long long next_step;         // step of system 0 at which the next trial starts
+    long long last_step;         // step of system 0 at the last decision (0 before the first)
     double acc[2];               // summed durations per variant, ns
 };
 

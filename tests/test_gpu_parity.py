@@ -412,10 +412,13 @@ def test_force_code_variants_agree_bitwise(md, name):
 
 def test_force_code_tuner_reports_its_choice(md):
     """force_unroll = 0: the device tuner times both variants every 500 steps
-    and reports the one in use; a fixed force_unroll is reported as set."""
+    (from step 500) and reports the one in use; a fixed force_unroll is
+    reported as set."""
     x, t, L = CONFIGS["liquid_2000"]()
     s, _ = load(md, x, t, L, 0)
     s.step(10, 0.0)
+    assert s.info()["force_trials"] == 0 and s.info()["force_code"] == 4     # long until step 500
+    s.step(500, 0.0)
     info = s.info()
     assert info["force_trials"] == 1 and info["force_code"] in (2, 4)
     s.close()
