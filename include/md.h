@@ -101,12 +101,12 @@ typedef struct {
                                 nodes).  Results are the same. */
     int32_t force_unroll;    /* split force-pass code: 4 = long unrolled loops
                                 (fastest where the far Coulomb field dominates:
-                                dense states); 2 = compact (fits the instruction
-                                cache where several pair classes run at once:
-                                clustered, dilute states); 0 (default) = chosen
-                                on the device every 500 steps (from step 500 on;
-                                the long one before) by timing 4 force passes of
-                                each.  Results are bitwise the same. */
+                                dense states); 2 = compact, 1 = minimal (fit the
+                                instruction cache where several pair classes run
+                                at once: clustered, dilute states); 0 (default) =
+                                chosen on the device every 500 steps (from step
+                                500 on; the long one before) by timing 4 force
+                                passes of each.  Results are bitwise the same. */
 } md_params;
 
 typedef struct {
@@ -167,8 +167,9 @@ typedef struct {
                                 the per-tile blocks) / available */
     int64_t verlet_capacity;
     int32_t force_code;      /* code variant of the split force pass now in use:
-                                4 long unrolled loops, 2 compact (md_params
-                                force_unroll; 0 there: the device tuner's choice) */
+                                4 long unrolled loops, 2 compact, 1 minimal
+                                (md_params force_unroll; 0 there: the device
+                                tuner's choice) */
     int32_t pad0;
     int64_t force_trials;    /* trials the device tuner has completed */
 } md_info_t;

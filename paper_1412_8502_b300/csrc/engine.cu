@@ -224,8 +224,8 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
     if (p.coulomb < 0 || p.coulomb > 2) return fail(MD_EINVAL, "coulomb must be 0, 1 or 2");
     if (p.affine != 0 && p.affine != 1) return fail(MD_EINVAL, "affine must be 0 or 1");
-    if (p.force_unroll != 0 && p.force_unroll != 2 && p.force_unroll != 4)
-        return fail(MD_EINVAL, "force_unroll must be 0, 2 or 4");
+    if (p.force_unroll != 0 && p.force_unroll != 1 && p.force_unroll != 2 && p.force_unroll != 4)
+        return fail(MD_EINVAL, "force_unroll must be 0, 1, 2 or 4");
     if (p.list_kind != 0 && p.list_kind != 1) return fail(MD_EINVAL, "list_kind must be 0 or 1");
     if (p.list_kind == 1 && p.precision != MD_PREC_SPLIT)
         return fail(MD_EINVAL, "Verlet lists (list_kind 1) need split precision");
@@ -505,10 +505,16 @@ int Engine::capture(GraphRec& g, int kind, bool energy) {
 
 int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
     CK(cudaGraphCreate(&graph, 0));
-    // one handle per conditional node (a graph may not hold a handle without its node)
-    cudaGraphConditionalHandle h[2] = {0, 0};
-    if (sys.empty() || sys[0]->prm.cond_graph != 0)
+    // one handle per conditional node (a graph may not hold a handle without
+    // its node): the two rebuild IF nodes and, in split precision, the SWITCH
+    // node of the force-pass code variant
+    const bool cond = sys.empty() || sys[0]->prm.cond_graph != 0;
+    const bool split = precision != MD_PREC_FP64;
+    cudaGraphConditionalHandle h[3] = {0, 0, 0};
+    if (cond) {
         for (int k = 0; k < 2; ++k) CK(cudaGraphConditionalHandleCreate(&h[k], graph, 0, cudaGraphCondAssignDefault));
+        if (split) CK(cudaGraphConditionalHandleCreate(&h[2], graph, 0, cudaGraphCondAssignDefault));
+    }
     std::vector<cudaGraphNode_t> front;
     int rc;
     // segment: launches captured into `graph` after the frontier, which then moves
@@ -549,33 +555,29 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
         front.assign(1, node);
         return MD_OK;
     };
-    const bool cond = sys.empty() || sys[0]->prm.cond_graph != 0;
-    if (!cond) {
-        // plain nodes: the rebuild kernels return at once unless a system rebuilds
-        rc = segment([&] {
-            if (kind == 0) launch_kick_drift(H_, stream_);
-            else launch_sd_update(H_, stream_);
-            launch_decide(H_, stream_, 0, -1, 0, 0, false);
-            H_.rec("cell_build", stream_);
-            launch_cell_build(H_, stream_, false);
-            H_.rec("lists", stream_);
-            launch_list_build(H_, stream_, false);
-        });
-        if (rc) return rc;
-    } else {
-        if ((rc = segment([&] {
-                 if (kind == 0) launch_kick_drift(H_, stream_);
-                 else launch_sd_update(H_, stream_);
-                 launch_decide(H_, stream_, 0, -1, h[0], h[1], true);
-                 H_.rec("cell_build", stream_);
-             })))
-            return rc;
-        if ((rc = conditional(0))) return rc;
-        if ((rc = segment([&] { H_.rec("lists", stream_); }))) return rc;
-        if ((rc = conditional(1))) return rc;
-    }
-    return segment([&] {
-        launch_force(H_, stream_, kind == 0 && energy, -1, 0);
+    // SWITCH node after the frontier: body v launches force-pass variant v
+    auto variant_switch = [&]() -> int {
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h[2];
+        p.conditional.type = cudaGraphCondTypeSwitch;
+        p.conditional.size = kVariants;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, graph, front.empty() ? nullptr : front.data(), nullptr, front.size(), &p));
+        const int n0 = capture_nodes_;
+        for (int v = 0; v < kVariants; ++v) {
+            CK(cudaStreamBeginCaptureToGraph(aux_stream_, p.conditional.phGraph_out[v], nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+            launch_force_variant(H_, aux_stream_, kind == 0 && energy, -1, v, false);
+            cudaGraph_t body = nullptr;
+            CK(cudaStreamEndCapture(aux_stream_, &body));
+        }
+        capture_nodes_ = n0 + 1;           // one variant runs every step
+        front.assign(1, node);
+        return MD_OK;
+    };
+    // the closing part of a step: forces, kick, finalisation
+    auto closing = [&]() {
         if (kind == 0) launch_kick_finalize(H_, stream_, energy);
         if (timing_) {
             cudaEvent_t ev;
@@ -583,6 +585,52 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
             cudaEventRecordWithFlags(ev, stream_, cudaEventRecordExternal);
             cur_rec_->events.push_back(ev);
         }
+    };
+    const bool fe = kind == 0 && energy;
+    if (!cond) {
+        // plain nodes: the rebuild kernels return at once unless a system rebuilds
+        rc = segment([&] {
+            if (kind == 0) launch_kick_drift(H_, stream_);
+            else launch_sd_update(H_, stream_);
+            launch_decide(H_, stream_, 0, -1, 0, 0, false, 0, false);
+            H_.rec("cell_build", stream_);
+            launch_cell_build(H_, stream_, false);
+            H_.rec("lists", stream_);
+            launch_list_build(H_, stream_, false);
+        });
+        if (rc) return rc;
+        // all three force-pass variants; two return at once
+        return segment([&] {
+            if (split) {
+                launch_force_pre(H_, stream_, fe, -1);
+                for (int v = 0; v < kVariants; ++v) launch_force_variant(H_, stream_, fe, -1, v, true);
+                launch_force_post(H_, stream_, fe, -1, 0);
+            } else {
+                launch_force(H_, stream_, fe, -1, 0);
+            }
+            closing();
+        });
+    } else {
+        if ((rc = segment([&] {
+                 if (kind == 0) launch_kick_drift(H_, stream_);
+                 else launch_sd_update(H_, stream_);
+                 launch_decide(H_, stream_, 0, -1, h[0], h[1], true, h[2], split);
+                 H_.rec("cell_build", stream_);
+             })))
+            return rc;
+        if ((rc = conditional(0))) return rc;
+        if ((rc = segment([&] { H_.rec("lists", stream_); }))) return rc;
+        if ((rc = conditional(1))) return rc;
+    }
+    if (!split) return segment([&] {
+        launch_force(H_, stream_, fe, -1, 0);
+        closing();
+    });
+    if ((rc = segment([&] { launch_force_pre(H_, stream_, fe, -1); }))) return rc;
+    if ((rc = variant_switch())) return rc;
+    return segment([&] {
+        launch_force_post(H_, stream_, fe, -1, 0);
+        closing();
     });
 }
 
@@ -906,8 +954,8 @@ int Engine::set_params(int idx, const md_params& p) {
     if (!(p.dt > 0.0) || !(p.r_nuc > 0.0) || !(p.skin > 0.0) || !(p.lambda_s >= 0.0))
         return fail(MD_EINVAL, "dt, r_nuc, skin must be > 0 and lambda_s >= 0");
     if (p.affine != 0 && p.affine != 1) return fail(MD_EINVAL, "affine must be 0 or 1");
-    if (p.force_unroll != 0 && p.force_unroll != 2 && p.force_unroll != 4)
-        return fail(MD_EINVAL, "force_unroll must be 0, 2 or 4");
+    if (p.force_unroll != 0 && p.force_unroll != 1 && p.force_unroll != 2 && p.force_unroll != 4)
+        return fail(MD_EINVAL, "force_unroll must be 0, 1, 2 or 4");
     if (p.precision != MD_PREC_SPLIT && p.precision != MD_PREC_FP64) return fail(MD_EINVAL, "bad precision");
     if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
     if (p.list_kind != 0 && p.list_kind != 1) return fail(MD_EINVAL, "list_kind must be 0 or 1");
@@ -1093,7 +1141,8 @@ int Engine::info(int idx, md_info_t* out) {
     ForceTune tu{};
     CK(cudaMemcpyAsync(&tu, d_tune_, sizeof(tu), cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));
-    out->force_code = h.c.force_unroll != 0 ? h.c.force_unroll : (tu.cur == 1 ? 2 : 4);
+    static const int code[kVariants] = {4, 2, 1};
+    out->force_code = code[tu.sel < 0 || tu.sel >= kVariants ? 0 : tu.sel];
     out->force_trials = tu.trials;
     return MD_OK;
 }

@@ -129,7 +129,8 @@ __device__ __forceinline__ void warp_bounds(double v, bool valid, double& lo, do
 // drives one node); it sets both, so the rebuild kernels are not launched at
 // all on steps without a rebuild.
 __global__ void k_decide(EngineDev E, int forced_only, int only, cudaGraphConditionalHandle cond_cell,
-                         cudaGraphConditionalHandle cond_list, int set_cond) {
+                         cudaGraphConditionalHandle cond_list, int set_cond, cudaGraphConditionalHandle cond_var,
+                         int set_var) {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -164,6 +165,13 @@ __global__ void k_decide(EngineDev E, int forced_only, int only, cudaGraphCondit
             cudaGraphSetConditional(cond_list, any ? 1u : 0u);
             if (any) *E.cond_runs += 1ull;
         }
+        // force-pass code variant of this step: fixed by system 0's
+        // force_unroll, else the tuner's
+        ForceTune* tu = E.tune;
+        const int fu = E.nsys > 0 ? E.sys[0].force_unroll : 0;
+        const int sel = fu == 4 ? 0 : fu == 2 ? 1 : fu == 1 ? 2 : tu->cur;
+        tu->sel = sel;
+        if (set_var) cudaGraphSetConditional(cond_var, (unsigned)sel);
     }
 }
 
@@ -827,9 +835,11 @@ __global__ void k_lwrite(EngineDev E, int only) {
 
 // ---------------------------------------------------------------- launchers
 void launch_decide(const EngineHost& H, cudaStream_t s, int forced_only, int only,
-                   cudaGraphConditionalHandle cond_cell, cudaGraphConditionalHandle cond_list, bool set_cond) {
+                   cudaGraphConditionalHandle cond_cell, cudaGraphConditionalHandle cond_list, bool set_cond,
+                   cudaGraphConditionalHandle cond_var, bool set_var) {
     H.rec("decide", s);
-    k_decide<<<1, 1024, 0, s>>>(H.dev, forced_only, only, cond_cell, cond_list, set_cond ? 1 : 0);
+    k_decide<<<1, 1024, 0, s>>>(H.dev, forced_only, only, cond_cell, cond_list, set_cond ? 1 : 0, cond_var,
+                                set_var ? 1 : 0);
     H.count(1);
 }
 
@@ -872,7 +882,7 @@ void launch_list_build(const EngineHost& H, cudaStream_t s, bool rec) {
 // Decision and rebuild launched directly (outside a step graph): the rebuild
 // kernels run and return at once unless a system rebuilds.
 void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int only) {
-    launch_decide(H, s, forced_only, only, 0, 0, false);
+    launch_decide(H, s, forced_only, only, 0, 0, false, 0, false);
     launch_cell_build(H, s, true);
     launch_list_build(H, s, true);
 }

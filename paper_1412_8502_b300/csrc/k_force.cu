@@ -55,20 +55,22 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 
 enum PairClass { kPPNuc = 0, kPPCoul = 1, kNucCross = 2, kNucSame = 3 };
 
-// Two code variants of the split force pass, chosen per system and step:
+// Three code variants of the split force pass, chosen per system and step:
 // long unrolled loops (kULong: rotated blocks 4 steps, the tile with itself
-// 8 sources) and a compact one (kUCompact: 2 and 2).  Where the far Coulomb
-// field dominates (dense states), one block kind runs on most warps and the
-// long loops issue best; where nuclear pairs are a large part of the work
-// (clustered, dilute states), warps of one SM run several block kinds at a
-// time, and the long variant's code no longer fits the instruction cache
-// (ncu: 6 "no instruction" stalls per issue at rho = 0.00125 against 0.3 in
-// the dense state).  Both variants do the same arithmetic in the same order.
+// 8 sources), compact (2 and 2) and minimal (1 and 2).  Where the far
+// Coulomb field dominates (dense states), one block kind runs on most warps
+// and the long loops issue best; where nuclear pairs are a large part of the
+// work (clustered, dilute states), warps of one SM run several block kinds
+// at a time and the long code no longer fits the instruction cache (ncu:
+// 6 "no instruction" stalls per issue at rho = 0.00125 against 0.3 in the
+// dense state); the smaller variants trade instruction-level parallelism
+// for footprint.  All variants do the same arithmetic in the same order.
 #ifndef PASTA_N3_UNROLL
 #define PASTA_N3_UNROLL 4            // steps unrolled in a rotated block, long variant
 #endif
 constexpr int kULong = PASTA_N3_UNROLL;
 constexpr int kUCompact = 2;
+constexpr int kUMinimal = 1;
 __host__ __device__ constexpr int self_unroll(int kU) { return kU == kULong ? 8 : 2; }
 
 struct PairConsts {
@@ -690,33 +692,33 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
 }
 
 // kSingle: the engine holds one system, whose pair constants come in as a
-// kernel parameter (constant bank: operands without registers).  The code
-// variant comes from the system's force_unroll, or (0) from the device
-// tuner; block 0 records the start of the pass for the tuner.
-template <bool kEnergy, bool kSingle>
+// kernel parameter (constant bank: operands without registers).  kVar: the
+// code variant (0 long, 1 compact, 2 minimal), each its own kernel so that
+// the variants do not share one register allocation and code layout (one
+// kernel holding all three made the long variant 1.8% slower).  gate: the
+// launch returns at once unless kVar is this step's selection (plain graphs
+// launch all three).  Block 0 records the start of the pass for the tuner.
+template <bool kEnergy, bool kSingle, int kVar>
 __global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS)
-    k_force_split(EngineDev E, int only, const __grid_constant__ PairF pf) {
+    k_force_split(EngineDev E, int only, const __grid_constant__ PairF pf, int gate) {
     __shared__ WarpQueues qs[kForceWarps];
     ForceTune* tu = E.tune;
+    if (gate && tu->sel != kVar) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) tu->t_start = global_ns();   // k_force_fix takes the end
+    constexpr int kU = kVar == 0 ? kULong : kVar == 1 ? kUCompact : kUMinimal;
+    constexpr int kUWrap = kVar == 0 ? kULong : kUCompact;                  // per-pair wrap halves it
     const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
-    const int s = g < E.nitems ? E.item_sys[g] : -1;
-    if (s >= 0 && (only < 0 || s == only)) {
-        const SysConst& S = E.sys[s];
-        const int v = g - S.item_base;
-        if (S.list_kind == 0 && v < S.n_items) {       // per-particle lists: k_force_verlet
-            WarpQueues& Q = qs[threadIdx.x >> 5];
-            const PairF& P = kSingle ? pf : S.pf;
-            const bool compact = S.force_unroll == kUCompact || (S.force_unroll == 0 && tu->cur == 1);
-            if (S.st->need_wrap) {
-                if (compact) force_item<true, kEnergy, kUCompact>(S, P, v, Q);
-                else force_item<true, kEnergy, kULong>(S, P, v, Q);
-            } else {
-                if (compact) force_item<false, kEnergy, kUCompact>(S, P, v, Q);
-                else force_item<false, kEnergy, kULong>(S, P, v, Q);
-            }
-        }
-    }
+    if (g >= E.nitems) return;
+    const int s = E.item_sys[g];
+    if (s < 0 || (only >= 0 && s != only)) return;
+    const SysConst& S = E.sys[s];
+    if (S.list_kind != 0) return;          // per-particle lists: k_force_verlet
+    const int v = g - S.item_base;
+    if (v >= S.n_items) return;
+    WarpQueues& Q = qs[threadIdx.x >> 5];
+    const PairF& P = kSingle ? pf : S.pf;
+    if (S.st->need_wrap) force_item<true, kEnergy, kUWrap>(S, P, v, Q);
+    else force_item<false, kEnergy, kU>(S, P, v, Q);
 }
 
 // ---------------------------------------------------------------- Verlet
@@ -1068,27 +1070,42 @@ __global__ void k_ezero(EngineDev E, int only) {
     for (int k = 0; k < 6; ++k) E.sys[s].st->eacc[k] = 0;
 }
 
-void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt) {
+namespace {
+template <bool kEnergy, bool kSingle>
+void split_variant(const EngineHost& H, cudaStream_t s, int only, int var, bool gate) {
+    const EngineDev& E = H.dev;
+    const int nbi = (E.nitems + kForceWarps - 1) / kForceWarps;
+    const int g = gate ? 1 : 0;
+    if (var == 0) k_force_split<kEnergy, kSingle, 0><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0, g);
+    else if (var == 1) k_force_split<kEnergy, kSingle, 1><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0, g);
+    else k_force_split<kEnergy, kSingle, 2><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0, g);
+}
+}  // namespace
+
+void launch_force_pre(const EngineHost& H, cudaStream_t s, bool energy, int only) {
     const EngineDev& E = H.dev;
     if (energy) {
         k_ezero<<<(E.nsys + 127) / 128, 128, 0, s>>>(E, only);
         H.count(1);
     }
-    const int nb = (E.ntiles + kForceWarps - 1) / kForceWarps;
-    const int nbi = (E.nitems + kForceWarps - 1) / kForceWarps;
     H.rec("force", s);
-    if (H.precision == 1) {
-        if (energy) k_force_fp64<true><<<E.ntiles, kFW * 32, 0, s>>>(E, only, out_alt);
-        else k_force_fp64<false><<<E.ntiles, kFW * 32, 0, s>>>(E, only, out_alt);
-        H.count(1);
+}
+
+void launch_force_variant(const EngineHost& H, cudaStream_t s, bool energy, int only, int var, bool gate) {
+    if (H.single) {
+        if (energy) split_variant<true, true>(H, s, only, var, gate);
+        else split_variant<false, true>(H, s, only, var, gate);
     } else {
-        if (H.single) {
-            if (energy) k_force_split<true, true><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0);
-            else k_force_split<false, true><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0);
-        } else {
-            if (energy) k_force_split<true, false><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0);
-            else k_force_split<false, false><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0);
-        }
+        if (energy) split_variant<true, false>(H, s, only, var, gate);
+        else split_variant<false, false>(H, s, only, var, gate);
+    }
+    H.count(1);
+}
+
+void launch_force_post(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt) {
+    const EngineDev& E = H.dev;
+    if (H.precision != 1) {
+        const int nb = (E.ntiles + kForceWarps - 1) / kForceWarps;
         if (H.any_verlet) {
             H.rec("force_verlet", s);
             if (energy) k_force_verlet<true><<<E.ntiles, kVW * 32, 0, s>>>(E, only);
@@ -1097,9 +1114,24 @@ void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, in
         }
         H.rec("force_fix", s);
         k_force_fix<<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
-        H.count(2);
+        H.count(1);
     }
     launch_coulomb_pp(H, s, energy, only, out_alt);
+}
+
+// A whole force pass outside a step graph: the split kernel runs the long
+// variant (all variants give the same results).
+void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt) {
+    const EngineDev& E = H.dev;
+    launch_force_pre(H, s, energy, only);
+    if (H.precision == 1) {
+        if (energy) k_force_fp64<true><<<E.ntiles, kFW * 32, 0, s>>>(E, only, out_alt);
+        else k_force_fp64<false><<<E.ntiles, kFW * 32, 0, s>>>(E, only, out_alt);
+        H.count(1);
+    } else {
+        launch_force_variant(H, s, energy, only, 0, false);
+    }
+    launch_force_post(H, s, energy, only, out_alt);
 }
 
 }  // namespace pasta

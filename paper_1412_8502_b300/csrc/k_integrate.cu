@@ -324,27 +324,35 @@ __global__ void k_kick(EngineDev E) {
 
 // One block per system.  energy: also record the energy pass's totals.
 // Force-pass code variant (ForceTune): account the pass of the step just
-// taken (variant tu->cur), then advance the trial: kTuneSteps passes of the
-// long variant, kTuneSteps of the compact one, keep the faster.
+// taken (variant tu->cur), then advance the trial: kTuneSteps passes of each
+// variant in turn, then keep the fastest.
 __device__ inline void tune_step(ForceTune* tu, long long step, bool active) {
     if (!active) return;
     if (tu->phase != 0) {
-        tu->acc[tu->cur] += (double)tu->t_last;
-        tu->n[tu->cur] += 1;
-        if (tu->phase == 1 && tu->n[0] >= kTuneSteps) {
-            tu->phase = 2;
-            tu->cur = 1;
-        } else if (tu->phase == 2 && tu->n[1] >= kTuneSteps) {
-            tu->cur = tu->acc[1] < tu->acc[0] ? 1 : 0;
-            tu->phase = 0;
-            tu->trials += 1;
-            tu->last_step = step;
+        const int c = tu->cur;
+        tu->acc[c] += (double)tu->t_last;
+        tu->n[c] += 1;
+        if (tu->n[c] >= kTuneSteps) {
+            if (c + 1 < kVariants) {
+                tu->cur = c + 1;
+                tu->phase = c + 2;
+            } else {
+                int best = 0;
+                for (int k = 1; k < kVariants; ++k)
+                    if (tu->acc[k] < tu->acc[best]) best = k;
+                tu->cur = best;
+                tu->phase = 0;
+                tu->trials += 1;
+                tu->last_step = step;
+            }
         }
     } else if (step >= tu->last_step + kTuneEvery) {
         tu->phase = 1;
         tu->cur = 0;
-        tu->n[0] = tu->n[1] = 0;
-        tu->acc[0] = tu->acc[1] = 0.0;
+        for (int k = 0; k < kVariants; ++k) {
+            tu->n[k] = 0;
+            tu->acc[k] = 0.0;
+        }
     }
 }
 

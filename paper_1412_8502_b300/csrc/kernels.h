@@ -46,11 +46,19 @@ struct EngineHost {
 
 void launch_rebuild(const EngineHost& H, cudaStream_t s, int forced_only, int only);
 void launch_decide(const EngineHost& H, cudaStream_t s, int forced_only, int only,
-                   cudaGraphConditionalHandle cond_cell, cudaGraphConditionalHandle cond_list, bool set_cond);
+                   cudaGraphConditionalHandle cond_cell, cudaGraphConditionalHandle cond_list, bool set_cond,
+                   cudaGraphConditionalHandle cond_var, bool set_var);
 void launch_cell_build(const EngineHost& H, cudaStream_t s, bool rec);
 void launch_list_build(const EngineHost& H, cudaStream_t s, bool rec);
 void launch_cluster_lists(const EngineHost& H, cudaStream_t s, int phase, int only);
 void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt);
+// The force pass in three parts, for step graphs: energy clear; the split
+// kernel of one code variant (gate: the kernel returns at once unless the
+// variant is this step's selection); the Verlet-list pass, the fixed-point
+// conversion and the all-pairs Coulomb term.
+void launch_force_pre(const EngineHost& H, cudaStream_t s, bool energy, int only);
+void launch_force_variant(const EngineHost& H, cudaStream_t s, bool energy, int only, int var, bool gate);
+void launch_force_post(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt);
 void launch_coulomb_pp(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt);
 void launch_init(const EngineHost& H, cudaStream_t s, const unsigned long long* d_seeds);
 void launch_sd_update(const EngineHost& H, cudaStream_t s);

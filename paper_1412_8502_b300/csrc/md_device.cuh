@@ -105,7 +105,7 @@ struct SysConst {
     int thermostat_every, rebuild_every, coulomb, energy_every;
     int affine;              // scale positions with the box (option, not the paper)
     int list_kind;           // 0 half tile-pair lists, 1 per-particle Verlet lists
-    int force_unroll;        // split force-pass code variant: 0 automatic, 2 compact, 4 long
+    int force_unroll;        // split force-pass code variant: 0 automatic, 4 long, 2 compact, 1 minimal
     PairF pf;
     // state arrays (index [cur] is current)
     double* x[2];
@@ -140,24 +140,28 @@ struct SysConst {
 };
 
 // Global tables of an engine.
-// Choice between the two code variants of the split force pass, made on
-// the device by timing (the variants give bitwise the same results): every
+// Choice between the code variants of the split force pass, made on the
+// device by timing (the variants give bitwise the same results): every
 // kTuneEvery steps kTuneSteps force passes run with each variant, their
 // durations (%globaltimer at the start of the force kernel's block 0 to the
 // start of the k_force_fix launch that follows it) are summed, and the
-// faster variant is kept until the next trial.  The first trial comes at
+// fastest variant is kept until the next trial.  Each variant is its own
+// kernel: in a step graph a SWITCH node launches the selected one (k_decide
+// sets it); in plain graphs all three are launched and two return at once.  The first trial comes at
 // step kTuneEvery: until then the long variant runs (systems start dense).
 constexpr int kTuneEvery = 500;
 constexpr int kTuneSteps = 4;
+constexpr int kVariants = 3;         // long, compact, minimal
 struct ForceTune {
     unsigned long long t_start;  // start of the running force pass, ns
     unsigned long long t_last;   // duration of the last force pass, ns
-    int cur;                     // variant of the next pass: 0 long, 1 compact
-    int phase;                   // 0 idle, 1 timing the long, 2 timing the compact variant
+    int cur;                     // tuner: variant to run next: 0 long, 1 compact, 2 minimal
+    int sel;                     // variant of this step's pass (set by k_decide from cur or force_unroll)
+    int phase;                   // 0 idle, 1 + v timing variant v
     int trials;                  // trials completed
-    int n[2];
+    int n[kVariants];
     long long last_step;         // step of system 0 at the last decision (0 before the first)
-    double acc[2];               // summed durations per variant, ns
+    double acc[kVariants];       // summed durations per variant, ns
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
