@@ -303,8 +303,9 @@ def run_gpu(args):
                                      "candidate_pairs_per_step": cand / K,
                                      "candidate_efficiency": (pairs_nuc + pairs_coul) / max(cand, 1)}},
         "force_code": {"variant": info["force_code"], "tuner_trials": info["force_trials"],
-                       "note": "split force-pass code in use: 4 long unrolled loops, 2 compact; chosen on the device "
-                               "by timing both every 500 steps (bitwise the same results)"},
+                       "note": "split force-pass code in use: 4 long unrolled loops, 2 compact, 1 minimal; chosen on "
+                               "the device by timing all three every 500 steps from step 500 (bitwise the same "
+                               "results)"},
         "tiles": {"count": info["tiles"], "list_entries": info["list_entries"], "rebuilds": info["rebuilds"],
                   "halfext_mean_fm": info["tile_halfext_mean"], "halfext_max_fm": info["tile_halfext_max"],
                   "need_wrap": info["need_wrap"]},
@@ -508,6 +509,8 @@ def run_full(args):
     p.T = W["T"]
     if args.precision == "fp64":
         p.precision = md.MD_PREC_FP64
+    if args.force_unroll is not None:
+        p.force_unroll = args.force_unroll
     s = md.System(N, W["Yp"], W["rho"], W["T"], W["seed"], p)
     stream = torch.cuda.Stream()
     s.set_stream(stream)
@@ -535,6 +538,11 @@ def run_full(args):
                          "A_mean": round(cst["A_mean"], 2), "Z_mean": round(cst["Z_mean"], 2),
                          "m_free_n": round(cst["m_free_n"], 5), "rebuilds": info["rebuilds"],
                          "force_code": info["force_code"]})
+    if args.late_pass:                 # one energy force pass of the final state, for kernel profilers
+        torch.cuda.nvtx.range_push("late")
+        s.energy()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     s.close()
     tot_ms = sum(r["ms_per_step"] * chunk for r in rows)
     first, last = rows[0], rows[-1]
@@ -623,6 +631,10 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=4.0)
     ap.add_argument("--precision", default="split", choices=["split", "fp64"],
                     help="with --full-steps: split FP32/FP64 (default) or the FP64 mode")
+    ap.add_argument("--force-unroll", type=int, default=None, choices=[0, 1, 2, 4],
+                    help="with --full-steps: fix the force-pass code variant (md_params.force_unroll)")
+    ap.add_argument("--late-pass", action="store_true",
+                    help="with --full-steps: one more force pass of the final state in an NVTX range 'late'")
     ap.add_argument("--full-steps", type=int, default=0,
                     help="run the workload's schedule for this many steps (20000: the whole expansion) in "
                          "1,000-step chunks and report throughput per density window instead")

@@ -106,7 +106,9 @@ typedef struct {
                                 at once: clustered, dilute states); 0 (default) =
                                 chosen on the device every 500 steps (from step
                                 500 on; the long one before) by timing 4 force
-                                passes of each.  Results are bitwise the same. */
+                                passes of each, in engines of at least 131,072
+                                nucleons (smaller ones run the long variant).
+                                Results are bitwise the same. */
 } md_params;
 
 typedef struct {

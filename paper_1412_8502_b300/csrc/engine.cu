@@ -430,6 +430,13 @@ int Engine::build_tables() {
     E.any_rebuild = d_any_;
     E.cond_runs = d_cond_runs_;
     E.tune = d_tune_;
+    long long ntot = 0;
+    for (SysHost* h : sys) ntot += h->N;
+    E.tune_variants = (precision != MD_PREC_FP64 && ntot >= kVariantMinN) ? 1 : 0;
+    {
+        const int fu = sys.empty() ? 0 : (int)sys[0]->prm.force_unroll;
+        H_.fixed_var = fu == 2 ? 1 : fu == 1 ? 2 : 0;
+    }
     H_.precision = precision;
     H_.any_pp = false;
     H_.any_verlet = false;
@@ -510,10 +517,14 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
     // node of the force-pass code variant
     const bool cond = sys.empty() || sys[0]->prm.cond_graph != 0;
     const bool split = precision != MD_PREC_FP64;
+    const bool multi = split && H_.dev.tune_variants;     // the step selects the force-pass variant
+    // otherwise the variant md_params.force_unroll fixes (0: the long one)
+    const int fu = sys.empty() ? 0 : (int)sys[0]->prm.force_unroll;
+    const int fixed_var = fu == 2 ? 1 : fu == 1 ? 2 : 0;
     cudaGraphConditionalHandle h[3] = {0, 0, 0};
     if (cond) {
         for (int k = 0; k < 2; ++k) CK(cudaGraphConditionalHandleCreate(&h[k], graph, 0, cudaGraphCondAssignDefault));
-        if (split) CK(cudaGraphConditionalHandleCreate(&h[2], graph, 0, cudaGraphCondAssignDefault));
+        if (multi) CK(cudaGraphConditionalHandleCreate(&h[2], graph, 0, cudaGraphCondAssignDefault));
     }
     std::vector<cudaGraphNode_t> front;
     int rc;
@@ -599,11 +610,14 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
             launch_list_build(H_, stream_, false);
         });
         if (rc) return rc;
-        // all three force-pass variants; two return at once
+        // all three force-pass variants (two return at once), or the fixed one
         return segment([&] {
             if (split) {
                 launch_force_pre(H_, stream_, fe, -1);
-                for (int v = 0; v < kVariants; ++v) launch_force_variant(H_, stream_, fe, -1, v, true);
+                if (multi)
+                    for (int v = 0; v < kVariants; ++v) launch_force_variant(H_, stream_, fe, -1, v, true);
+                else
+                    launch_force_variant(H_, stream_, fe, -1, fixed_var, false);
                 launch_force_post(H_, stream_, fe, -1, 0);
             } else {
                 launch_force(H_, stream_, fe, -1, 0);
@@ -614,7 +628,7 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
         if ((rc = segment([&] {
                  if (kind == 0) launch_kick_drift(H_, stream_);
                  else launch_sd_update(H_, stream_);
-                 launch_decide(H_, stream_, 0, -1, h[0], h[1], true, h[2], split);
+                 launch_decide(H_, stream_, 0, -1, h[0], h[1], true, h[2], multi);
                  H_.rec("cell_build", stream_);
              })))
             return rc;
@@ -624,6 +638,12 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
     }
     if (!split) return segment([&] {
         launch_force(H_, stream_, fe, -1, 0);
+        closing();
+    });
+    if (!multi) return segment([&] {
+        launch_force_pre(H_, stream_, fe, -1);
+        launch_force_variant(H_, stream_, fe, -1, fixed_var, false);
+        launch_force_post(H_, stream_, fe, -1, 0);
         closing();
     });
     if ((rc = segment([&] { launch_force_pre(H_, stream_, fe, -1); }))) return rc;
@@ -994,7 +1014,8 @@ int Engine::set_params(int idx, const md_params& p) {
         cudaStreamSynchronize(stream_);
         drop_graphs();
     }
-    if ((h.prm.cond_graph != 0) != (p.cond_graph != 0)) {   // graph layout changes
+    if (idx == 0) H_.fixed_var = p.force_unroll == 2 ? 1 : p.force_unroll == 1 ? 2 : 0;
+    if ((h.prm.cond_graph != 0) != (p.cond_graph != 0) || h.prm.force_unroll != p.force_unroll) {   // graph layout
         cudaStreamSynchronize(stream_);
         drop_graphs();
     }
@@ -1142,7 +1163,8 @@ int Engine::info(int idx, md_info_t* out) {
     CK(cudaMemcpyAsync(&tu, d_tune_, sizeof(tu), cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));
     static const int code[kVariants] = {4, 2, 1};
-    out->force_code = code[tu.sel < 0 || tu.sel >= kVariants ? 0 : tu.sel];
+    const int fu = (int)h.prm.force_unroll;
+    out->force_code = H_.dev.tune_variants ? code[tu.sel < 0 || tu.sel >= kVariants ? 0 : tu.sel] : (fu ? fu : 4);
     out->force_trials = tu.trials;
     return MD_OK;
 }

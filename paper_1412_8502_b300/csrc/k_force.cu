@@ -691,16 +691,15 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
     }
 }
 
-// kSingle: the engine holds one system, whose pair constants come in as a
-// kernel parameter (constant bank: operands without registers).  kVar: the
-// code variant (0 long, 1 compact, 2 minimal), each its own kernel so that
-// the variants do not share one register allocation and code layout (one
-// kernel holding all three made the long variant 1.8% slower).  gate: the
-// launch returns at once unless kVar is this step's selection (plain graphs
-// launch all three).  Block 0 records the start of the pass for the tuner.
-template <bool kEnergy, bool kSingle, int kVar>
+// kVar: the code variant (0 long, 1 compact, 2 minimal), each its own
+// kernel so that the variants do not share one register allocation and code
+// layout (one kernel holding all three made the long variant 1.8% slower).
+// gate: the launch returns at once unless kVar is this step's selection
+// (plain graphs launch all three).  Block 0 records the start of the pass
+// for the tuner.
+template <bool kEnergy, int kVar>
 __global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS)
-    k_force_split(EngineDev E, int only, const __grid_constant__ PairF pf, int gate) {
+    k_force_split(EngineDev E, int only, int gate) {
     __shared__ WarpQueues qs[kForceWarps];
     ForceTune* tu = E.tune;
     if (gate && tu->sel != kVar) return;
@@ -716,7 +715,7 @@ __global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS)
     const int v = g - S.item_base;
     if (v >= S.n_items) return;
     WarpQueues& Q = qs[threadIdx.x >> 5];
-    const PairF& P = kSingle ? pf : S.pf;
+    const PairF& P = S.pf;
     if (S.st->need_wrap) force_item<true, kEnergy, kUWrap>(S, P, v, Q);
     else force_item<false, kEnergy, kU>(S, P, v, Q);
 }
@@ -1071,14 +1070,14 @@ __global__ void k_ezero(EngineDev E, int only) {
 }
 
 namespace {
-template <bool kEnergy, bool kSingle>
+template <bool kEnergy>
 void split_variant(const EngineHost& H, cudaStream_t s, int only, int var, bool gate) {
     const EngineDev& E = H.dev;
     const int nbi = (E.nitems + kForceWarps - 1) / kForceWarps;
     const int g = gate ? 1 : 0;
-    if (var == 0) k_force_split<kEnergy, kSingle, 0><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0, g);
-    else if (var == 1) k_force_split<kEnergy, kSingle, 1><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0, g);
-    else k_force_split<kEnergy, kSingle, 2><<<nbi, kForceWarps * 32, 0, s>>>(E, only, H.pf0, g);
+    if (var == 0) k_force_split<kEnergy, 0><<<nbi, kForceWarps * 32, 0, s>>>(E, only, g);
+    else if (var == 1) k_force_split<kEnergy, 1><<<nbi, kForceWarps * 32, 0, s>>>(E, only, g);
+    else k_force_split<kEnergy, 2><<<nbi, kForceWarps * 32, 0, s>>>(E, only, g);
 }
 }  // namespace
 
@@ -1092,13 +1091,8 @@ void launch_force_pre(const EngineHost& H, cudaStream_t s, bool energy, int only
 }
 
 void launch_force_variant(const EngineHost& H, cudaStream_t s, bool energy, int only, int var, bool gate) {
-    if (H.single) {
-        if (energy) split_variant<true, true>(H, s, only, var, gate);
-        else split_variant<false, true>(H, s, only, var, gate);
-    } else {
-        if (energy) split_variant<true, false>(H, s, only, var, gate);
-        else split_variant<false, false>(H, s, only, var, gate);
-    }
+    if (energy) split_variant<true>(H, s, only, var, gate);
+    else split_variant<false>(H, s, only, var, gate);
     H.count(1);
 }
 
@@ -1119,8 +1113,8 @@ void launch_force_post(const EngineHost& H, cudaStream_t s, bool energy, int onl
     launch_coulomb_pp(H, s, energy, only, out_alt);
 }
 
-// A whole force pass outside a step graph: the split kernel runs the long
-// variant (all variants give the same results).
+// A whole force pass outside a step graph: the split kernel runs the variant
+// force_unroll fixes, the long one by default (all give the same results).
 void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt) {
     const EngineDev& E = H.dev;
     launch_force_pre(H, s, energy, only);
@@ -1129,7 +1123,7 @@ void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, in
         else k_force_fp64<false><<<E.ntiles, kFW * 32, 0, s>>>(E, only, out_alt);
         H.count(1);
     } else {
-        launch_force_variant(H, s, energy, only, 0, false);
+        launch_force_variant(H, s, energy, only, H.fixed_var, false);
     }
     launch_force_post(H, s, energy, only, out_alt);
 }

@@ -391,7 +391,7 @@ __global__ void k_finalize(EngineDev E, int energy) {
         st->e_cand = st->eacc[5] / 2;
         st->have_energy = 1;
     }
-    if (s == 0 && E.tune) tune_step(E.tune, st->step, S.force_unroll == 0 && S.list_kind == 0);
+    if (s == 0 && E.tune) tune_step(E.tune, st->step, E.tune_variants && S.force_unroll == 0 && S.list_kind == 0);
 }
 
 // Energies at the current state (md_energy): KE from the block partials of

@@ -31,8 +31,7 @@ struct EngineHost {
     int precision = 0;
     bool any_pp = false;     // some system uses the all-pairs Coulomb (coulomb = 2)
     bool any_verlet = false; // some system uses per-particle Verlet lists (list_kind 1)
-    bool single = false;     // one system: its pair constants are passed as kernel parameters
-    PairF pf0{};             // that system's constants (kept equal to its SysConst::pf)
+    int fixed_var = 0;       // force-pass variant of launches outside step graphs (system 0's force_unroll)
     void* owner = nullptr;   // Engine*, for rec/count callbacks
     void (*rec_fn)(void*, const char*, cudaStream_t) = nullptr;
     void (*count_fn)(void*, int) = nullptr;

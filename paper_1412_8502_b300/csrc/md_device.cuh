@@ -185,7 +185,12 @@ struct EngineDev {
     int* any_rebuild;        // set when any system rebuilds this step
     unsigned long long* cond_runs;   // step-graph rebuilds run through the conditional node
     ForceTune* tune;                 // force-pass code variant (automatic choice)
+    int tune_variants;               // 1: steps select the variant (SWITCH node) and the tuner runs
 };
+
+// Engines below this many particles run one force-pass variant: the SWITCH
+// node costs ~7 us per step, more than the variants gain on short passes.
+constexpr long long kVariantMinN = 131072;
 
 // Force work items of a system.  A proton tile's list holds its near
 // entries (nuclear range) first and its Coulomb-only entries from the back of

@@ -411,21 +411,29 @@ def test_force_code_variants_agree_bitwise(md, name):
 
 
 def test_force_code_tuner_reports_its_choice(md):
-    """force_unroll = 0: the device tuner times both variants every 500 steps
-    (from step 500) and reports the one in use; a fixed force_unroll is
-    reported as set."""
+    """Engines of at least 131,072 nucleons select the force-pass variant per
+    step (a SWITCH graph node) and the device tuner times all three every 500
+    steps from step 500: the trial runs every variant and the trajectory is
+    bitwise that of the fixed long variant.  Smaller engines run the variant
+    force_unroll fixes (the long one by default)."""
+    x, t, L = cfg_liquid(135000, 0.40, 0.080, 12)
+    outs = []
+    for fu in (4, 0):
+        s, _ = load(md, x, t, L, 0, T=0.5, force_unroll=fu)
+        s.step(10, 7.5e-5)
+        assert s.info()["force_trials"] == 0 and s.info()["force_code"] == 4     # long until step 500
+        s.step(510, 7.5e-5)                  # the trial: steps 501-512, four passes of each variant
+        info = s.info()
+        assert info["force_trials"] == (1 if fu == 0 else 0) and info["force_code"] in (1, 2, 4)
+        outs.append(s.state(f=True))
+        s.close()
+    for k in ("x", "v", "f"):
+        assert np.array_equal(outs[0][k], outs[1][k])
     x, t, L = CONFIGS["liquid_2000"]()
-    s, _ = load(md, x, t, L, 0)
-    s.step(10, 0.0)
-    assert s.info()["force_trials"] == 0 and s.info()["force_code"] == 4     # long until step 500
-    s.step(510, 0.0)                 # the trial: steps 501-512, four passes of each variant
-    info = s.info()
-    assert info["force_trials"] == 1 and info["force_code"] in (1, 2, 4)
-    s.close()
-    for fu in (1, 2, 4):
+    for fu in (0, 1, 2, 4):
         s, _ = load(md, x, t, L, 0, force_unroll=fu)
-        s.step(10, 0.0)
-        assert s.info()["force_code"] == fu and s.info()["force_trials"] == 0
+        s.step(520, 0.0)
+        assert s.info()["force_code"] == (fu or 4) and s.info()["force_trials"] == 0
         s.close()
     with pytest.raises(md.MDError):
         load(md, x, t, L, 0, force_unroll=3)
