@@ -587,9 +587,12 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
         front.assign(1, node);
         return MD_OK;
     };
-    // the closing part of a step: forces, kick, finalisation
+    // split precision steps convert the force accumulators in the closing kick
+    // (not with the all-pairs Coulomb term, which adds to the converted forces)
+    const bool fuse = split && kind == 0 && !H_.any_pp;
+    // the closing part of a step: kick, finalisation
     auto closing = [&]() {
-        if (kind == 0) launch_kick_finalize(H_, stream_, energy);
+        if (kind == 0) launch_kick_finalize(H_, stream_, energy, fuse);
         if (timing_) {
             cudaEvent_t ev;
             cudaEventCreate(&ev);
@@ -613,12 +616,12 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
         // all three force-pass variants (two return at once), or the fixed one
         return segment([&] {
             if (split) {
-                launch_force_pre(H_, stream_, fe, -1);
+                launch_force_pre(H_, stream_, fe, -1, false);
                 if (multi)
                     for (int v = 0; v < kVariants; ++v) launch_force_variant(H_, stream_, fe, -1, v, true);
                 else
                     launch_force_variant(H_, stream_, fe, -1, fixed_var, false);
-                launch_force_post(H_, stream_, fe, -1, 0);
+                launch_force_post(H_, stream_, fe, -1, 0, !fuse);
             } else {
                 launch_force(H_, stream_, fe, -1, 0);
             }
@@ -641,15 +644,15 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
         closing();
     });
     if (!multi) return segment([&] {
-        launch_force_pre(H_, stream_, fe, -1);
+        launch_force_pre(H_, stream_, fe, -1, false);
         launch_force_variant(H_, stream_, fe, -1, fixed_var, false);
-        launch_force_post(H_, stream_, fe, -1, 0);
+        launch_force_post(H_, stream_, fe, -1, 0, !fuse);
         closing();
     });
-    if ((rc = segment([&] { launch_force_pre(H_, stream_, fe, -1); }))) return rc;
+    if ((rc = segment([&] { launch_force_pre(H_, stream_, fe, -1, false); }))) return rc;
     if ((rc = variant_switch())) return rc;
     return segment([&] {
-        launch_force_post(H_, stream_, fe, -1, 0);
+        launch_force_post(H_, stream_, fe, -1, 0, !fuse);
         closing();
     });
 }

@@ -144,6 +144,9 @@ __global__ void k_decide(EngineDev E, int forced_only, int only, cudaGraphCondit
             need |= (st->step - st->last_build >= S.rebuild_every) || (h <= 0.0f) || (md2 > h * h);
         }
         if (only >= 0 && s != only) need = 0;
+        // energy record of this step's force pass (step graphs launch no
+        // separate clear)
+        for (int k = 0; k < 6; ++k) st->eacc[k] = 0;
         st->maxdisp2 = 0u;
         st->rebuild = need;
         st->cur_next = need ? (st->cur ^ 1) : st->cur;

@@ -1081,9 +1081,9 @@ void split_variant(const EngineHost& H, cudaStream_t s, int only, int var, bool 
 }
 }  // namespace
 
-void launch_force_pre(const EngineHost& H, cudaStream_t s, bool energy, int only) {
+void launch_force_pre(const EngineHost& H, cudaStream_t s, bool energy, int only, bool clear) {
     const EngineDev& E = H.dev;
-    if (energy) {
+    if (energy && clear) {
         k_ezero<<<(E.nsys + 127) / 128, 128, 0, s>>>(E, only);
         H.count(1);
     }
@@ -1096,7 +1096,7 @@ void launch_force_variant(const EngineHost& H, cudaStream_t s, bool energy, int 
     H.count(1);
 }
 
-void launch_force_post(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt) {
+void launch_force_post(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt, bool fix) {
     const EngineDev& E = H.dev;
     if (H.precision != 1) {
         const int nb = (E.ntiles + kForceWarps - 1) / kForceWarps;
@@ -1106,9 +1106,11 @@ void launch_force_post(const EngineHost& H, cudaStream_t s, bool energy, int onl
             else k_force_verlet<false><<<E.ntiles, kVW * 32, 0, s>>>(E, only);
             H.count(1);
         }
-        H.rec("force_fix", s);
-        k_force_fix<<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
-        H.count(1);
+        if (fix) {
+            H.rec("force_fix", s);
+            k_force_fix<<<nb, kForceWarps * 32, 0, s>>>(E, only, out_alt);
+            H.count(1);
+        }
     }
     launch_coulomb_pp(H, s, energy, only, out_alt);
 }

@@ -208,29 +208,46 @@ __global__ void k_sub_com(EngineDev E) {
 }
 
 // Pending thermostat factor on v; with the affine option, the pending box
-// factor on x (displacement and tile-frame positions follow).
+// factor on x (displacement and tile-frame positions follow).  Launched with
+// a small grid that strides over the blocks of slots: on most steps no system
+// has a factor pending and every thread returns after reading the flags.
 __global__ void k_rescale(EngineDev E, int only) {
-    Slot o;
-    if (!slot_of(E, only, o) || !o.valid) return;
-    const SysConst& S = E.sys[o.s];
-    const SysState* st = S.st;
-    const double f = st->vscale, g = st->xscale;
-    const int c = st->cur, N = S.N, p = o.p;
-    if (f != 1.0) {
-        S.v[c][p] *= f;
-        S.v[c][N + p] *= f;
-        S.v[c][2 * N + p] *= f;
+    bool any = false;
+    for (int s = 0; s < E.nsys; ++s) {
+        const SysState* st = E.sys[s].st;
+        any |= (st->vscale != 1.0) || (st->xscale != 1.0);
     }
-    if (g != 1.0) {
-        const float4 prev = S.xhi[o.t * kTile + (threadIdx.x & 31)];
-        double xs[3];
-        for (int a = 0; a < 3; ++a) {
-            const double x0 = S.x[c][a * N + p];
-            xs[a] = x0 * g;
-            S.x[c][a * N + p] = xs[a];
-            S.disp[a * N + p] += (float)(xs[a] - x0);
+    if (!any) return;
+    const int nb = (E.ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int g = b * kTilesPerBlock + (threadIdx.x >> 5);
+        if (g >= E.ntiles) continue;
+        const int s = E.tile_sys[g];
+        if (s < 0 || (only >= 0 && s != only)) continue;
+        const SysConst& S = E.sys[s];
+        const int t = g - S.tile_base;
+        if (t >= S.T) continue;
+        const int p = tile_slot0(S, t) + (threadIdx.x & 31);
+        if (p >= tile_end(S, t)) continue;
+        const SysState* st = S.st;
+        const double f = st->vscale, gx = st->xscale;
+        const int c = st->cur, N = S.N;
+        if (f != 1.0) {
+            S.v[c][p] *= f;
+            S.v[c][N + p] *= f;
+            S.v[c][2 * N + p] *= f;
         }
-        write_xt_moved(S, o.t, threadIdx.x & 31, xs, st->L, narrow_trunc(st->L), prev);
+        if (gx != 1.0) {
+            const float4 prev = S.xhi[t * kTile + (threadIdx.x & 31)];
+            double xs[3];
+            for (int a = 0; a < 3; ++a) {
+                const double x0 = S.x[c][a * N + p];
+                xs[a] = x0 * gx;
+                S.x[c][a * N + p] = xs[a];
+                S.disp[a * N + p] += (float)(xs[a] - x0);
+            }
+            write_xt_moved(S, t, threadIdx.x & 31, xs, st->L, narrow_trunc(st->L), prev);
+        }
     }
 }
 
@@ -315,6 +332,38 @@ __global__ void k_kick(EngineDev E) {
         const double h = S.hkick;
         for (int a = 0; a < 3; ++a) {
             const double v = fma(h, to_double(F[a * N + p]), S.v[c][a * N + p]);
+            S.v[c][a * N + p] = v;
+            v2 = fma(v, v, v2);
+        }
+    }
+    block_sum1(S, v2);
+}
+
+// The closing half-kick fused with the conversion of the split force pass's
+// fixed-point accumulators (what k_force_fix does, in the same arithmetic):
+// F = FP32(facc) 2^-32 is stored for the next step's first half-kick and for
+// readers of the state, the accumulators are cleared, v += dt/(2M) F.  Its
+// start also closes the force pass's duration for the device tuner.
+__global__ void k_kick_fix(EngineDev E) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) E.tune->t_last = global_ns() - E.tune->t_start;
+    Slot o;
+    if (!slot_of(E, -1, o)) return;
+    const SysConst& S = E.sys[o.s];
+    const SysState* st = S.st;
+    double v2 = 0.0;
+    if (o.valid) {
+        const int c = st->cur, N = S.N, p = o.p;
+        long long q[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) q[a] = S.facc[a * N + p];
+        float* F = S.f32[c];
+        const double h = S.hkick;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            S.facc[a * N + p] = 0;
+            const float fa = __ll2float_rn(q[a]) * (1.0f / 4294967296.0f);
+            F[a * N + p] = fa;
+            const double v = fma(h, to_double(fa), S.v[c][a * N + p]);
             S.v[c][a * N + p] = v;
             v2 = fma(v, v, v2);
         }
@@ -532,15 +581,16 @@ void launch_kick_drift(const EngineHost& H, cudaStream_t s) {
     H.count(1);
 }
 
-void launch_kick_finalize(const EngineHost& H, cudaStream_t s, bool energy) {
+void launch_kick_finalize(const EngineHost& H, cudaStream_t s, bool energy, bool fused_fix) {
     const EngineDev& E = H.dev;
     H.rec("kick", s);
     if (H.precision == 1) k_kick<double><<<nblk(E), kBlock, 0, s>>>(E);
+    else if (fused_fix) k_kick_fix<<<nblk(E), kBlock, 0, s>>>(E);
     else k_kick<float><<<nblk(E), kBlock, 0, s>>>(E);
     H.rec("finalize", s);
     k_finalize<<<E.nsys, kRed, 0, s>>>(E, energy ? 1 : 0);
     H.rec("rescale", s);
-    k_rescale<<<nblk(E), kBlock, 0, s>>>(E, -1);
+    k_rescale<<<std::min(nblk(E), 2 * 148), kBlock, 0, s>>>(E, -1);
     H.count(3);
 }
 

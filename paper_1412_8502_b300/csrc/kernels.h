@@ -55,14 +55,18 @@ void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, in
 // kernel of one code variant (gate: the kernel returns at once unless the
 // variant is this step's selection); the Verlet-list pass, the fixed-point
 // conversion and the all-pairs Coulomb term.
-void launch_force_pre(const EngineHost& H, cudaStream_t s, bool energy, int only);
+// clear: launch the energy clear (step graphs leave it to k_decide); fix:
+// launch k_force_fix (step graphs may fuse it into the closing kick).
+void launch_force_pre(const EngineHost& H, cudaStream_t s, bool energy, int only, bool clear = true);
 void launch_force_variant(const EngineHost& H, cudaStream_t s, bool energy, int only, int var, bool gate);
-void launch_force_post(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt);
+void launch_force_post(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt, bool fix = true);
 void launch_coulomb_pp(const EngineHost& H, cudaStream_t s, bool energy, int only, int out_alt);
 void launch_init(const EngineHost& H, cudaStream_t s, const unsigned long long* d_seeds);
 void launch_sd_update(const EngineHost& H, cudaStream_t s);
 void launch_kick_drift(const EngineHost& H, cudaStream_t s);
-void launch_kick_finalize(const EngineHost& H, cudaStream_t s, bool energy);
+// fused_fix: the closing kick also converts the split force pass's
+// fixed-point accumulators (the force pass was launched without k_force_fix).
+void launch_kick_finalize(const EngineHost& H, cudaStream_t s, bool energy, bool fused_fix);
 void launch_energy_now(const EngineHost& H, cudaStream_t s, int only, double* d_out);
 void launch_gather(const EngineHost& H, cudaStream_t s, int only, double* ox, double* ov, double* of,
                    int8_t* otype);
