@@ -177,14 +177,20 @@ __global__ void k_cl_link(EngineDev E, int only) {
     }
 }
 
-// Smallest original index per component.
+// Smallest original index per component.  Lanes of a warp with the same
+// root combine first (one atomic per root and warp: a large cluster would
+// otherwise serialise every proton's atomic on one address).
 __global__ void k_cl_minid(EngineDev E, int only) {
     const SysConst& S = E.sys[only];
     const ClusterBufs& B = *S.cl;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= S.Np) return;
-    const int r = uf_find(B.parent, q);
-    atomicMin(&B.minid[r], S.id[S.st->cur][q]);
+    const bool ok = q < S.Np;
+    const int r = ok ? uf_find(B.parent, q) : -1 - (int)(threadIdx.x & 31);
+    int id = ok ? S.id[S.st->cur][q] : 0x7fffffff;
+    const unsigned same = __match_any_sync(0xffffffffu, r);
+    const int lane = threadIdx.x & 31;
+    for (unsigned m = same; m; m &= m - 1) id = min(id, __shfl_sync(same, id, __ffs(m) - 1));
+    if (ok && lane == __ffs(same) - 1) atomicMin(&B.minid[r], id);
 }
 
 // Proton labels; neutron assignment (warp per neutron tile).
@@ -241,19 +247,25 @@ __global__ void k_cl_assign(EngineDev E, int only) {
     if (valid) B.label[p] = best_slot < 0 ? -1 : B.minid[uf_find(B.parent, best_slot)];
 }
 
-// Per-cluster counts (labels are original proton indices < Np).
+// Per-cluster counts (labels are original proton indices < Np).  Lanes of a
+// warp with the same label (and kind) add their counts in one atomic.
 __global__ void k_cl_count(EngineDev E, int only) {
     const SysConst& S = E.sys[only];
     const ClusterBufs& B = *S.cl;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= S.N) return;
-    const int lab = B.label[p];
+    const int lane = threadIdx.x & 31;
+    const bool ok = p < S.N;
+    const int lab = ok ? B.label[p] : -2;
+    const bool prot = ok && p < S.Np;
+    const unsigned same = __match_any_sync(0xffffffffu, lab);
+    const unsigned nprot = __popc(same & __ballot_sync(0xffffffffu, prot));
+    if (!ok || lane != __ffs(same) - 1) return;
     if (lab < 0) {
-        atomicAdd((unsigned long long*)&B.stats[1], 1ull);
+        atomicAdd((unsigned long long*)&B.stats[1], (unsigned long long)__popc(same));
         return;
     }
-    atomicAdd(&B.ac[lab], 1);
-    if (p < S.Np) atomicAdd(&B.zc[lab], 1);
+    atomicAdd(&B.ac[lab], __popc(same));
+    if (nprot) atomicAdd(&B.zc[lab], (int)nprot);
 }
 
 // Histograms over clusters; labels written in original order.
