@@ -764,6 +764,41 @@ __global__ void __launch_bounds__(kVB * 32) k_vbuild(EngineDev E) {
 
 // Cluster lists: count, scan, write into a buffer sized by the host.  Boxes
 // are those of the last rebuild; the cluster ranges add the skin.
+// Proton tiles J in cluster range of tile I, in ascending order: proton
+// super-tiles (32 consecutive tiles) out of range of I are skipped whole,
+// then the members of the others are tested (visit(J) for each hit).
+template <typename Visit>
+__device__ __forceinline__ void cluster_tiles(const SysConst& S, int I, int lane, const ListTest& T,
+                                              const float4& oI, const float* hI, Visit&& visit) {
+    const float R2 = (I < S.Tp) ? T.R2same : T.R2cross;
+    const int nsp = (S.Tp + kTile - 1) / kTile;          // super-tiles holding proton tiles
+    for (int s0 = 0; s0 < nsp; s0 += 32) {
+        const int sg = s0 + lane;
+        bool pass = false;
+        if (sg < nsp) {
+            const float4 c = S.sorg[sg], h = S.shalf[sg];
+            const float dd[3] = {oI.x - c.x, oI.y - c.y, oI.z - c.z};
+            const float hh[3] = {h.x, h.y, h.z};
+            float d2 = 0.0f;
+            for (int a = 0; a < 3; ++a) {
+                float d = dd[a];
+                d -= T.Lf * rintf(d * T.iLf);
+                const float gap = fmaxf(fabsf(d) - hI[a] - hh[a], 0.0f);
+                d2 = fmaf(gap, gap, d2);
+            }
+            pass = d2 < R2;
+        }
+        unsigned sm = __ballot_sync(0xffffffffu, pass);
+        while (sm) {
+            const int b = __ffs(sm) - 1;
+            sm &= sm - 1;
+            const int J = (s0 + b) * kTile + lane;
+            const int e = J < S.Tp ? list_entry(S, I, J, oI, hI, T) : -1;
+            visit(e);
+        }
+    }
+}
+
 __global__ void k_lcount(EngineDev E, int only) {
     const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -778,11 +813,7 @@ __global__ void k_lcount(EngineDev E, int only) {
     const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
     const float hI[3] = {S.thalf[3 * I], S.thalf[3 * I + 1], S.thalf[3 * I + 2]};
     int cnt = 0;
-    for (int J0 = 0; J0 < S.Tp; J0 += 32) {
-        const int J = J0 + lane;
-        const bool hit = J < S.Tp && list_entry(S, I, J, oI, hI, T) >= 0;
-        cnt += __popc(__ballot_sync(0xffffffffu, hit));
-    }
+    cluster_tiles(S, I, lane, T, oI, hI, [&](int e) { cnt += __popc(__ballot_sync(0xffffffffu, e >= 0)); });
     if (lane == 0) S.cl->count[I] = cnt;
 }
 
@@ -827,13 +858,11 @@ __global__ void k_lwrite(EngineDev E, int only) {
     const float hI[3] = {S.thalf[3 * I], S.thalf[3 * I + 1], S.thalf[3 * I + 2]};
     int* lst = S.cl->list;
     int out = S.cl->start[I];
-    for (int J0 = 0; J0 < S.Tp; J0 += 32) {
-        const int J = J0 + lane;
-        const int e = J < S.Tp ? list_entry(S, I, J, oI, hI, T) : -1;
+    cluster_tiles(S, I, lane, T, oI, hI, [&](int e) {
         const unsigned m = __ballot_sync(0xffffffffu, e >= 0);
         if (e >= 0) lst[out + __popc(m & ((1u << lane) - 1u))] = e;
         out += __popc(m);
-    }
+    });
 }
 
 // ---------------------------------------------------------------- launchers
