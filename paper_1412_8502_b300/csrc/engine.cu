@@ -131,7 +131,7 @@ Engine::~Engine() {
 
 void Engine::free_tables() {
     void* ptrs[] = {d_sys_, d_tile_sys_, d_item_sys_, d_hist_, d_binstart_, d_cursor_, d_blocksum_, d_any_, d_out_,
-                    d_clock_, d_seeds_, d_cond_runs_, d_tune_};
+                    d_clock_, d_seeds_, d_cond_runs_, d_tune_, d_f64part_, d_f64cnt_};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d_sys_ = nullptr;
@@ -141,6 +141,8 @@ void Engine::free_tables() {
     d_any_ = nullptr;
     d_cond_runs_ = nullptr;
     d_tune_ = nullptr;
+    d_f64part_ = nullptr;
+    d_f64cnt_ = nullptr;
     d_out_ = d_clock_ = nullptr;
     d_seeds_ = nullptr;
     table_bytes_ = 0;
@@ -407,6 +409,15 @@ int Engine::build_tables() {
     if ((rc = A(&d_any_, sizeof(int)))) return rc;
     if ((rc = A(&d_cond_runs_, sizeof(unsigned long long)))) return rc;
     if ((rc = A(&d_tune_, sizeof(ForceTune)))) return rc;
+    // FP64 mode: split the tiles' entries over blocks while tiles < SMs
+    int sms = 148, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int chunks = precision == MD_PREC_FP64 ? std::max(1, std::min(8, sms / std::max(tiles, 1))) : 1;
+    if (chunks > 1) {
+        if ((rc = A(&d_f64part_, sizeof(double) * 3 * (size_t)chunks * tiles * kTile))) return rc;
+        if ((rc = A(&d_f64cnt_, sizeof(int) * tiles))) return rc;
+    }
     if ((rc = A(&d_out_, sizeof(double) * 16))) return rc;
     if ((rc = A(&d_clock_, sizeof(double) * 8))) return rc;
     if ((rc = A(&d_seeds_, sizeof(unsigned long long) * std::max(n, 1)))) return rc;
@@ -430,6 +441,9 @@ int Engine::build_tables() {
     E.any_rebuild = d_any_;
     E.cond_runs = d_cond_runs_;
     E.tune = d_tune_;
+    E.f64chunks = chunks;
+    E.f64part = d_f64part_;
+    E.f64cnt = d_f64cnt_;
     long long ntot = 0;
     for (SysHost* h : sys) ntot += h->N;
     E.tune_variants = (precision != MD_PREC_FP64 && ntot >= kVariantMinN) ? 1 : 0;

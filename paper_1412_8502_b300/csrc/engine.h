@@ -133,6 +133,8 @@ private:
     cudaStream_t aux_stream_ = nullptr;     // captures the bodies of conditional nodes
     unsigned long long* d_cond_runs_ = nullptr;
     ForceTune* d_tune_ = nullptr;
+    double* d_f64part_ = nullptr;
+    int* d_f64cnt_ = nullptr;
     int build_step_graph(cudaGraph_t& graph, int kind, bool energy);
     std::map<std::string, std::pair<int64_t, double>> ktimes_;
     std::vector<std::string> korder_;

@@ -929,12 +929,16 @@ __global__ void __launch_bounds__(kForceWarps * 32) k_force_fix(EngineDev E, int
 constexpr int kFW = 16;
 
 template <bool kEnergy>
-__global__ void __launch_bounds__(kFW * 32) k_force_fp64(EngineDev E, int only, int out_alt) {
+__global__ void __launch_bounds__(kFW * 32) k_force_fp64(EngineDev E, int only, int out_alt, int chunks) {
     __shared__ double sb[kFW][3][kTile];
     __shared__ float4 sh[kFW][kTile], sl[kFW][kTile];
     __shared__ double red[kFW][3][kTile];
     __shared__ double ered[kFW][5];
-    const int g = blockIdx.x;
+    __shared__ int last;
+    // block -> (tile g, chunk ch): with few tiles, chunks of a tile's entries
+    // run in separate blocks (entries ch kFW + w, + chunks kFW, ...) and the
+    // last block of a tile adds the chunks' partial forces in chunk order
+    const int g = blockIdx.x % E.ntiles, ch = blockIdx.x / E.ntiles;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (g >= E.ntiles) return;
     const int s = E.tile_sys[g];
@@ -961,7 +965,7 @@ __global__ void __launch_bounds__(kFW * 32) k_force_fp64(EngineDev E, int only, 
     int nn = 0, nc = 0;
     const int* lst = S.list + (long long)I * S.T;
     const int e1 = S.lcount[I], nnear = S.lnear[I];
-    for (int e = w; e < e1; e += kFW) {
+    for (int e = ch * kFW + w; e < e1; e += chunks * kFW) {
         const int J = lst[list_pos(S, e, nnear)] & kJMask;
         const int q = tile_slot0(S, J) + lane;
         const int nq = tile_end(S, J) - tile_slot0(S, J);
@@ -1035,6 +1039,7 @@ __global__ void __launch_bounds__(kFW * 32) k_force_fp64(EngineDev E, int only, 
         }
     }
     __syncthreads();
+    double* F = S.f64[out_alt ? (st->cur ^ 1) : st->cur];
     if (w == 0) {
         double sx = 0.0, sy = 0.0, sz = 0.0;
         for (int k = 0; k < kFW; ++k) {
@@ -1042,21 +1047,54 @@ __global__ void __launch_bounds__(kFW * 32) k_force_fp64(EngineDev E, int only, 
             sy += red[k][1][lane];
             sz += red[k][2][lane];
         }
-        double* F = S.f64[out_alt ? (st->cur ^ 1) : st->cur];
-        if (valid) {
-            F[p] = sx;
-            F[N + p] = sy;
-            F[2 * N + p] = sz;
-            if (!isfinite(sx) || !isfinite(sy) || !isfinite(sz)) atomicOr(&st->error, 1);
+        if (chunks == 1) {
+            if (valid) {
+                F[p] = sx;
+                F[N + p] = sy;
+                F[2 * N + p] = sz;
+                if (!isfinite(sx) || !isfinite(sy) || !isfinite(sz)) atomicOr(&st->error, 1);
+            }
+        } else {
+            // this chunk's partial: slot g * 32 + lane of the chunk's plane
+            double* part = E.f64part + (long long)ch * 3 * E.ntiles * kTile;
+            const long long k0 = (long long)g * kTile + lane;
+            part[k0] = sx;
+            part[(long long)E.ntiles * kTile + k0] = sy;
+            part[2ll * E.ntiles * kTile + k0] = sz;
         }
         if (kEnergy && lane == 0) {
             double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
             for (int k = 0; k < kFW; ++k)
                 for (int c = 0; c < 5; ++c) t[c] += ered[k][c];
-            // ordered pairs: twice the pairs
+            // ordered pairs: twice the pairs; this chunk's entries
+            long long nent = 0;
+            for (int e = ch * kFW; e < e1; e += chunks * kFW) nent += min(kFW, e1 - e);
             add_energy(st, 0.5 * t[0], 0.5 * t[1], 0.5 * t[2], (long long)t[3], (long long)t[4],
-                       (long long)e1 * (kTile * kTile));
+                       nent * (kTile * kTile));
         }
+    }
+    if (chunks == 1) return;
+    // the last chunk of tile g to finish adds the partials in chunk order
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&E.f64cnt[g], 1) == chunks - 1) ? 1 : 0;
+    __syncthreads();
+    if (!last || w != 0) return;
+    __threadfence();
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    const long long k0 = (long long)g * kTile + lane, plane = (long long)E.ntiles * kTile;
+    for (int c = 0; c < chunks; ++c) {
+        const volatile double* part = E.f64part + (long long)c * 3 * plane;
+        sx += part[k0];
+        sy += part[plane + k0];
+        sz += part[2 * plane + k0];
+    }
+    if (lane == 0) E.f64cnt[g] = 0;
+    if (valid) {
+        F[p] = sx;
+        F[N + p] = sy;
+        F[2 * N + p] = sz;
+        if (!isfinite(sx) || !isfinite(sy) || !isfinite(sz)) atomicOr(&st->error, 1);
     }
 }
 
@@ -1121,8 +1159,9 @@ void launch_force(const EngineHost& H, cudaStream_t s, bool energy, int only, in
     const EngineDev& E = H.dev;
     launch_force_pre(H, s, energy, only);
     if (H.precision == 1) {
-        if (energy) k_force_fp64<true><<<E.ntiles, kFW * 32, 0, s>>>(E, only, out_alt);
-        else k_force_fp64<false><<<E.ntiles, kFW * 32, 0, s>>>(E, only, out_alt);
+        const int ch = E.f64chunks;
+        if (energy) k_force_fp64<true><<<E.ntiles * ch, kFW * 32, 0, s>>>(E, only, out_alt, ch);
+        else k_force_fp64<false><<<E.ntiles * ch, kFW * 32, 0, s>>>(E, only, out_alt, ch);
         H.count(1);
     } else {
         launch_force_variant(H, s, energy, only, H.fixed_var, false);

@@ -186,6 +186,12 @@ struct EngineDev {
     unsigned long long* cond_runs;   // step-graph rebuilds run through the conditional node
     ForceTune* tune;                 // force-pass code variant (automatic choice)
     int tune_variants;               // 1: steps select the variant (SWITCH node) and the tuner runs
+    // FP64 mode with fewer tiles than SMs: a tile's list entries run in
+    // f64chunks blocks whose partial forces meet in f64part ([chunk][3][tile
+    // slot]); f64cnt[tile] counts the finished chunks (the last one adds them)
+    int f64chunks;
+    double* f64part;
+    int* f64cnt;
 };
 
 // Engines below this many particles run one force-pass variant: the SWITCH
