@@ -205,6 +205,13 @@ MD_API int md_set_stream(md_system* s, void* stream);
  * in use, Eq. (3) is re-based at the current time so L stays continuous.
  * Synchronises the stream once at the end to report MD_ENUMERIC. */
 MD_API int md_step(md_system* s, int64_t n, double xi_dot);
+/* As md_step, without the synchronisation: the n steps are enqueued on the
+ * handle's stream and the call returns at once.  A non-finite force or a
+ * device error is reported by the next md_sync or md_step. */
+MD_API int md_step_async(md_system* s, int64_t n, double xi_dot);
+/* Wait for the handle's enqueued work; MD_ENUMERIC (or MD_ECUDA) if it
+ * failed. */
+MD_API int md_sync(md_system* s);
 
 /* Forces of the last force evaluation ([N][3] doubles, original order). */
 MD_API int md_forces(md_system* s, double* f_out);

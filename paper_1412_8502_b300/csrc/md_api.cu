@@ -133,6 +133,20 @@ int md_step(md_system* s, int64_t n, double xi_dot) {
     return s->eng->step(n, &xi);
 }
 
+int md_step_async(md_system* s, int64_t n, double xi_dot) {
+    GUARD(s);
+    if (!std::isfinite(xi_dot)) return fail(MD_EINVAL, "xi_dot must be finite");
+    if (!s->owner) return fail(MD_EINVAL, "step a batch member through md_batch_step");
+    if (n < 0) return fail(MD_EINVAL, "n must be >= 0");
+    std::vector<double> xi(1, xi_dot);
+    return s->eng->step_async(n, &xi, nullptr);
+}
+
+int md_sync(md_system* s) {
+    GUARD(s);
+    return s->eng->check_errors();
+}
+
 int md_forces(md_system* s, double* f_out) {
     GUARD(s);
     if (!f_out) return fail(MD_EINVAL, "f_out is null");

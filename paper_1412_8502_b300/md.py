@@ -88,6 +88,8 @@ _SIGS = {
     "md_set_params": (ctypes.c_int, [_P, ctypes.POINTER(md_params)]),
     "md_set_stream": (ctypes.c_int, [_P, _P]),
     "md_step": (ctypes.c_int, [_P, _I64, _D]),
+    "md_step_async": (ctypes.c_int, [_P, _I64, _D]),
+    "md_sync": (ctypes.c_int, [_P]),
     "md_forces": (ctypes.c_int, [_P, ctypes.POINTER(_D)]),
     "md_energy": (ctypes.c_int, [_P, ctypes.POINTER(md_energy_t)]),
     "md_step_energy": (ctypes.c_int, [_P, ctypes.POINTER(md_energy_t)]),
@@ -173,6 +175,14 @@ def md_destroy(h) -> None:
 
 def md_step(h, n: int, xi_dot: float = 0.0) -> None:
     _ck(LIB.md_step(h, int(n), float(xi_dot)), "md_step")
+
+
+def md_step_async(h, n: int, xi_dot: float = 0.0) -> None:
+    _ck(LIB.md_step_async(h, int(n), float(xi_dot)), "md_step_async")
+
+
+def md_sync(h) -> None:
+    _ck(LIB.md_sync(h), "md_sync")
 
 
 def md_forces(h, N: int) -> np.ndarray:
@@ -423,6 +433,12 @@ class System:
 
     def step(self, n, xi_dot=0.0):
         md_step(self.h, n, xi_dot)
+
+    def step_async(self, n, xi_dot=0.0):
+        md_step_async(self.h, n, xi_dot)
+
+    def sync(self):
+        md_sync(self.h)
 
     def forces(self):
         return md_forces(self.h, self.N)

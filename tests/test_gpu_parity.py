@@ -437,3 +437,24 @@ def test_force_code_tuner_reports_its_choice(md):
         s.close()
     with pytest.raises(md.MDError):
         load(md, x, t, L, 0, force_unroll=3)
+
+
+def test_step_async_matches_step(md):
+    """md_step_async enqueues the same steps as md_step (bitwise the same
+    state); md_sync reports completion."""
+    x, t, L = CONFIGS["liquid_2000"]()
+    outs = []
+    for asynchronous in (False, True):
+        s, _ = load(md, x, t, L, 0, energy_every=1)
+        for _ in range(6):
+            if asynchronous:
+                s.step_async(1, 7.5e-5)
+            else:
+                s.step(1, 7.5e-5)
+        if asynchronous:
+            s.sync()
+        outs.append((s.state(f=True), s.step_energy()))
+        s.close()
+    for k in ("x", "v", "f"):
+        assert np.array_equal(outs[0][0][k], outs[1][0][k])
+    assert outs[0][1] == outs[1][1]
