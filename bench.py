@@ -34,7 +34,7 @@ sys.path.insert(0, str(ROOT))
 
 MEASURED = ROOT / "MEASURED_PEAKS.json"
 TRAFFIC = ROOT / "profiles" / "force_split_409600_traffic.json"
-PIPES = ROOT / "profiles" / "force_split_204800_pipes.json"
+PIPES = ROOT / "profiles" / "force_split_307200_pipes.json"
 FORCE_SRC = ROOT / "paper_1412_8502_b300" / "csrc" / "k_force.cu"
 
 WORKLOADS = {
@@ -42,8 +42,11 @@ WORKLOADS = {
                      desc="409,600 nucleons, Yp=0.40, T=0.5 MeV, rho 0.080 fm^-3 expanding at 7.5e-5 c/fm "
                           "(to 0.00125 over 20,000 steps), split FP32/FP64, 1 fm skin, rebuild <= 10 steps"),
     "md204800": dict(N=204800, Yp=0.40, T=0.5, rho=0.080, seed=6, xi=7.5e-5,
-                     desc="204,800 nucleons, Yp=0.40, T=0.5 MeV, rho 0.080 fm^-3 expanding at 7.5e-5 c/fm "
-                          "(profiling size of the 409,600 workload)"),
+                     desc="204,800 nucleons, Yp=0.40, T=0.5 MeV, rho 0.080 fm^-3 expanding at 7.5e-5 c/fm"),
+    "md307200": dict(N=307200, Yp=0.40, T=0.5, rho=0.080, seed=7, xi=7.5e-5,
+                     desc="307,200 nucleons, Yp=0.40, T=0.5 MeV, rho 0.080 fm^-3 expanding at 7.5e-5 c/fm "
+                          "(profiling size of the 409,600 workload: the same force-kernel path, no per-pair "
+                          "wrap)"),
     "md51200": dict(N=51200, Yp=0.30, T=1.0, rho=0.080, seed=2, xi=7.5e-5,
                     desc="51,200 nucleons, Yp=0.30, T=1.0 MeV, rho 0.080 fm^-3 expanding at 7.5e-5 c/fm"),
     "md2000": dict(N=2000, Yp=0.30, T=1.0, rho=0.080, seed=1, xi=0.0,
