@@ -298,7 +298,8 @@ __global__ void k_scatter(EngineDev E) {
 
 // Destination of slot q's particle: its bin start plus the number of
 // particles of the same bin with a smaller previous slot index (stable,
-// deterministic).  Moves x, v, id (and the cached force if keep_forces).
+// deterministic).  Moves x, v, id (the forces are evaluated after the
+// rebuild, or placed by id when a state is loaded with its forces).
 __global__ void k_move(EngineDev E) {
     if (!*E.any_rebuild) return;
     const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
@@ -328,13 +329,6 @@ __global__ void k_move(EngineDev E) {
         S.v[cn][a * N + d] = S.v[c][a * N + j];
     }
     S.id[cn][d] = S.id[c][j];
-    if (st->keep_forces) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            S.f32[cn][a * N + d] = S.f32[c][a * N + j];
-            S.f64[cn][a * N + d] = S.f64[c][a * N + j];
-        }
-    }
 }
 
 // ---------------------------------------------------------------- tiles

@@ -56,7 +56,7 @@ struct SysState {
     int cur_next;            // buffer the running rebuild writes
     int rebuild;             // this step rebuilds (set by the decision kernel)
     int force_rebuild;       // rebuild at the next decision regardless
-    int keep_forces;         // permute cached forces during the rebuild
+    int pad2;
     int need_wrap;           // per-pair minimum image needed in FP32
     int have_energy;         // energies recorded by a step
     int error;               // bit 0: non-finite force; bit 2: Verlet list pool exhausted
