@@ -92,7 +92,7 @@ def cfg_relaxed(N, Yp, rho, seed, iters=40):
     return x, t, L
 
 
-CONFIGS = {
+PARITY_CASES = {
     "liquid_2000": lambda: cfg_liquid(2000, 0.30, 0.080, 3),
     "liquid_8000_yp04": lambda: cfg_liquid(8000, 0.40, 0.080, 4),
     "drops_3000_dilute": lambda: cfg_drops(3000, 0.30, 0.005, 5),
@@ -140,10 +140,10 @@ def test_relax_fp64_matches_oracle(md):
 
 
 # --------------------------------------------------------------- forces
-@pytest.mark.parametrize("name", list(CONFIGS))
+@pytest.mark.parametrize("name", list(PARITY_CASES))
 @pytest.mark.parametrize("precision", [0, 1])
 def test_forces_and_energy_vs_oracle(md, name, precision):
-    x, t, L = CONFIGS[name]()
+    x, t, L = PARITY_CASES[name]()
     s, v = load(md, x, t, L, precision)
     F = s.forces()
     Fo, (en, ec, w) = oracle.forces(x, t, L, oparams(s))
@@ -262,7 +262,7 @@ def test_plain_and_conditional_step_graphs_agree_bitwise(md):
     """The rebuild kernels in conditional graph nodes (default) or as plain
     nodes that return at once without a rebuild: the same kernels run on
     the same data, so trajectories (through several rebuilds) are identical."""
-    x, t, L = CONFIGS["liquid_2000"]()
+    x, t, L = PARITY_CASES["liquid_2000"]()
     out = []
     for cond in (1, 0):
         s, v = load(md, x, t, L, 0, cond_graph=cond)
@@ -303,7 +303,7 @@ def _check_clusters(s, x, t, L):
 
 @pytest.mark.parametrize("name", ["drops_3000_dilute", "liquid_2000", "liquid_4096_yp005", "drops_20000_L464"])
 def test_clusters_bit_exact(md, name):
-    x, t, L = CONFIGS[name]()
+    x, t, L = PARITY_CASES[name]()
     s, _ = load(md, x, t, L, 0)
     _check_clusters(s, x, t, L)
 
@@ -361,7 +361,7 @@ def test_state_round_trip_with_forces(md, precision):
     restores them bit for bit (no fresh force pass), and the restored system
     continues the trajectory of the original one (differences only from the
     FP32 summation order of the re-sorted tiles)."""
-    x, t, L = CONFIGS["liquid_2000"]()
+    x, t, L = PARITY_CASES["liquid_2000"]()
     s, _ = load(md, x, t, L, precision)
     xi = 7.5e-5
     s.step(7, xi)
@@ -395,7 +395,7 @@ def test_force_code_variants_agree_bitwise(md, name):
     the same arithmetic in the same order: identical forces, energies and
     pair counts, before and after steps (force_unroll = 0: the device tuner's
     choice)."""
-    x, t, L = CONFIGS[name]()
+    x, t, L = PARITY_CASES[name]()
     outs = []
     for fu in (4, 2, 1, 0):
         s, _ = load(md, x, t, L, 0, force_unroll=fu, energy_every=1)
@@ -429,7 +429,7 @@ def test_force_code_tuner_reports_its_choice(md):
         s.close()
     for k in ("x", "v", "f"):
         assert np.array_equal(outs[0][k], outs[1][k])
-    x, t, L = CONFIGS["liquid_2000"]()
+    x, t, L = PARITY_CASES["liquid_2000"]()
     for fu in (0, 1, 2, 4):
         s, _ = load(md, x, t, L, 0, force_unroll=fu)
         s.step(520, 0.0)
@@ -442,7 +442,7 @@ def test_force_code_tuner_reports_its_choice(md):
 def test_step_async_matches_step(md):
     """md_step_async enqueues the same steps as md_step (bitwise the same
     state); md_sync reports completion."""
-    x, t, L = CONFIGS["liquid_2000"]()
+    x, t, L = PARITY_CASES["liquid_2000"]()
     outs = []
     for asynchronous in (False, True):
         s, _ = load(md, x, t, L, 0, energy_every=1)
