@@ -354,6 +354,39 @@ def test_relax_lowers_energy():
     assert x1.min() >= 0 and x1.max() < L
 
 
+@pytest.mark.parametrize("r,clamped", [(1.6, False), (1.3, True)])
+def test_relax_one_iteration_by_hand(r, clamped):
+    """One steepest-descent iteration on two neutrons, written out from Table I.
+
+    Two neutrons (nn: s = b + c) at separation r along the diagonal (1, 1, 0)/sqrt(2).
+    The force on neutron 0 is F = r_vec ((2a/Lambda) g^2 + (s/Lambda) g),
+    g = exp(-r^2 / 2 Lambda) (Eq. 1), so each moves by gamma |F| along the
+    separation, outward, unless gamma |F| > dmax, when the displacement VECTOR is
+    scaled to length dmax.  At r = 1.6 fm gamma |F| = 0.0708 fm (no clamp); at
+    r = 1.3 fm gamma |F| = 0.1163 fm > 0.1 while each component is 0.0822 < 0.1,
+    so a per-component clamp would leave it unchanged and fails here, as would a
+    wrong gamma, a wrong sign or a dropped Gaussian."""
+    a, b, c, Lam = T1["a_MeV"], T1["b_MeV"], T1["c_MeV"], T1["Lambda_fm2"]
+    gamma, dmax = 0.002, 0.1
+    s = b + c
+    g = math.exp(-r * r / (2.0 * Lam))
+    fmag = r * ((2.0 * a / Lam) * g * g + (s / Lam) * g)        # |F|, repulsive here
+    step = gamma * fmag
+    assert (step > dmax) == clamped
+    if clamped:
+        assert step / math.sqrt(2.0) < dmax                     # components below the clamp
+        step = dmax
+    u = np.array([1.0, 1.0, 0.0]) / math.sqrt(2.0)
+    L = 100.0
+    c0 = np.array([40.0, 40.0, 40.0])
+    x = np.array([c0, c0 + r * u])
+    t = np.zeros(2, dtype=np.int8)                               # two neutrons
+    p = P(r_C=20.0)
+    x1 = oracle.relax(x, t, L, p, 1, gamma=gamma, dmax=dmax)
+    expect = np.array([c0 - step * u, c0 + (r + step) * u])
+    assert np.abs(x1 - expect).max() < 1e-12
+
+
 # ---------------------------------------------------------------- clusters
 
 def test_cluster_chain_threshold():
