@@ -109,6 +109,13 @@ typedef struct {
                                 passes of each, in engines of at least 131,072
                                 nucleons (smaller ones run the long variant).
                                 Results are bitwise the same. */
+    int64_t uf_iter_limit;   /* bound on the iterations of every union-find loop
+                                of the cluster analyses (a root walk, or the
+                                retries of a union), 1 .. 2^31-1 (default 2^26,
+                                far above the longest path any input can have).
+                                A loop that reaches it gives up and the call
+                                returns MD_ETIMEOUT: its labels are then not
+                                valid.  No device wait is involved. */
 } md_params;
 
 typedef struct {
@@ -285,6 +292,13 @@ MD_API double md_lambda_thomas_fermi(double n_e);
 /* Thread-local message describing the last error of this thread. */
 MD_API const char* md_last_error(void);
 
+/* Test hook for allocation-failure handling: after md_debug_fail_alloc(n),
+ * the n-th device allocation the library makes (1 = the next one), in any
+ * thread and through any entry point, fails as if the device were out of
+ * memory; the call that made it returns MD_ENOMEM and releases what it had
+ * allocated.  n = 0 disarms the hook.  Returns MD_EINVAL for n < 0. */
+MD_API int md_debug_fail_alloc(int64_t nth);
+
 /* Cluster analysis (same rules and results as md_clusters) on positions the
  * caller already holds in device memory, for callers that cannot allocate
  * device memory: code running inside another application's memory pool
@@ -302,10 +316,15 @@ MD_API const char* md_last_error(void);
  *             with A >= 12, sum of their A, sum of their Z
  *   stream    cudaStream_t (NULL: legacy default stream); the call is
  *             asynchronous on it.
- * N above 32768 gives MD_EINVAL (fixed scratch limit).  The first call on
- * each device looks up the scratch array's device address with that device
- * current, so make it before any stream capture.  Calls share the scratch
- * array: two calls whose work overlaps on the GPU race. */
+ * N above 32768 gives MD_EINVAL (fixed scratch limit).  A call whose stream
+ * is not capturing looks the scratch array's device address up in the
+ * context current at the call (so a device reset or another context on the
+ * same device is picked up); a call made under stream capture reuses the
+ * address the last uncaptured call on that device found, so make one
+ * uncaptured call, in the same context, before capturing (a first call under
+ * capture gives MD_EINVAL).  The union-find loops are bounded; if one gives
+ * up, d_counts[0] is set to -1 and the labels are not valid.  Calls share the
+ * scratch array: two calls whose work overlaps on the GPU race. */
 MD_API int md_clusters_noalloc(const double* d_x, int64_t N, int64_t Np, double L, double r_pp, double r_np,
                                int32_t* d_labels, int64_t* d_hist_A, int64_t* d_hist_Z, int64_t* d_counts,
                                void* stream);

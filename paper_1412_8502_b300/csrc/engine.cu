@@ -2,6 +2,7 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -48,6 +49,18 @@ static PairF pair_consts(const SysConst& c) {
 namespace {
 thread_local std::string g_err;
 
+// Allocation-failure injection (md_debug_fail_alloc): when armed with n, the
+// n-th device allocation made from then on, in any thread, fails as if the
+// device were out of memory.
+std::atomic<long long> g_fail_countdown{0};
+
+bool injected_alloc_failure() {
+    long long c = g_fail_countdown.load();
+    while (c > 0)
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+    return false;
+}
+
 void rec_cb(void* o, const char* name, cudaStream_t s) { static_cast<Engine*>(o)->on_rec(name, s); }
 void count_cb(void* o, int n) { static_cast<Engine*>(o)->on_count(n); }
 
@@ -61,6 +74,8 @@ void count_cb(void* o, int n) { static_cast<Engine*>(o)->on_count(n); }
 template <typename T>
 int dalloc(SysHost& h, T** p, size_t count) {
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (injected_alloc_failure())
+        return fail(MD_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected)");
     cudaError_t e = cudaMalloc((void**)p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -99,6 +114,8 @@ double lambda_thomas_fermi(double n_e) {
     const double k_F = std::cbrt(3.0 * pi * pi * n_e);
     return std::sqrt(pi) / (2.0 * std::sqrt(fine)) / std::sqrt(k_F * std::sqrt(k_F * k_F + m_e * m_e));
 }
+
+void arm_alloc_failure(long long nth) { g_fail_countdown.store(nth); }
 
 void set_error(const std::string& msg) { g_err = msg; }
 int fail(int code, const std::string& msg) {
@@ -232,6 +249,8 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     if (p.list_kind == 1 && p.precision != MD_PREC_SPLIT)
         return fail(MD_EINVAL, "Verlet lists (list_kind 1) need split precision");
     if (p.list_kind == 1 && !(p.verlet_pool > 0.0)) return fail(MD_EINVAL, "verlet_pool must be > 0");
+    if (p.uf_iter_limit < 1 || p.uf_iter_limit > 0x7fffffff)
+        return fail(MD_EINVAL, "uf_iter_limit must be in [1, 2^31 - 1]");
     const double L0 = std::cbrt((double)N / rho);
     double rC = p.r_C > 0.0 ? p.r_C : std::min(40.0, 0.5 * L0);
     // (relative slack of 1e-12 absorbs the rounding of cbrt)
@@ -336,6 +355,7 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     c.energy_every = (int)p.energy_every;
     c.list_kind = p.list_kind;
     c.force_unroll = p.force_unroll;
+    c.uf_limit = (int)p.uf_iter_limit;
     c.pf = pair_consts(c);
 
     SysState st{};
@@ -389,6 +409,7 @@ int Engine::build_tables() {
     }
     const int nscan = (int)((bins + 8191) / 8192);
     auto A = [&](auto** p, size_t bytes) -> int {
+        if (injected_alloc_failure()) return fail(MD_ENOMEM, "engine table allocation failed (injected)");
         cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(bytes, 16));
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -883,6 +904,9 @@ int Engine::clusters(int idx, int32_t* labels, int64_t* hA, int64_t* hZ, md_clus
     if (hZ) CK(cudaMemcpyAsync(hZ, h.hcl.hist_Z, sizeof(int64_t) * (h.Np + 1), cudaMemcpyDeviceToHost, stream_));
     CK(cudaMemcpyAsync(st, h.hcl.stats, sizeof(st), cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));
+    if (st[7])
+        return fail(MD_ETIMEOUT, "a union-find loop reached uf_iter_limit (" + std::to_string(h.prm.uf_iter_limit) +
+                                     " iterations); the cluster labels are not valid");
     if (out) {
         out->n_clusters = st[0];
         out->n_free = st[1];
@@ -908,6 +932,9 @@ int Engine::clusters_mste(int idx, int32_t* labels, int64_t* hA, int64_t* hZ, md
     if (hZ) CK(cudaMemcpyAsync(hZ, h.hcl.hist_Z, sizeof(int64_t) * (h.Np + 1), cudaMemcpyDeviceToHost, stream_));
     CK(cudaMemcpyAsync(st, h.hcl.stats, sizeof(st), cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));
+    if (st[7])
+        return fail(MD_ETIMEOUT, "a union-find loop reached uf_iter_limit (" + std::to_string(h.prm.uf_iter_limit) +
+                                     " iterations); the cluster labels are not valid");
     if (out) {
         out->n_clusters = st[0];
         out->n_free = st[1];
@@ -999,6 +1026,8 @@ int Engine::set_params(int idx, const md_params& p) {
     if (p.list_kind == 1 && p.precision != MD_PREC_SPLIT)
         return fail(MD_EINVAL, "Verlet lists (list_kind 1) need split precision");
     if (p.list_kind == 1 && !(p.verlet_pool > 0.0)) return fail(MD_EINVAL, "verlet_pool must be > 0");
+    if (p.uf_iter_limit < 1 || p.uf_iter_limit > 0x7fffffff)
+        return fail(MD_EINVAL, "uf_iter_limit must be in [1, 2^31 - 1]");
     const int nbits = p.sort_bits ? p.sort_bits : auto_bits(h.N);
     if (p.list_kind == 1) {
         // (re)allocate the list pool when it is missing or too small
@@ -1061,6 +1090,7 @@ int Engine::set_params(int idx, const md_params& p) {
     c.energy_every = (int)p.energy_every;
     c.list_kind = p.list_kind;
     c.force_unroll = p.force_unroll;
+    c.uf_limit = (int)p.uf_iter_limit;
     c.pf = pair_consts(c);
     if (pp_changed || lists_changed) {
         cudaStreamSynchronize(stream_);

@@ -143,6 +143,9 @@ private:
 // Eq. (2) screening length (fm) at electron density n_e (fm^-3).
 double lambda_thomas_fermi(double n_e);
 
+// Test hook: the nth device allocation from now on fails (0 disarms).
+void arm_alloc_failure(long long nth);
+
 // Thread-local error message helpers.
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);

@@ -35,10 +35,20 @@ __device__ __forceinline__ double d2_exact(double xi, double yi, double zi, doub
 }
 
 // Roots only ever hook onto smaller roots and path halving only shortens
-// paths, so the chain is acyclic; the bound is a safety net.
-__device__ inline int uf_find(int* parent, int a) {
+// paths, so every walk ends.  Each loop is bounded all the same by the
+// host-set limit (md_params.uf_iter_limit); a loop that reaches it gives up
+// and records the fact in *gave_up (ClusterBufs.stats[7], cleared by the
+// init kernels), which the host reports as MD_ETIMEOUT.  A walk that gives
+// up returns the slot it reached, a valid index, so nothing downstream
+// reads out of bounds; the counting kernels skip their work once the flag
+// is set.
+__device__ inline int uf_find(int* parent, int a, int limit, long long* gave_up) {
     int p = ((volatile int*)parent)[a];
-    for (int it = 0; p != a && it < (1 << 26); ++it) {
+    for (int it = 0; p != a; ++it) {
+        if (it >= limit) {
+            *(volatile long long*)gave_up = 1;
+            break;
+        }
         const int gp = ((volatile int*)parent)[p];
         if (gp != p) atomicCAS(&parent[a], p, gp);   // path halving
         a = p;
@@ -47,10 +57,10 @@ __device__ inline int uf_find(int* parent, int a) {
     return a;
 }
 
-__device__ inline void uf_union(int* parent, int a, int b) {
-    for (int it = 0; it < (1 << 20); ++it) {
-        a = uf_find(parent, a);
-        b = uf_find(parent, b);
+__device__ inline void uf_union(int* parent, int a, int b, int limit, long long* gave_up) {
+    for (int it = 0; it < limit; ++it) {
+        a = uf_find(parent, a, limit, gave_up);
+        b = uf_find(parent, b, limit, gave_up);
         if (a == b) return;
         if (a < b) {
             const int t = a;
@@ -59,6 +69,7 @@ __device__ inline void uf_union(int* parent, int a, int b) {
         }
         if (atomicCAS(&parent[a], a, b) == a) return;
     }
+    *(volatile long long*)gave_up = 1;
 }
 
 constexpr int kCW = 4;   // warps per block
@@ -172,7 +183,7 @@ __global__ void k_cl_link(EngineDev E, int only) {
             bool link = d2 < lo2;
             if (!link)
                 link = d2_exact(x[p], x[N + p], x[2 * N + p], x[qq], x[N + qq], x[2 * N + qq], L, hL) < r2c;
-            if (link) uf_union(B.parent, p, qq);
+            if (link) uf_union(B.parent, p, qq, S.uf_limit, &B.stats[7]);
         }
     }
 }
@@ -185,7 +196,7 @@ __global__ void k_cl_minid(EngineDev E, int only) {
     const ClusterBufs& B = *S.cl;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = q < S.Np;
-    const int r = ok ? uf_find(B.parent, q) : -1 - (int)(threadIdx.x & 31);
+    const int r = ok ? uf_find(B.parent, q, S.uf_limit, &B.stats[7]) : -1 - (int)(threadIdx.x & 31);
     int id = ok ? S.id[S.st->cur][q] : 0x7fffffff;
     const unsigned same = __match_any_sync(0xffffffffu, r);
     const int lane = threadIdx.x & 31;
@@ -208,7 +219,7 @@ __global__ void k_cl_assign(EngineDev E, int only) {
     const int p = tile_slot0(S, I) + lane;
     const bool valid = p < tile_end(S, I);
     if (I < S.Tp) {
-        if (valid) B.label[p] = B.minid[uf_find(B.parent, p)];
+        if (valid) B.label[p] = B.minid[uf_find(B.parent, p, S.uf_limit, &B.stats[7])];
         return;
     }
     const Frame F = frame_of(st);
@@ -244,7 +255,7 @@ __global__ void k_cl_assign(EngineDev E, int only) {
             }
         }
     }
-    if (valid) B.label[p] = best_slot < 0 ? -1 : B.minid[uf_find(B.parent, best_slot)];
+    if (valid) B.label[p] = best_slot < 0 ? -1 : B.minid[uf_find(B.parent, best_slot, S.uf_limit, &B.stats[7])];
 }
 
 // Per-cluster counts (labels are original proton indices < Np).  Lanes of a
@@ -252,6 +263,7 @@ __global__ void k_cl_assign(EngineDev E, int only) {
 __global__ void k_cl_count(EngineDev E, int only) {
     const SysConst& S = E.sys[only];
     const ClusterBufs& B = *S.cl;
+    if (B.stats[7]) return;      // a union-find loop gave up: labels are not valid
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool ok = p < S.N;
@@ -273,7 +285,7 @@ __global__ void k_cl_hist(EngineDev E, int only, int32_t* labels_out) {
     const SysConst& S = E.sys[only];
     const ClusterBufs& B = *S.cl;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= S.N) return;
+    if (p >= S.N || B.stats[7]) return;   // (union-find gave up: labels are not valid)
     const int i = S.id[S.st->cur][p];
     const int lab = B.label[p];
     if (labels_out) labels_out[i] = lab;
@@ -425,7 +437,7 @@ __global__ void k_ms_link(EngineDev E, int only, int prec) {
             else if (e > band) bound = false;
             else if (e < -band && r2 < near2) bound = true;
             else bound = ms_bound_exact(S, x, v, p, q, L, hL);
-            if (bound) uf_union(B.parent, p, q);
+            if (bound) uf_union(B.parent, p, q, S.uf_limit, &B.stats[7]);
         }
     }
 }
@@ -436,7 +448,7 @@ __global__ void k_ms_root(EngineDev E, int only) {
     const ClusterBufs& B = *S.cl;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= S.N) return;
-    const int r = uf_find(B.parent, q);
+    const int r = uf_find(B.parent, q, S.uf_limit, &B.stats[7]);
     atomicMin(&B.minid[r], S.id[S.st->cur][q]);
     atomicAdd(&B.ac[r], 1);
 }
@@ -448,7 +460,7 @@ __global__ void k_ms_label(EngineDev E, int only) {
     const ClusterBufs& B = *S.cl;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= S.N) return;
-    const int r = uf_find(B.parent, q);
+    const int r = uf_find(B.parent, q, S.uf_limit, &B.stats[7]);
     B.label[q] = (q >= S.Np && B.ac[r] == 1) ? -1 : B.minid[r];
 }
 
@@ -467,7 +479,7 @@ __global__ void k_ms_hist(EngineDev E, int only, int32_t* labels_out) {
     const SysConst& S = E.sys[only];
     const ClusterBufs& B = *S.cl;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= S.N) return;
+    if (p >= S.N || B.stats[7]) return;   // (union-find gave up: labels are not valid)
     const int i = S.id[S.st->cur][p];
     const int lab = B.label[p];
     if (labels_out) labels_out[i] = lab;

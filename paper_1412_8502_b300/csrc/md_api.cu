@@ -70,11 +70,18 @@ void md_params_default(md_params* p) {
     p->verlet_pool = 2.0;
     p->cond_graph = 1;
     p->force_unroll = 0;
+    p->uf_iter_limit = 1ll << 26;
 }
 
 double md_lambda_thomas_fermi(double n_e) { return pasta::lambda_thomas_fermi(n_e); }
 
 const char* md_last_error(void) { return pasta::last_error_cstr(); }
+
+int md_debug_fail_alloc(int64_t nth) {
+    if (nth < 0) return fail(MD_EINVAL, "nth must be >= 0");
+    pasta::arm_alloc_failure((long long)nth);
+    return MD_OK;
+}
 
 int md_create_ex(int64_t N, double Yp, double rho, double T, uint64_t seed, const md_params* p, md_system** out) {
     if (!out) return fail(MD_EINVAL, "out is null");

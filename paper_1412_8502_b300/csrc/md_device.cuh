@@ -106,6 +106,7 @@ struct SysConst {
     int affine;              // scale positions with the box (option, not the paper)
     int list_kind;           // 0 half tile-pair lists, 1 per-particle Verlet lists
     int force_unroll;        // split force-pass code variant: 0 automatic, 4 long, 2 compact, 1 minimal
+    int uf_limit;            // iterations of a union-find loop before it gives up (cluster analyses)
     PairF pf;
     // state arrays (index [cur] is current)
     double* x[2];

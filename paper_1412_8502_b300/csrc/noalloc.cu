@@ -14,10 +14,16 @@
 // Limits and rules of use:
 //  - at most kMaxN = 32768 nucleons; larger inputs are rejected with
 //    MD_EINVAL before anything is launched;
-//  - host code cannot use the array's symbol as a device address: the first
-//    call on each device looks the address up with cudaGetSymbolAddress
-//    while that device is current, so make that first call before any
-//    stream capture begins;
+//  - host code cannot use the array's symbol as a device address: each call
+//    that is not being captured into a CUDA graph looks the address up with
+//    cudaGetSymbolAddress in the context current at the call (a cached
+//    address could belong to a context that was reset or to another context
+//    on the same device); a call made while its stream is capturing uses the
+//    address that the last uncaptured call on that device found, so make an
+//    uncaptured call first, in the same context, before capturing one;
+//  - the union-find loops are bounded (kNaLimit iterations, far above any
+//    path an input within the size limit can produce); a loop that reaches
+//    the bound sets d_counts[0] = -1 and the labels are then not valid;
 //  - every call on a device shares the one array, and each call clears the
 //    parts it needs first; calls whose work overlaps on the GPU (different
 //    streams, or several host threads) race and must be serialised by the
@@ -35,13 +41,17 @@ namespace {
 
 constexpr int kMaxN = 32768;
 constexpr int kNaWarps = 4;
+constexpr int kNaLimit = 1 << 26;   // iterations of a union-find loop before it gives up
 
-// parent, minid, zc, ac: kMaxN ints each; then 8 counters (long long).
+// Four int arrays of kMaxN entries (union-find parents, smallest index per
+// root, protons and nucleons per cluster label: 512 KB) and the flag of a
+// union-find loop that gave up.
 struct NoAllocScratch {
     int parent[kMaxN];
     int minid[kMaxN];
     int zc[kMaxN];
     int ac[kMaxN];
+    int gave_up;
 };
 static __device__ __align__(256) NoAllocScratch g_na_scratch;
 
@@ -63,9 +73,15 @@ __device__ __forceinline__ double na_d2(const double* a, const double* b, double
     return s;
 }
 
-__device__ inline int na_find(int* parent, int a) {
+// Bounded union-find: a loop that reaches kNaLimit records it in *gave_up
+// (a walk that gives up returns the valid slot it reached).
+__device__ inline int na_find(int* parent, int a, int* gave_up) {
     int p = ((volatile int*)parent)[a];
-    for (int it = 0; p != a && it < (1 << 26); ++it) {
+    for (int it = 0; p != a; ++it) {
+        if (it >= kNaLimit) {
+            *(volatile int*)gave_up = 1;
+            break;
+        }
         const int gp = ((volatile int*)parent)[p];
         if (gp != p) atomicCAS(&parent[a], p, gp);
         a = p;
@@ -74,10 +90,10 @@ __device__ inline int na_find(int* parent, int a) {
     return a;
 }
 
-__device__ inline void na_union(int* parent, int a, int b) {
-    for (int it = 0; it < (1 << 20); ++it) {
-        a = na_find(parent, a);
-        b = na_find(parent, b);
+__device__ inline void na_union(int* parent, int a, int b, int* gave_up) {
+    for (int it = 0; it < kNaLimit; ++it) {
+        a = na_find(parent, a, gave_up);
+        b = na_find(parent, b, gave_up);
         if (a == b) return;
         if (a < b) {
             const int t = a;
@@ -86,6 +102,7 @@ __device__ inline void na_union(int* parent, int a, int b) {
         }
         if (atomicCAS(&parent[a], a, b) == a) return;
     }
+    *(volatile int*)gave_up = 1;
 }
 
 __global__ void k_na_init(NoAllocScratch* W, int N, int Np, long long* hA, long long* hZ, long long* counts) {
@@ -99,6 +116,7 @@ __global__ void k_na_init(NoAllocScratch* W, int N, int Np, long long* hA, long 
     if (i <= N) hA[i] = 0;
     if (i <= Np) hZ[i] = 0;
     if (i < 5) counts[i] = 0;
+    if (i == 0) W->gave_up = 0;
 }
 
 // Warp per 32-proton tile I, all tiles J >= I: link pairs closer than r_pp.
@@ -124,7 +142,7 @@ __global__ void k_na_link(NoAllocScratch* W, const double* x, int Np, double L, 
         for (int k = 0; k < nq; ++k) {
             const int qq = J * kTile + k;
             if (qq <= p) continue;
-            if (na_d2(xi, sb[w][k], L, hL) < r2c) na_union(W->parent, p, qq);
+            if (na_d2(xi, sb[w][k], L, hL) < r2c) na_union(W->parent, p, qq, &W->gave_up);
         }
     }
 }
@@ -132,7 +150,7 @@ __global__ void k_na_link(NoAllocScratch* W, const double* x, int Np, double L, 
 __global__ void k_na_minid(NoAllocScratch* W, int Np) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= Np) return;
-    atomicMin(&W->minid[na_find(W->parent, q)], q);
+    atomicMin(&W->minid[na_find(W->parent, q, &W->gave_up)], q);
 }
 
 // Labels of protons; nearest proton closer than r_np for each neutron
@@ -146,7 +164,7 @@ __global__ void k_na_assign(NoAllocScratch* W, const double* x, int N, int Np, d
     if (I * kTile >= N) return;
     const bool valid = p < N;
     if (p < Np) {
-        labels[p] = W->minid[na_find(W->parent, p)];
+        labels[p] = W->minid[na_find(W->parent, p, &W->gave_up)];
     }
     const bool neutron = valid && p >= Np;
     if (!__any_sync(0xffffffffu, neutron)) return;
@@ -172,12 +190,12 @@ __global__ void k_na_assign(NoAllocScratch* W, const double* x, int N, int Np, d
             }
         }
     }
-    if (neutron) labels[p] = best < 0 ? -1 : W->minid[na_find(W->parent, best)];
+    if (neutron) labels[p] = best < 0 ? -1 : W->minid[na_find(W->parent, best, &W->gave_up)];
 }
 
 __global__ void k_na_count(NoAllocScratch* W, const int32_t* labels, int N, int Np, long long* counts) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= N) return;
+    if (p >= N || W->gave_up) return;      // (labels are not valid then)
     const int lab = labels[p];
     if (lab < 0) {
         atomicAdd((unsigned long long*)&counts[1], 1ull);
@@ -190,7 +208,7 @@ __global__ void k_na_count(NoAllocScratch* W, const int32_t* labels, int N, int 
 __global__ void k_na_hist(NoAllocScratch* W, const int32_t* labels, int Np, long long* hA, long long* hZ,
                           long long* counts) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Np || labels[i] != i) return;
+    if (i >= Np || W->gave_up || labels[i] != i) return;
     const int A = W->ac[i], Z = W->zc[i];
     atomicAdd((unsigned long long*)&hA[A], 1ull);
     atomicAdd((unsigned long long*)&hZ[Z], 1ull);
@@ -202,20 +220,33 @@ __global__ void k_na_hist(NoAllocScratch* W, const int32_t* labels, int Np, long
     }
 }
 
-// Device address of the scratch array for the current device (looked up
-// once per device, with that device current).
-int scratch_for_current_device(NoAllocScratch** out) {
+// A union-find loop that gave up marks the result as not valid.
+__global__ void k_na_status(const NoAllocScratch* W, long long* counts) {
+    if (W->gave_up) counts[0] = -1;
+}
+
+// Device address of the scratch array in the current context.  A call that
+// is not being captured looks it up (cudaGetSymbolAddress: no allocation)
+// and remembers it for the device; a call under stream capture takes the
+// remembered address, so that no lookup (which may load the module) runs
+// inside a capture.
+int scratch_address(cudaStream_t s, NoAllocScratch** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(MD_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= 64) return fail(MD_ENODEV, "device index out of range");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return fail(MD_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_na_scratch);
         if (e != cudaSuccess)
             return fail(MD_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_na_ptr[dev] = static_cast<NoAllocScratch*>(ptr);
+    } else if (!g_na_ptr[dev]) {
+        return fail(MD_EINVAL, "md_clusters_noalloc: the first call on a device must not be captured");
     }
     *out = g_na_ptr[dev];
     return MD_OK;
@@ -235,10 +266,10 @@ extern "C" int md_clusters_noalloc(const double* d_x, int64_t N, int64_t Np, dou
         return fail(MD_EINVAL, "md_clusters_noalloc: N = " + std::to_string(N) + " exceeds the fixed scratch limit of " +
                                    std::to_string(kMaxN) + " nucleons");
     if (!(L > 0.0) || !(r_pp > 0.0) || !(r_np > 0.0)) return fail(MD_EINVAL, "md_clusters_noalloc: L, r_pp, r_np > 0");
-    NoAllocScratch* W = nullptr;
-    int rc = scratch_for_current_device(&W);
-    if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    NoAllocScratch* W = nullptr;
+    int rc = scratch_address(s, &W);
+    if (rc) return rc;
     const int n = (int)N, np = (int)Np;
     const int Tp = (np + kTile - 1) / kTile, T = (n + kTile - 1) / kTile;
     long long* hA = (long long*)d_hist_A;
@@ -252,6 +283,7 @@ extern "C" int md_clusters_noalloc(const double* d_x, int64_t N, int64_t Np, dou
     k_na_assign<<<(T + kNaWarps - 1) / kNaWarps, kNaWarps * 32, 0, s>>>(W, d_x, n, np, L, r_np * r_np, d_labels);
     k_na_count<<<(n + 255) / 256, 256, 0, s>>>(W, d_labels, n, np, cnt);
     if (np > 0) k_na_hist<<<(np + 255) / 256, 256, 0, s>>>(W, d_labels, np, hA, hZ, cnt);
+    k_na_status<<<1, 1, 0, s>>>(W, cnt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(MD_ECUDA, std::string("md_clusters_noalloc: ") + cudaGetErrorString(e));
     return MD_OK;

@@ -38,7 +38,8 @@ class md_params(ctypes.Structure):
                 ("precision", _I32), ("coulomb", _I32), ("r_pp", _D), ("r_np", _D),
                 ("relax_iters", _I64), ("relax_gamma", _D), ("relax_dmax", _D),
                 ("energy_every", _I64), ("sort_bits", _I32), ("affine", _I32), ("list_kind", _I32),
-                ("verlet_pool", _D), ("cond_graph", _I32), ("force_unroll", _I32)]
+                ("verlet_pool", _D), ("cond_graph", _I32), ("force_unroll", _I32),
+                ("uf_iter_limit", _I64)]
 
 
 class md_energy_t(ctypes.Structure):
@@ -104,6 +105,7 @@ _SIGS = {
     "md_kernel_times": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                        ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_int)]),
     "md_last_error": (ctypes.c_char_p, []),
+    "md_debug_fail_alloc": (ctypes.c_int, [_I64]),
     "md_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(md_job), ctypes.POINTER(md_params),
                                        ctypes.POINTER(_P)]),
     "md_batch_step": (ctypes.c_int, [_P, _I64]),
