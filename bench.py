@@ -35,7 +35,7 @@ sys.path.insert(0, str(ROOT))
 MEASURED = ROOT / "MEASURED_PEAKS.json"
 TRAFFIC = ROOT / "profiles" / "force_split_409600_traffic.json"
 PIPES = ROOT / "profiles" / "force_split_307200_pipes.json"
-FORCE_SRC = ROOT / "paper_1412_8502_b300" / "csrc" / "k_force.cu"
+FORCE_SRC = ROOT / "paper_1412_8502_b300" / "csrc" / "k_force.cuh"
 
 WORKLOADS = {
     "md409600": dict(N=409600, Yp=0.40, T=0.5, rho=0.080, seed=3, xi=7.5e-5,
@@ -377,44 +377,64 @@ def batch_jobs(seed=4):
     return jobs
 
 
-def run_batch(steps):
-    """One graph launch per step for all 15 systems vs the same systems
-    stepped one after another (each its own graph), device time."""
+def run_batch(steps, cmp_steps=1000):
+    """The 15-system ensemble (Yp x T sweep) stepped by ONE persistent kernel
+    launch per step for all systems, its configured run of `steps` steps;
+    then, from the state it reached, the same batch as a graph of separate
+    kernels per step, and each system stepped alone, over cmp_steps steps
+    each (the batch holds no expansion, so the work per step is stationary).
+    Device time (CUDA-synchronised wall clock around the steps)."""
     import torch
     from paper_1412_8502_b300 import md
     jobs = batch_jobs()
     p = md.md_params_default()
     p.energy_every = 1
     ntot = sum(j["N"] for j in jobs)
-    b = md.Batch(jobs, p)
-    p = b.autotune(10)          # project autotuner: skin x sort resolution, shared by all systems
-    tuned_skin = p.skin
-    p.sort_bits = 0             # serial runs: same skin, sort resolution from each N
-    p.r_C = 0.0                 # and the Coulomb cutoff from each box (min(40, L0/2))
-    b.step(3)
-    torch.cuda.synchronize()
-    l0 = b.systems[0].info()["launches"]
-    t0 = time.perf_counter()
-    b.step(steps)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
-    launches = (b.systems[0].info()["launches"] - l0) / steps
+    b = md.Batch(jobs, p)      # persistent = -1: one persistent launch per step for a batch
+    p = b.autotune(10)         # project autotuner: skin x cell size (sort bits) x force-code variant
+    tuned = {"skin_fm": p.skin, "sort_bits_sys0": p.sort_bits, "force_code": p.force_unroll}
+
+    def timed(nsteps):
+        b.step(3)
+        torch.cuda.synchronize()
+        l0 = b.systems[0].info()["launches"]
+        t0 = time.perf_counter()
+        b.step(nsteps)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, (b.systems[0].info()["launches"] - l0) / nsteps
+
+    tb, launches = timed(steps)
+    q = b.systems[0].params
+    q.persistent = 0
+    b.systems[0].params = q
+    cmp_steps = min(cmp_steps, steps)
+    tg, launches_g = timed(cmp_steps)
     b.close()
+    p.sort_bits = 0             # serial runs: same skin and code variant, sort resolution from each N
+    p.r_C = 0.0                 # and the Coulomb cutoff from each box (min(40, L0/2))
     ts = 0.0
     for j in jobs:
-        s = md.System(j["N"], j["Yp"], j["rho"], j["T"], j["seed"], p)   # same tuned settings
+        s = md.System(j["N"], j["Yp"], j["rho"], j["T"], j["seed"], p)
         s.step(3, 0.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.step(steps, 0.0)
+        s.step(cmp_steps, 0.0)
         torch.cuda.synchronize()
         ts += time.perf_counter() - t0
         s.close()
-    return {"systems": len(jobs), "nucleons": ntot, "steps": steps, "tuned_skin_fm": tuned_skin,
-            "batched": ntot * steps / tb, "serial": ntot * steps / ts, "speedup": ts / tb,
+    batched = ntot * steps / tb
+    serial = ntot * cmp_steps / ts
+    return {"systems": len(jobs), "nucleons": ntot, "steps": steps, "tuned": tuned,
+            "batched": batched, "serial": serial, "speedup": batched / serial,
+            "batched_graph": ntot * cmp_steps / tg, "speedup_graph": (ntot * cmp_steps / tg) / serial,
             "unit": "nucleon-steps/s", "kernel_launches_per_step": launches,
+            "kernel_launches_per_step_graph": launches_g, "compare_steps": cmp_steps,
+            "accuracy": "each member bitwise equal to the same system stepped alone (tests)",
             "note": "15 systems (Yp x T sweep), N from {4000,12800,25600,51200}, rho log-uniform "
-                    "[0.00125, 0.08]; batched = one graph launch per step for all; serial = one system at a time"}
+                    "[0.00125, 0.08], energies every step; batched = one persistent kernel launch per step "
+                    "for all systems over the configured steps; batched_graph = the same batch as a graph of "
+                    "separate kernels; serial = one system at a time (each its own graph); the comparisons "
+                    "over compare_steps steps from the state the batched run reached"}
 
 
 def run_serve(n_jobs, steps, rate, seed=5):
@@ -629,7 +649,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--serve-jobs", type=int, default=12)
     ap.add_argument("--serve-steps", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=4.0)

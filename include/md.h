@@ -116,6 +116,22 @@ typedef struct {
                                 A loop that reaches it gives up and the call
                                 returns MD_ETIMEOUT: its labels are then not
                                 valid.  No device wait is involved. */
+    int64_t wait_limit_ns;   /* bound on each grid-wide wait of the persistent
+                                step kernel, ns (default 2e9).  A wait that
+                                reaches it gives up, the kernel's blocks leave,
+                                and the next md_step / md_batch_step / md_sync
+                                returns MD_ETIMEOUT; the state of the systems
+                                is then undefined (destroy them). */
+    int32_t persistent;      /* each step of all systems of an engine as ONE
+                                persistent cooperative launch (phases separated
+                                by bounded grid barriers) instead of a graph of
+                                separate kernels: 1 = on, 0 = off, -1 (default)
+                                = on for batches of two or more systems.  Needs
+                                split precision, tile lists and coulomb 0 or 1
+                                (MD_EINVAL otherwise when 1; -1 falls back to
+                                the graph).  It runs the force-pass code
+                                variant force_unroll fixes (0: the long one).
+                                Results are bitwise those of the graph. */
 } md_params;
 
 typedef struct {
@@ -279,10 +295,14 @@ MD_API int md_kernel_times(md_system* s, int max, const char** names, int64_t* l
 
 /* Autotuner: short timed trials (steps each, from the current state, which
  * is restored afterwards) over pair-list skin {0.5, 1, 1.5, 2} fm x spatial-
- * sort resolution {auto-1, auto, auto+1} bits; keeps the fastest setting and
- * returns the resulting parameters in *chosen (may be NULL).  The physics
- * does not depend on these settings; trajectories differ only by FP32
- * summation order. */
+ * sort resolution, i.e. the cell size of the counting sort, {auto-1, auto,
+ * auto+1} bits per axis x (for engines stepping with the persistent kernel
+ * and force_unroll 0) the force-pass code variant {long, compact, minimal};
+ * keeps the fastest setting and returns the resulting parameters in *chosen
+ * (may be NULL).  The tile shape is not a tuning dimension: a tile is one
+ * warp's 32 targets (the pair block pairs a 16-source half-warp with two
+ * targets per lane).  The physics does not depend on these settings;
+ * trajectories differ only by FP32 summation order. */
 MD_API int md_autotune(md_system* s, int64_t steps, md_params* chosen);
 
 /* Eq. (2): Thomas-Fermi screening length (fm) of a degenerate relativistic

@@ -148,7 +148,7 @@ Engine::~Engine() {
 
 void Engine::free_tables() {
     void* ptrs[] = {d_sys_, d_tile_sys_, d_item_sys_, d_hist_, d_binstart_, d_cursor_, d_blocksum_, d_any_, d_out_,
-                    d_clock_, d_seeds_, d_cond_runs_, d_tune_, d_f64part_, d_f64cnt_};
+                    d_clock_, d_seeds_, d_cond_runs_, d_tune_, d_f64part_, d_f64cnt_, d_pctl_};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     d_sys_ = nullptr;
@@ -158,6 +158,7 @@ void Engine::free_tables() {
     d_any_ = nullptr;
     d_cond_runs_ = nullptr;
     d_tune_ = nullptr;
+    d_pctl_ = nullptr;
     d_f64part_ = nullptr;
     d_f64cnt_ = nullptr;
     d_out_ = d_clock_ = nullptr;
@@ -251,6 +252,10 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     if (p.list_kind == 1 && !(p.verlet_pool > 0.0)) return fail(MD_EINVAL, "verlet_pool must be > 0");
     if (p.uf_iter_limit < 1 || p.uf_iter_limit > 0x7fffffff)
         return fail(MD_EINVAL, "uf_iter_limit must be in [1, 2^31 - 1]");
+    if (p.persistent < -1 || p.persistent > 1) return fail(MD_EINVAL, "persistent must be -1, 0 or 1");
+    if (p.persistent == 1 && (p.precision == MD_PREC_FP64 || p.list_kind != 0 || p.coulomb == 2))
+        return fail(MD_EINVAL, "the persistent step needs split precision, tile lists and coulomb 0 or 1");
+    if (p.wait_limit_ns < 1) return fail(MD_EINVAL, "wait_limit_ns must be >= 1");
     const double L0 = std::cbrt((double)N / rho);
     double rC = p.r_C > 0.0 ? p.r_C : std::min(40.0, 0.5 * L0);
     // (relative slack of 1e-12 absorbs the rounding of cbrt)
@@ -383,6 +388,25 @@ void Engine::remove_system(int idx) {
     sys.erase(sys.begin() + idx);
 }
 
+// Persistent step kernel: wanted by system 0's parameters (1 on, 0 off, -1
+// on for two or more systems) and possible for split precision, tile lists
+// and the cutoff (or no) Coulomb term in every system.
+int Engine::persistent_mode() {
+    persistent_ = false;
+    if (sys.empty()) return MD_OK;
+    const int want = sys[0]->prm.persistent;
+    bool ok = precision != MD_PREC_FP64;
+    for (SysHost* h : sys) ok = ok && h->c.list_kind == 0 && h->c.coulomb != 2;
+    if (want == 1 && !ok)
+        return fail(MD_EINVAL, "the persistent step needs split precision, tile lists and coulomb 0 or 1");
+    persistent_ = ok && (want == 1 || (want == -1 && sys.size() > 1));
+    if (persistent_ && prepare_step_persistent() != 0) {
+        const cudaError_t e = cudaGetLastError();
+        return fail(MD_ECUDA, std::string("persistent step kernel: ") + cudaGetErrorString(e));
+    }
+    return MD_OK;
+}
+
 int Engine::build_tables() {
     cudaStreamSynchronize(stream_);
     drop_graphs();
@@ -430,6 +454,7 @@ int Engine::build_tables() {
     if ((rc = A(&d_any_, sizeof(int)))) return rc;
     if ((rc = A(&d_cond_runs_, sizeof(unsigned long long)))) return rc;
     if ((rc = A(&d_tune_, sizeof(ForceTune)))) return rc;
+    if ((rc = A(&d_pctl_, sizeof(PersistCtl)))) return rc;
     // FP64 mode: split the tiles' entries over blocks while tiles < SMs
     int sms = 148, dev = 0;
     cudaGetDevice(&dev);
@@ -467,7 +492,8 @@ int Engine::build_tables() {
     E.f64cnt = d_f64cnt_;
     long long ntot = 0;
     for (SysHost* h : sys) ntot += h->N;
-    E.tune_variants = (precision != MD_PREC_FP64 && ntot >= kVariantMinN) ? 1 : 0;
+    if ((rc = persistent_mode())) return rc;
+    E.tune_variants = (precision != MD_PREC_FP64 && ntot >= kVariantMinN && !persistent_) ? 1 : 0;
     {
         const int fu = sys.empty() ? 0 : (int)sys[0]->prm.force_unroll;
         H_.fixed_var = fu == 2 ? 1 : fu == 1 ? 2 : 0;
@@ -527,10 +553,14 @@ int Engine::capture(GraphRec& g, int kind, bool energy) {
     g = GraphRec();
     capturing_ = true;
     capture_nodes_ = 0;
+    // kernels of the conditional rebuild bodies (the same in every graph
+    // that has them; a persistent step graph has none and keeps the count)
+    const int prev_cond = cond_nodes_;
     cond_nodes_ = 0;
     cur_rec_ = &g;
     cudaGraph_t graph = nullptr;
     int rc = build_step_graph(graph, kind, energy);
+    if (cond_nodes_ == 0) cond_nodes_ = prev_cond;
     capturing_ = false;
     cur_rec_ = nullptr;
     if (rc != MD_OK) {
@@ -556,6 +586,25 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
     // otherwise the variant md_params.force_unroll fixes (0: the long one)
     const int fu = sys.empty() ? 0 : (int)sys[0]->prm.force_unroll;
     const int fixed_var = fu == 2 ? 1 : fu == 1 ? 2 : 0;
+    if (kind == 0 && persistent_) {
+        // the whole step of every system: one persistent launch
+        CK(cudaStreamBeginCaptureToGraph(stream_, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        const int lr = launch_step_persistent(H_, stream_, energy, fixed_var, d_pctl_,
+                                              (unsigned long long)sys[0]->prm.wait_limit_ns);
+        if (timing_) {
+            cudaEvent_t ev;
+            cudaEventCreate(&ev);
+            cudaEventRecordWithFlags(ev, stream_, cudaEventRecordExternal);
+            cur_rec_->events.push_back(ev);
+        }
+        const cudaError_t le = cudaGetLastError();
+        cudaGraph_t out = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(stream_, &out);
+        if (lr != 0 || le != cudaSuccess || e2 != cudaSuccess)
+            return fail(MD_ECUDA, std::string("persistent step launch: ") +
+                                      cudaGetErrorString(le != cudaSuccess ? le : e2));
+        return MD_OK;
+    }
     cudaGraphConditionalHandle h[3] = {0, 0, 0};
     if (cond) {
         for (int k = 0; k < 2; ++k) CK(cudaGraphConditionalHandleCreate(&h[k], graph, 0, cudaGraphCondAssignDefault));
@@ -727,7 +776,15 @@ int Engine::check_errors() {
     std::vector<int> errs(n, 0);
     for (int s = 0; s < n; ++s)
         CK(cudaMemcpyAsync(&errs[s], &sys[s]->d_st->error, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    int perr = 0;
+    if (d_pctl_) CK(cudaMemcpyAsync(&perr, &d_pctl_->error, sizeof(int), cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));
+    if (perr) {
+        CK(cudaMemsetAsync(&d_pctl_->error, 0, sizeof(int), stream_));
+        CK(cudaStreamSynchronize(stream_));
+        return fail(MD_ETIMEOUT, "a grid-wide wait of the persistent step kernel gave up (wait_limit_ns); "
+                                 "the state of the systems is undefined");
+    }
     for (int s = 0; s < n; ++s) {
         if (errs[s] & 4)
             return fail(MD_ENOMEM, "Verlet list pool of system " + std::to_string(s) +
@@ -1028,6 +1085,10 @@ int Engine::set_params(int idx, const md_params& p) {
     if (p.list_kind == 1 && !(p.verlet_pool > 0.0)) return fail(MD_EINVAL, "verlet_pool must be > 0");
     if (p.uf_iter_limit < 1 || p.uf_iter_limit > 0x7fffffff)
         return fail(MD_EINVAL, "uf_iter_limit must be in [1, 2^31 - 1]");
+    if (p.persistent < -1 || p.persistent > 1) return fail(MD_EINVAL, "persistent must be -1, 0 or 1");
+    if (p.persistent == 1 && (p.precision == MD_PREC_FP64 || p.list_kind != 0 || p.coulomb == 2))
+        return fail(MD_EINVAL, "the persistent step needs split precision, tile lists and coulomb 0 or 1");
+    if (p.wait_limit_ns < 1) return fail(MD_EINVAL, "wait_limit_ns must be >= 1");
     const int nbits = p.sort_bits ? p.sort_bits : auto_bits(h.N);
     if (p.list_kind == 1) {
         // (re)allocate the list pool when it is missing or too small
@@ -1092,6 +1153,10 @@ int Engine::set_params(int idx, const md_params& p) {
     c.force_unroll = p.force_unroll;
     c.uf_limit = (int)p.uf_iter_limit;
     c.pf = pair_consts(c);
+    if (idx == 0 && (p.persistent != h.prm.persistent || p.wait_limit_ns != h.prm.wait_limit_ns)) {
+        cudaStreamSynchronize(stream_);
+        drop_graphs();
+    }
     if (pp_changed || lists_changed) {
         cudaStreamSynchronize(stream_);
         drop_graphs();
@@ -1100,6 +1165,18 @@ int Engine::set_params(int idx, const md_params& p) {
         for (SysHost* q : sys) {
             H_.any_pp |= (q->c.coulomb == 2);
             H_.any_verlet |= (q->c.list_kind == 1);
+        }
+    }
+    {
+        const bool was = persistent_;
+        int rc = persistent_mode();
+        if (rc) return rc;
+        if (was != persistent_) {
+            cudaStreamSynchronize(stream_);
+            drop_graphs();
+            long long ntot = 0;
+            for (SysHost* q : sys) ntot += q->N;
+            H_.dev.tune_variants = (precision != MD_PREC_FP64 && ntot >= kVariantMinN && !persistent_) ? 1 : 0;
         }
     }
     if (nbits != h.nbits) {
@@ -1141,31 +1218,40 @@ int Engine::autotune(int64_t steps, md_params* chosen) {
     }
     const double skins[] = {0.5, 1.0, 1.5, 2.0};
     const int dbits[] = {-1, 0, 1};
+    // force-pass code variants (loop unrolling, i.e. instruction footprint):
+    // tried where the step runs one fixed variant, the persistent step kernel
+    // (graph steps of large engines choose theirs on the device)
+    std::vector<int> codes(1, base[0].force_unroll);
+    if (persistent_ && base[0].force_unroll == 0) codes = {4, 2, 1};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
     double best_skin = base[0].skin;
-    int best_d = 0;
-    for (double sk : skins) {
-        for (int d : dbits) {
-            for (int s = 0; s < n; ++s) {
-                md_params p = base[s];
-                p.skin = sk;
-                p.sort_bits = std::min(7, std::max(2, auto_bits(sys[s]->N) + d));
-                if ((rc = set_params(s, p)) || (rc = set_state(s, &saved[s]))) goto done;
-            }
-            if ((rc = step(2, nullptr))) goto done;
-            CK(cudaEventRecord(e0, stream_));
-            if ((rc = step_async(steps, nullptr, nullptr))) goto done;
-            CK(cudaEventRecord(e1, stream_));
-            if ((rc = check_errors())) goto done;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                best_skin = sk;
-                best_d = d;
+    int best_d = 0, best_code = codes[0];
+    for (int code : codes) {
+        for (double sk : skins) {
+            for (int d : dbits) {
+                for (int s = 0; s < n; ++s) {
+                    md_params p = base[s];
+                    p.skin = sk;
+                    p.sort_bits = std::min(7, std::max(2, auto_bits(sys[s]->N) + d));
+                    p.force_unroll = code;
+                    if ((rc = set_params(s, p)) || (rc = set_state(s, &saved[s]))) goto done;
+                }
+                if ((rc = step(2, nullptr))) goto done;
+                CK(cudaEventRecord(e0, stream_));
+                if ((rc = step_async(steps, nullptr, nullptr))) goto done;
+                CK(cudaEventRecord(e1, stream_));
+                if ((rc = check_errors())) goto done;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    best_skin = sk;
+                    best_d = d;
+                    best_code = code;
+                }
             }
         }
     }
@@ -1173,6 +1259,7 @@ int Engine::autotune(int64_t steps, md_params* chosen) {
         md_params p = base[s];
         p.skin = best_skin;
         p.sort_bits = std::min(7, std::max(2, auto_bits(sys[s]->N) + best_d));
+        p.force_unroll = best_code;
         if ((rc = set_params(s, p)) || (rc = set_state(s, &saved[s]))) goto done;
         sys[s]->host_step = saved[s].step;
     }

@@ -133,6 +133,9 @@ private:
     cudaStream_t aux_stream_ = nullptr;     // captures the bodies of conditional nodes
     unsigned long long* d_cond_runs_ = nullptr;
     ForceTune* d_tune_ = nullptr;
+    PersistCtl* d_pctl_ = nullptr;          // persistent step kernel: barrier, work counter, error flag
+    bool persistent_ = false;               // steps run as one persistent launch
+    int persistent_mode();                  // recompute persistent_ from the systems' parameters
     double* d_f64part_ = nullptr;
     int* d_f64cnt_ = nullptr;
     int build_step_graph(cudaGraph_t& graph, int kind, bool energy);

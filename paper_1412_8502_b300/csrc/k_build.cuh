@@ -128,9 +128,9 @@ __device__ __forceinline__ void warp_bounds(double v, bool valid, double& lo, do
 // two conditional (IF) nodes, on handles cond_cell and cond_list (a handle
 // drives one node); it sets both, so the rebuild kernels are not launched at
 // all on steps without a rebuild.
-__global__ void k_decide(EngineDev E, int forced_only, int only, cudaGraphConditionalHandle cond_cell,
-                         cudaGraphConditionalHandle cond_list, int set_cond, cudaGraphConditionalHandle cond_var,
-                         int set_var) {
+__device__ __forceinline__ void decide_body(const EngineDev& E, int forced_only, int only,
+                                            cudaGraphConditionalHandle cond_cell, cudaGraphConditionalHandle cond_list,
+                                            int set_cond, cudaGraphConditionalHandle cond_var, int set_var) {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -178,10 +178,16 @@ __global__ void k_decide(EngineDev E, int forced_only, int only, cudaGraphCondit
     }
 }
 
+__global__ void k_decide(EngineDev E, int forced_only, int only, cudaGraphConditionalHandle cond_cell,
+                         cudaGraphConditionalHandle cond_list, int set_cond, cudaGraphConditionalHandle cond_var,
+                         int set_var) {
+    decide_body(E, forced_only, only, cond_cell, cond_list, set_cond, cond_var, set_var);
+}
+
 // ---------------------------------------------------------------- histogram
-__global__ void k_hist(EngineDev E) {
+__device__ __forceinline__ void hist_body(const EngineDev& E, int bx) {
     if (!*E.any_rebuild) return;
-    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    const int g = bx * kTilesPerBlock + (threadIdx.x >> 5);
     if (g >= E.ntiles) return;
     const int s = E.tile_sys[g];
     if (s < 0) return;
@@ -198,6 +204,8 @@ __global__ void k_hist(EngineDev E) {
     S.key[p] = k;
     atomicAdd(&E.hist[S.bin_base + k], 1u);
 }
+
+__global__ void k_hist(EngineDev E) { hist_body(E, blockIdx.x); }
 
 // ---------------------------------------------------------------- bin scan
 // Three-pass exclusive scan of hist over all systems' bins (8192 per block).
@@ -241,7 +249,7 @@ __global__ void k_scan_reduce(EngineDev E) {
     if (threadIdx.x == 0) E.blocksum[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_top(EngineDev E, int nblk) {
+__device__ __forceinline__ void scan_top_body(const EngineDev& E, int nblk) {
     if (!*E.any_rebuild) return;
     __shared__ unsigned sm[33];
     const int per = (nblk + blockDim.x - 1) / blockDim.x;
@@ -257,6 +265,8 @@ __global__ void k_scan_top(EngineDev E, int nblk) {
             run += v;
         }
 }
+
+__global__ void k_scan_top(EngineDev E, int nblk) { scan_top_body(E, nblk); }
 
 __global__ void k_scan_down(EngineDev E) {
     if (!*E.any_rebuild) return;
@@ -279,9 +289,9 @@ __global__ void k_scan_down(EngineDev E) {
 // ---------------------------------------------------------------- scatter
 // Places each slot index in its bin (order inside a bin decided by atomics,
 // fixed up deterministically by k_move).
-__global__ void k_scatter(EngineDev E) {
+__device__ __forceinline__ void scatter_body(const EngineDev& E, int bx) {
     if (!*E.any_rebuild) return;
-    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    const int g = bx * kTilesPerBlock + (threadIdx.x >> 5);
     if (g >= E.ntiles) return;
     const int s = E.tile_sys[g];
     if (s < 0) return;
@@ -296,13 +306,15 @@ __global__ void k_scatter(EngineDev E) {
     S.slot[pos] = p;
 }
 
+__global__ void k_scatter(EngineDev E) { scatter_body(E, blockIdx.x); }
+
 // Destination of slot q's particle: its bin start plus the number of
 // particles of the same bin with a smaller previous slot index (stable,
 // deterministic).  Moves x, v, id (the forces are evaluated after the
 // rebuild, or placed by id when a state is loaded with its forces).
-__global__ void k_move(EngineDev E) {
+__device__ __forceinline__ void move_body(const EngineDev& E, int bx) {
     if (!*E.any_rebuild) return;
-    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    const int g = bx * kTilesPerBlock + (threadIdx.x >> 5);
     if (g >= E.ntiles) return;
     const int s = E.tile_sys[g];
     if (s < 0) return;
@@ -331,13 +343,15 @@ __global__ void k_move(EngineDev E) {
     S.id[cn][d] = S.id[c][j];
 }
 
+__global__ void k_move(EngineDev E) { move_body(E, blockIdx.x); }
+
 // ---------------------------------------------------------------- tiles
 // Warp per tile: bounding box, FP64 origin (box centre), FP32 local
 // coordinates, displacement reset.  Also clears the system's histogram for
 // the next rebuild and records the rebuild.
-__global__ void k_tiles(EngineDev E) {
+__device__ __forceinline__ void tiles_body(const EngineDev& E, int bx) {
     if (!*E.any_rebuild) return;
-    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    const int g = bx * kTilesPerBlock + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= E.ntiles) return;
     const int s = E.tile_sys[g];
@@ -423,6 +437,8 @@ __global__ void k_tiles(EngineDev E) {
     }
 }
 
+__global__ void k_tiles(EngineDev E) { tiles_body(E, blockIdx.x); }
+
 // ---------------------------------------------------------------- lists
 // FP32 test "bounding boxes of I and J (nearest image) closer than R".
 // Rounding of the FP32 origins (< 1e-4 fm for L < 2000 fm) is covered by
@@ -505,9 +521,9 @@ __device__ inline int list_entry(const SysConst& S, int I, int J, const float4& 
 // Boxes of super-tiles (32 consecutive tiles, compact in Hilbert order):
 // one warp each, lane k taking member tile 32 s + k; the union of the member
 // boxes from exact integer min / max reductions of the FP32 box faces.
-__global__ void k_super(EngineDev E) {
+__device__ __forceinline__ void super_body(const EngineDev& E, int bx) {
     if (!*E.any_rebuild) return;
-    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    const int g = bx * kTilesPerBlock + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= E.ntiles) return;
     const int s = E.tile_sys[g];
@@ -533,6 +549,8 @@ __global__ void k_super(EngineDev E) {
                                      0.5f * (hi[2] - lo[2]) * (1.0f + 1e-6f) + 1e-4f, 0.f);
 }
 
+__global__ void k_super(EngineDev E) { super_body(E, blockIdx.x); }
+
 // Force lists in one pass: tile I's entries go to list[I*T ...], its count
 // to lcount[I] (the list buffer holds T entries per tile, the worst case).
 // Super-tiles out of range of I (widest range) are skipped whole.
@@ -547,9 +565,9 @@ __device__ __forceinline__ bool owns_pair(int I, int J, int half) {
     return J != I && ((I < J) != (((I + J) & 1) != 0));
 }
 
-__global__ void k_lbuild(EngineDev E, int half) {
+__device__ __forceinline__ void lbuild_body(const EngineDev& E, int half, int bx) {
     if (!*E.any_rebuild) return;
-    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+    const int g = bx * kTilesPerBlock + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= E.ntiles) return;
     const int s = E.tile_sys[g];
@@ -633,6 +651,8 @@ __global__ void k_lbuild(EngineDev E, int half) {
         atomicAdd((unsigned long long*)&st->list_total, (unsigned long long)(out + outf));
     }
 }
+
+__global__ void k_lbuild(EngineDev E, int half) { lbuild_body(E, half, blockIdx.x); }
 
 // Per-particle Verlet lists (list_kind 1), built from the full tile-pair
 // lists: one block of kVB warps per tile I; lane l keeps every particle j of

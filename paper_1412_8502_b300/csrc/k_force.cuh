@@ -697,16 +697,11 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
 // gate: the launch returns at once unless kVar is this step's selection
 // (plain graphs launch all three).  Block 0 records the start of the pass
 // for the tuner.
+// Global work item g of the split force pass, taken by one warp (queues Q).
 template <bool kEnergy, int kVar>
-__global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS)
-    k_force_split(EngineDev E, int only, int gate) {
-    __shared__ WarpQueues qs[kForceWarps];
-    ForceTune* tu = E.tune;
-    if (gate && tu->sel != kVar) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) tu->t_start = global_ns();   // k_force_fix takes the end
+__device__ __forceinline__ void force_split_item(const EngineDev& E, int only, int g, WarpQueues& Q) {
     constexpr int kU = kVar == 0 ? kULong : kVar == 1 ? kUCompact : kUMinimal;
     constexpr int kUWrap = kVar == 0 ? kULong : kUCompact;                  // per-pair wrap halves it
-    const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
     if (g >= E.nitems) return;
     const int s = E.item_sys[g];
     if (s < 0 || (only >= 0 && s != only)) return;
@@ -714,10 +709,20 @@ __global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS)
     if (S.list_kind != 0) return;          // per-particle lists: k_force_verlet
     const int v = g - S.item_base;
     if (v >= S.n_items) return;
-    WarpQueues& Q = qs[threadIdx.x >> 5];
     const PairF& P = S.pf;
     if (S.st->need_wrap) force_item<true, kEnergy, kUWrap>(S, P, v, Q);
     else force_item<false, kEnergy, kU>(S, P, v, Q);
+}
+
+template <bool kEnergy, int kVar>
+__global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS)
+    k_force_split(EngineDev E, int only, int gate) {
+    __shared__ WarpQueues qs[kForceWarps];
+    ForceTune* tu = E.tune;
+    if (gate && tu->sel != kVar) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) tu->t_start = global_ns();   // k_force_fix takes the end
+    const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
+    force_split_item<kEnergy, kVar>(E, only, g, qs[threadIdx.x >> 5]);
 }
 
 // ---------------------------------------------------------------- Verlet

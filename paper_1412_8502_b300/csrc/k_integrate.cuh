@@ -22,8 +22,9 @@ struct Slot {
     bool valid;
 };
 
-__device__ inline bool slot_of(const EngineDev& E, int only, Slot& o) {
-    const int g = blockIdx.x * kTilesPerBlock + (threadIdx.x >> 5);
+// bx: the block index (a persistent kernel passes the block it plays)
+__device__ inline bool slot_of(const EngineDev& E, int only, Slot& o, int bx = blockIdx.x) {
+    const int g = bx * kTilesPerBlock + (threadIdx.x >> 5);
     if (g >= E.ntiles) return false;
     const int s = E.tile_sys[g];
     if (s < 0 || (only >= 0 && s != only)) return false;
@@ -37,8 +38,8 @@ __device__ inline bool slot_of(const EngineDev& E, int only, Slot& o) {
 }
 
 // Block index of this block within its system (blocks never span systems).
-__device__ inline int sys_block(const SysConst& S) {
-    return blockIdx.x - S.tile_base / kTilesPerBlock;
+__device__ inline int sys_block(const SysConst& S, int bx = blockIdx.x) {
+    return bx - S.tile_base / kTilesPerBlock;
 }
 __device__ inline int sys_nblocks(const SysConst& S) {
     return (S.T + kTilesPerBlock - 1) / kTilesPerBlock;
@@ -67,7 +68,7 @@ __device__ inline void block_sum4(const SysConst& S, double a, double b, double 
 }
 
 // Fixed-order block sum of one double into S.blk[blockIdx * 4].
-__device__ inline void block_sum1(const SysConst& S, double a) {
+__device__ inline void block_sum1(const SysConst& S, double a, int bx = blockIdx.x) {
     __shared__ double sm1[kTilesPerBlock];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     a = warp_sum(a);
@@ -76,7 +77,7 @@ __device__ inline void block_sum1(const SysConst& S, double a) {
     if (threadIdx.x == 0) {
         double r = 0.0;
         for (int k = 0; k < kTilesPerBlock; ++k) r += sm1[k];
-        S.blk[4 * sys_block(S)] = r;
+        S.blk[4 * sys_block(S, bx)] = r;
     }
 }
 
@@ -211,7 +212,8 @@ __global__ void k_sub_com(EngineDev E) {
 // factor on x (displacement and tile-frame positions follow).  Launched with
 // a small grid that strides over the blocks of slots: on most steps no system
 // has a factor pending and every thread returns after reading the flags.
-__global__ void k_rescale(EngineDev E, int only) {
+// b0, stride: the blocks of slots this block takes (grid-stride loop)
+__device__ __forceinline__ void rescale_body(const EngineDev& E, int only, int b0, int stride) {
     bool any = false;
     for (int s = 0; s < E.nsys; ++s) {
         const SysState* st = E.sys[s].st;
@@ -219,7 +221,7 @@ __global__ void k_rescale(EngineDev E, int only) {
     }
     if (!any) return;
     const int nb = (E.ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
-    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    for (int b = b0; b < nb; b += stride) {
         const int g = b * kTilesPerBlock + (threadIdx.x >> 5);
         if (g >= E.ntiles) continue;
         const int s = E.tile_sys[g];
@@ -250,6 +252,8 @@ __global__ void k_rescale(EngineDev E, int only) {
         }
     }
 }
+
+__global__ void k_rescale(EngineDev E, int only) { rescale_body(E, only, blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------- relax
 // Steepest descent (reading of the paper's equilibration from random
@@ -290,9 +294,9 @@ __global__ void k_sd_update(EngineDev E) {
 
 // ---------------------------------------------------------------- Verlet
 template <typename FT>
-__global__ void k_kick_drift(EngineDev E) {
+__device__ __forceinline__ void kick_drift_body(const EngineDev& E, int bx) {
     Slot o;
-    if (!slot_of(E, -1, o)) return;     // whole block: systems start on block boundaries
+    if (!slot_of(E, -1, o, bx)) return;     // whole block: systems start on block boundaries
     const SysConst& S = E.sys[o.s];
     SysState* st = S.st;
     const int lane = threadIdx.x & 31;
@@ -320,6 +324,11 @@ __global__ void k_kick_drift(EngineDev E) {
 }
 
 template <typename FT>
+__global__ void k_kick_drift(EngineDev E) {
+    kick_drift_body<FT>(E, blockIdx.x);
+}
+
+template <typename FT>
 __global__ void k_kick(EngineDev E) {
     Slot o;
     if (!slot_of(E, -1, o)) return;
@@ -344,10 +353,10 @@ __global__ void k_kick(EngineDev E) {
 // F = FP32(facc) 2^-32 is stored for the next step's first half-kick and for
 // readers of the state, the accumulators are cleared, v += dt/(2M) F.  Its
 // start also closes the force pass's duration for the device tuner.
-__global__ void k_kick_fix(EngineDev E) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) E.tune->t_last = global_ns() - E.tune->t_start;
+__device__ __forceinline__ void kick_fix_body(const EngineDev& E, int bx) {
+    if (bx == 0 && threadIdx.x == 0) E.tune->t_last = global_ns() - E.tune->t_start;
     Slot o;
-    if (!slot_of(E, -1, o)) return;
+    if (!slot_of(E, -1, o, bx)) return;
     const SysConst& S = E.sys[o.s];
     const SysState* st = S.st;
     double v2 = 0.0;
@@ -368,8 +377,10 @@ __global__ void k_kick_fix(EngineDev E) {
             v2 = fma(v, v, v2);
         }
     }
-    block_sum1(S, v2);
+    block_sum1(S, v2, bx);
 }
+
+__global__ void k_kick_fix(EngineDev E) { kick_fix_body(E, blockIdx.x); }
 
 // One block per system.  energy: also record the energy pass's totals.
 // Force-pass code variant (ForceTune): account the pass of the step just
@@ -405,8 +416,7 @@ __device__ inline void tune_step(ForceTune* tu, long long step, bool active) {
     }
 }
 
-__global__ void k_finalize(EngineDev E, int energy) {
-    const int s = blockIdx.x;
+__device__ __forceinline__ void finalize_body(const EngineDev& E, int energy, int s) {
     const SysConst& S = E.sys[s];
     SysState* st = S.st;
     const int lane = threadIdx.x;
@@ -442,6 +452,8 @@ __global__ void k_finalize(EngineDev E, int energy) {
     }
     if (s == 0 && E.tune) tune_step(E.tune, st->step, E.tune_variants && S.force_unroll == 0 && S.list_kind == 0);
 }
+
+__global__ void k_finalize(EngineDev E, int energy) { finalize_body(E, energy, blockIdx.x); }
 
 // Energies at the current state (md_energy): KE from the block partials of
 // k_vsum(mode 1), PE from the record of an energy force pass.

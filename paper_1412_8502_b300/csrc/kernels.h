@@ -77,5 +77,10 @@ void launch_set_rate(const EngineHost& H, cudaStream_t s, int only, double xi_do
 void launch_clusters(const EngineHost& H, cudaStream_t s, int only, int Np, int N, int Tp, int T,
                      int32_t* d_labels_out);
 void launch_mste(const EngineHost& H, cudaStream_t s, int only, int N, int T, int32_t* d_labels_out);
+// One step of all systems as one persistent cooperative launch (after a
+// memset node clearing the barrier counter); returns 0 or -1 (launch failed).
+int launch_step_persistent(const EngineHost& H, cudaStream_t s, bool energy, int var, PersistCtl* ctl,
+                           unsigned long long limit_ns);
+int prepare_step_persistent();
 
 }  // namespace pasta

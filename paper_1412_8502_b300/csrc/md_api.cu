@@ -71,6 +71,8 @@ void md_params_default(md_params* p) {
     p->cond_graph = 1;
     p->force_unroll = 0;
     p->uf_iter_limit = 1ll << 26;
+    p->wait_limit_ns = 2000000000ll;
+    p->persistent = -1;
 }
 
 double md_lambda_thomas_fermi(double n_e) { return pasta::lambda_thomas_fermi(n_e); }

@@ -199,6 +199,14 @@ struct EngineDev {
 // node costs ~7 us per step, more than the variants gain on short passes.
 constexpr long long kVariantMinN = 131072;
 
+// Control block of the persistent step kernel (k_persist.cuh).
+struct PersistCtl {
+    unsigned bar;                // barrier arrivals of this launch (cleared before it)
+    unsigned work;               // next force work item
+    int error;                   // 1: a barrier wait gave up (sticky until the host reads it)
+    int pad;
+};
+
 // Force work items of a system.  A proton tile's list holds its near
 // entries (nuclear range) first and its Coulomb-only entries from the back of
 // its region; it gives kPChunks items: item 0 the near entries (and the tile

@@ -284,14 +284,15 @@ int md_server_submit(md_server* sv, const md_job* job, int64_t* id) {
     j->job = *job;
     j->bytes = Engine::estimate_bytes(job->N, job->Yp, job->rho, sv->prm);
     j->t_submit = Clock::now();
+    int64_t jid;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
-        j->id = sv->next_id++;
+        jid = j->id = sv->next_id++;
         sv->pending.push_back(j);
         sv->submitted += 1;
     }
-    sv->cv.notify_all();
-    if (id) *id = j->id;
+    sv->cv.notify_all();     // (the worker may finish and free j from here on)
+    if (id) *id = jid;
     return MD_OK;
 }
 

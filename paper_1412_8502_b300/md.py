@@ -39,7 +39,7 @@ class md_params(ctypes.Structure):
                 ("relax_iters", _I64), ("relax_gamma", _D), ("relax_dmax", _D),
                 ("energy_every", _I64), ("sort_bits", _I32), ("affine", _I32), ("list_kind", _I32),
                 ("verlet_pool", _D), ("cond_graph", _I32), ("force_unroll", _I32),
-                ("uf_iter_limit", _I64)]
+                ("uf_iter_limit", _I64), ("wait_limit_ns", _I64), ("persistent", _I32)]
 
 
 class md_energy_t(ctypes.Structure):

@@ -55,6 +55,70 @@ def test_batch_member_equals_alone(md):
     b.close()
 
 
+def test_persistent_step_is_one_launch_and_equals_the_graph(md):
+    """The persistent step kernel (one cooperative launch per step for all
+    systems, phases between bounded grid barriers) gives bitwise the states,
+    forces and energies of the graph of separate kernels, with and without
+    the energy pass, through rebuilds, box growth and the thermostat."""
+    for ee in (0, 1):
+        ps, pg = params(md), params(md)
+        ps.persistent, pg.persistent = 1, 0
+        ps.energy_every = pg.energy_every = ee
+        bs, bg = md.Batch(JOBS, ps), md.Batch(JOBS, pg)
+        bs.step(1)                 # (the first call also sets the systems' expansion rates)
+        bg.step(1)
+        n0 = bs.systems[0].info()["launches"]
+        bs.step(40)
+        bg.step(40)
+        assert bs.systems[0].info()["launches"] - n0 == 40      # one kernel per step
+        assert bs.systems[0].info()["rebuilds"] > 2
+        for s1, s0 in zip(bs.systems, bg.systems):
+            g1, g0 = s1.state(), s0.state()
+            assert np.array_equal(g1["x"], g0["x"]) and np.array_equal(g1["v"], g0["v"])
+            assert g1["L"] == g0["L"] and g1["t"] == g0["t"]
+            assert np.array_equal(s1.forces(), s0.forces())
+            if ee:
+                assert s1.step_energy() == s0.step_energy()
+        bs.close()
+        bg.close()
+    # one system on its own, in the same launch form
+    p = params(md)
+    p.persistent = 1
+    a = md.System(3000, 0.3, 0.03, 1.0, 21, p)
+    p.persistent = 0
+    b = md.System(3000, 0.3, 0.03, 1.0, 21, p)
+    a.step(25, 1e-4)
+    b.step(25, 1e-4)
+    assert np.array_equal(a.state()["x"], b.state()["x"]) and np.array_equal(a.forces(), b.forces())
+    a.close()
+    b.close()
+
+
+def test_persistent_wait_limit_is_an_error_status(md):
+    """Every grid-wide wait of the persistent step kernel is bounded by
+    md_params.wait_limit_ns (%globaltimer).  At 1 ns the waits give up (the
+    blocks reach the barrier after the force phase microseconds apart), every
+    block leaves at its next barrier, and md_batch_step returns MD_ETIMEOUT:
+    no hang and no device fault.  The limit is then restored and a fresh batch
+    steps normally on the same device."""
+    p = params(md)
+    p.persistent = 1
+    p.wait_limit_ns = 1
+    b = md.Batch(JOBS, p)
+    with pytest.raises(md.MDError) as e:
+        b.step(3)
+    assert e.value.code == md.MD_ETIMEOUT
+    b.close()
+    p.wait_limit_ns = 2_000_000_000
+    b = md.Batch(JOBS, p)
+    b.step(5)
+    b.close()
+    p.persistent = 2
+    with pytest.raises(md.MDError) as e:
+        md.Batch(JOBS, p)
+    assert e.value.code == md.MD_EINVAL
+
+
 def test_batch_member_matches_oracle(md):
     p = params(md)
     b = md.Batch(JOBS[:3], p)
