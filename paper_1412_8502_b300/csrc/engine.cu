@@ -794,6 +794,25 @@ int Engine::check_errors() {
     return MD_OK;
 }
 
+int Engine::enqueue_status(int* h) {
+    const int n = (int)sys.size();
+    for (int s = 0; s < n; ++s)
+        CK(cudaMemcpyAsync(&h[s], &sys[s]->d_st->error, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    h[n] = 0;
+    if (d_pctl_) CK(cudaMemcpyAsync(&h[n], &d_pctl_->error, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    return MD_OK;
+}
+
+int Engine::status_of(const int* h) const {
+    const int n = (int)sys.size();
+    if (h[n]) return fail(MD_ETIMEOUT, "a grid-wide wait of the persistent step kernel gave up (wait_limit_ns)");
+    for (int s = 0; s < n; ++s) {
+        if (h[s] & 4) return fail(MD_ENOMEM, "Verlet list pool of system " + std::to_string(s) + " exhausted");
+        if (h[s]) return fail(MD_ENUMERIC, "non-finite force in system " + std::to_string(s));
+    }
+    return MD_OK;
+}
+
 int Engine::step(int64_t n, const std::vector<double>* xi) {
     int rc = step_async(n, xi, nullptr);
     if (rc) return rc;

@@ -85,6 +85,11 @@ public:
     int info(int idx, md_info_t* out);
     int autotune(int64_t steps, md_params* chosen);
     int check_errors();                     // sync + MD_ENUMERIC
+    // Error words of all systems (and of the persistent step kernel) copied
+    // into host (pinned) memory h[0 .. sys.size()] on the stream, without a
+    // synchronisation; status_of reads them once the copies have completed.
+    int enqueue_status(int* h);
+    int status_of(const int* h) const;
     size_t device_bytes() const;
 
     void set_stream(cudaStream_t s);

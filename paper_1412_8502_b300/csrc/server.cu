@@ -5,10 +5,13 @@
 // next to the jobs already resident.  Each admitted job keeps its state in
 // device memory on its own stream.  Its creation (seeding, relaxation) and
 // then slices of steps are enqueued asynchronously; the worker polls each
-// job's completion event and enqueues the job's next slice as soon as the
-// previous one is done, so every job's stream stays busy and the jobs'
-// kernels overlap on the device.  Per-step latencies come from events on the
-// job's stream.  Finished jobs are retired and waiting ones admitted.  A
+// job's slices and keeps two of them queued on its stream (the next is
+// enqueued as soon as the older one is done), so a job's stream stays busy
+// while the worker serves the other jobs or admits a new one, and the jobs'
+// kernels overlap on the device.  A slice's error words are copied to pinned
+// host memory behind it, so reaping a slice never synchronises a stream.
+// Per-step latencies come from events on the job's stream.  Finished jobs
+// are retired and waiting ones admitted.  A
 // retired job's device memory is released only when the server is idle or
 // when a waiting job needs the room: freeing device memory waits for the
 // whole device, which would drain every other job's queued work and leave
@@ -32,7 +35,19 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-enum JobState { kInit = 0, kReady = 1, kRunning = 2 };
+// A slice of a job's work enqueued on its stream: relaxation iterations or
+// steps, with events around every step (latencies), the job's error words
+// copied into pinned memory behind it, and a completion event.
+struct Slice {
+    bool steps = false;
+    int64_t n = 0;
+    std::vector<cudaEvent_t> ev;     // n + 1 used (steps only)
+    cudaEvent_t done = nullptr;
+    int* err = nullptr;              // pinned: the engine's error words after the slice
+};
+
+constexpr int kInFlight = 2;         // slices queued per job: its stream never runs dry
+                                     // while the worker serves the other jobs
 
 struct Job {
     int64_t id;
@@ -40,13 +55,12 @@ struct Job {
     size_t bytes;
     Clock::time_point t_submit, t_admit;
     Engine* eng = nullptr;
-    int64_t done_steps = 0;
+    int64_t done_steps = 0;          // steps of completed slices
+    int64_t queued_steps = 0;        // steps enqueued so far
     std::vector<double> lat_ms;
-    std::vector<cudaEvent_t> ev;
-    cudaEvent_t done = nullptr;
-    int state = kInit;
-    int64_t slice = 0;
-    int64_t relax_left = 0;      // relaxation iterations not yet enqueued
+    Slice sl[kInFlight];
+    int head = 0, count = 0;         // in-flight slices: sl[head], sl[(head + 1) % kInFlight], ...
+    int64_t relax_left = 0;          // relaxation iterations not yet enqueued
 };
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
@@ -114,8 +128,12 @@ void md_server::retire(Job* j, int status) {
     r.run_ms = ms_between(j->t_admit, now);
     r.step_p50_ms = pct(j->lat_ms, 0.50);
     r.step_p99_ms = pct(j->lat_ms, 0.99);
-    for (cudaEvent_t e : j->ev) cudaEventDestroy(e);
-    if (j->done) cudaEventDestroy(j->done);
+    if (j->eng && j->count > 0) cudaStreamSynchronize(j->eng->stream());   // (a failed job's queued slices)
+    for (Slice& q : j->sl) {
+        for (cudaEvent_t e : q.ev) cudaEventDestroy(e);
+        if (q.done) cudaEventDestroy(q.done);
+        if (q.err) cudaFreeHost(q.err);
+    }
     // an admitted job's bytes stay in `used` until its engine is released;
     // a job larger than the budget was never admitted (no engine, no bytes)
     if (j->eng) retired.emplace_back(j->eng, j->bytes);
@@ -174,11 +192,18 @@ void md_server::admit() {
             retire(j, rc);
             continue;
         }
-        j->ev.resize(slice_steps + 1);
-        for (auto& ev : j->ev) cudaEventCreate(&ev);
-        cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming);
-        cudaEventRecord(j->done, e->stream());
-        j->state = kInit;
+        bool ok = true;
+        for (Slice& q : j->sl) {
+            q.ev.resize(slice_steps + 1);
+            for (auto& ev : q.ev) ok = ok && cudaEventCreate(&ev) == cudaSuccess;
+            ok = ok && cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming) == cudaSuccess;
+            ok = ok && cudaHostAlloc((void**)&q.err, sizeof(int) * (e->sys.size() + 1), cudaHostAllocDefault) ==
+                           cudaSuccess;
+        }
+        if (!ok) {
+            retire(j, MD_ECUDA);
+            continue;
+        }
         active.push_back(j);
     }
 }
@@ -196,57 +221,60 @@ void md_server::run() {
         bool progressed = false;
         std::vector<Job*> keep;
         for (Job* j : active) {
-            if (j->state != kReady) {
-                const cudaError_t q = cudaEventQuery(j->done);
-                if (q == cudaErrorNotReady) {
-                    keep.push_back(j);
-                    continue;
-                }
+            // reap the completed slices, oldest first
+            int rc = MD_OK;
+            while (j->count > 0) {
+                Slice& q = j->sl[j->head];
+                const cudaError_t e = cudaEventQuery(q.done);
+                if (e == cudaErrorNotReady) break;
                 progressed = true;
-                int rc = q == cudaSuccess ? j->eng->check_errors() : MD_ECUDA;
-                if (rc == MD_OK && j->state == kRunning) {
-                    for (int64_t k = 0; k < j->slice; ++k) {
+                rc = e == cudaSuccess ? j->eng->status_of(q.err) : MD_ECUDA;
+                if (rc != MD_OK) break;
+                if (q.steps) {
+                    for (int64_t k = 0; k < q.n; ++k) {
                         float ms = 0.f;
-                        cudaEventElapsedTime(&ms, j->ev[k], j->ev[k + 1]);
+                        cudaEventElapsedTime(&ms, q.ev[k], q.ev[k + 1]);
                         j->lat_ms.push_back(ms);
                     }
-                    j->done_steps += j->slice;
+                    j->done_steps += q.n;
                 }
-                if (rc != MD_OK) {
-                    retire(j, rc);
-                    continue;
-                }
-                j->state = kReady;
+                j->head = (j->head + 1) % kInFlight;
+                j->count -= 1;
             }
-            if (j->relax_left > 0 && !stop) {     // creation: the next slice of relaxation
-                const int64_t k = std::min(slice_steps, j->relax_left);
-                int rc = j->eng->relax_async(k);
-                if (rc == MD_OK && cudaEventRecord(j->done, j->eng->stream()) != cudaSuccess) rc = MD_ECUDA;
-                if (rc != MD_OK) {
-                    retire(j, rc);
-                    continue;
-                }
-                j->relax_left -= k;
-                j->state = kInit;
-                progressed = true;
-                keep.push_back(j);
-                continue;
-            }
-            const int64_t left = j->job.steps - j->done_steps;
-            if (left <= 0 || stop) {
-                retire(j, stop && left > 0 ? MD_ETIMEOUT : MD_OK);
-                continue;
-            }
-            j->slice = std::min(slice_steps, left);
-            std::vector<double> xi(1, j->job.xi_dot);
-            int rc = j->eng->step_async(j->slice, &xi, j->ev.data());
-            if (rc == MD_OK && cudaEventRecord(j->done, j->eng->stream()) != cudaSuccess) rc = MD_ECUDA;
             if (rc != MD_OK) {
                 retire(j, rc);
                 continue;
             }
-            j->state = kRunning;
-            progressed = true;
+            // keep kInFlight slices queued: relaxation first, then steps
+            while (j->count < kInFlight && !stop && (j->relax_left > 0 || j->queued_steps < j->job.steps)) {
+                Slice& q = j->sl[(j->head + j->count) % kInFlight];
+                if (j->relax_left > 0) {
+                    q.steps = false;
+                    q.n = std::min(slice_steps, j->relax_left);
+                    rc = j->eng->relax_async(q.n);
+                    j->relax_left -= q.n;
+                } else {
+                    q.steps = true;
+                    q.n = std::min(slice_steps, j->job.steps - j->queued_steps);
+                    std::vector<double> xi(1, j->job.xi_dot);
+                    rc = j->eng->step_async(q.n, &xi, q.ev.data());
+                    j->queued_steps += q.n;
+                }
+                if (rc == MD_OK) rc = j->eng->enqueue_status(q.err);
+                if (rc == MD_OK && cudaEventRecord(q.done, j->eng->stream()) != cudaSuccess) rc = MD_ECUDA;
+                if (rc != MD_OK) break;
+                j->count += 1;
+                progressed = true;
+            }
+            if (rc != MD_OK) {
+                retire(j, rc);
+                continue;
+            }
+            if (j->count == 0) {       // all of its work has completed (or the server stops)
+                const int64_t left = j->job.steps - j->done_steps;
+                retire(j, stop && left > 0 ? MD_ETIMEOUT : MD_OK);
+                continue;
+            }
             keep.push_back(j);
         }
         active.swap(keep);
