@@ -622,6 +622,9 @@ def run_reference(args):
     v = sum(x["value"] for x in vals) / len(vals)
     return {"impl": "reference", "metric": "nucleon-steps/s", "value": v, "unit": "nucleon-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * W["N"] / v,
+            "ms_per_step_note": "projected: the time one whole step of all N nucleons would take at the rate "
+                                "measured on the bounded samples (each sample step times a contiguous range "
+                                "of targets against all N sources, see cpu_baseline.sample); no whole step ran",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": W["desc"], "N": W["N"]},
             "cpu_baseline": {"value": v, "unit": "nucleon-steps/s", "cores": vals[0]["cores"], "kind": "oracle",

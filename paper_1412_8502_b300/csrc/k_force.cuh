@@ -5,22 +5,29 @@
 // Split precision: every pair is evaluated once and its force applied to
 // both particles (Newton's third law; the paper's GPU kernel instead sums
 // every target over all its sources, Sec. II.B.1).  Work unit: one warp per
-// 32-particle target tile I.  The warp first evaluates the tile with itself,
-// then walks I's half tile-pair list (each unordered tile pair is listed
-// once); for each source tile J every lane loads one source, moves it to the
-// periodic image next to I, and tests it against I's box (cutoff + skin/2
-// covers the drift since the rebuild).  Sources that pass are compacted
-// (ballot + popc) into shared-memory queues, one per pair class:
-// proton-proton with the nuclear term (PPN), proton-proton Coulomb only
-// (PPC), unlike species (nuclear, b - c) and like species (nuclear, b + c).
-// A queue holding 32 sources is evaluated as a rotated block: at step k lane
-// l pairs its target with source (l + k) mod 32, keeps the target's force in
-// registers and passes the reaction on the source one lane down, so that
-// after 32 steps each lane holds the full reaction on one source.  Target
-// sums are Kahan-compensated over blocks.  All force contributions go to
-// per-particle 64-bit fixed-point accumulators (2^-32 MeV/fm) with integer
-// atomics, so the result does not depend on their order; a second kernel
-// turns them into FP32 forces and clears them.
+// work item, a part of a 32-particle target tile I's half tile-pair list
+// (each unordered tile pair is listed once): a proton tile gives four items
+// (its near entries with the tile itself, and three parts of its Coulomb-only
+// entries), a neutron tile one; the four warps of a block take the same part
+// of four adjacent tiles.  The item with the near entries first evaluates the
+// tile with itself (broadcast sources, no reaction).  For each listed source
+// tile J every lane loads one source (cp.async, two entries in flight), moves
+// it to the periodic image next to I, and tests it against two boxes around
+// the current positions of I's targets 0-15 and 16-31 with the bare cutoffs.
+// Sources that pass are compacted (ballot + popc) into shared-memory queues,
+// one per pair class: proton-proton with the nuclear term (PPN), proton-
+// proton Coulomb only (PPC), unlike species (nuclear, b - c) and like species
+// (nuclear, b + c).  A queue holding 32 sources is evaluated as a rotated
+// block: lanes l and l ^ 16 hold the same two targets (j = l mod 16 and
+// j + 16), the half-warps take 16 sources each, and at step k lane l pairs
+// both targets with source (l + k) mod 16 of its half and passes the running
+// reaction on that source one lane on with a shuffle; after 16 steps each
+// lane holds the whole reaction on one source.  Target sums are plain FP32
+// sums of the block partials (energies Kahan-compensated).  All force
+// contributions go to per-particle 64-bit fixed-point accumulators
+// (2^-32 MeV/fm) with integer atomics, so the result does not depend on their
+// order; the closing kick (or k_force_fix) turns them into FP32 forces and
+// clears them.
 //
 // Precision: positions are FP32 pairs hi + lo of the image nearest the tile
 // origin (hi rounded to 24 bits, lo the rounded remainder: 48 significant
