@@ -292,20 +292,52 @@ void orc_clusters(int64_t N, const double* x, const int8_t* type, double L,
     for (int64_t a = 0; a < Np; ++a) parent[a] = a;
 
     const double rpp2 = r_pp * r_pp, rnp2 = r_np * r_np;
-    for (int64_t a = 0; a < Np; ++a)
-        for (int64_t b = a + 1; b < Np; ++b)
-            if (cl_d2(&x[3 * pidx[a]], &x[3 * pidx[b]], L) < rpp2) {
-                int64_t ra = uf_find(parent, a), rb = uf_find(parent, b);
-                if (ra != rb) {
-                    if (ra < rb) parent[rb] = ra;
-                    else parent[ra] = rb;
+    /* The edges (proton pairs closer than r_pp) are found by all threads,
+     * each proton a testing every b > a into a buffer of its thread; the
+     * clusters are the connected components of these edges, joined
+     * afterwards in one thread (the components do not depend on the order
+     * the edges are joined in). */
+    int64_t* edges = NULL;
+    int64_t nedges = 0;
+    #pragma omp parallel
+    {
+        int64_t* buf = NULL;
+        int64_t n = 0, cap = 0;
+        #pragma omp for schedule(dynamic, 64)
+        for (int64_t a = 0; a < Np; ++a)
+            for (int64_t b = a + 1; b < Np; ++b)
+                if (cl_d2(&x[3 * pidx[a]], &x[3 * pidx[b]], L) < rpp2) {
+                    if (n == cap) {
+                        cap = cap ? 2 * cap : 1024;
+                        buf = (int64_t*)realloc(buf, (size_t)(2 * cap) * sizeof(int64_t));
+                    }
+                    buf[2 * n] = a;
+                    buf[2 * n + 1] = b;
+                    n++;
                 }
-            }
+        #pragma omp critical
+        {
+            edges = (int64_t*)realloc(edges, (size_t)(2 * (nedges + n) + 2) * sizeof(int64_t));
+            if (n) memcpy(edges + 2 * nedges, buf, (size_t)(2 * n) * sizeof(int64_t));
+            nedges += n;
+        }
+        free(buf);
+    }
+    for (int64_t e = 0; e < nedges; ++e) {
+        int64_t ra = uf_find(parent, edges[2 * e]), rb = uf_find(parent, edges[2 * e + 1]);
+        if (ra != rb) {
+            if (ra < rb) parent[rb] = ra;
+            else parent[ra] = rb;
+        }
+    }
+    free(edges);
     /* The root of each component is its smallest member because roots only
      * ever point to smaller roots. */
     for (int64_t i = 0; i < N; ++i) labels[i] = -1;
     for (int64_t a = 0; a < Np; ++a) labels[pidx[a]] = (int32_t)pidx[uf_find(parent, a)];
 
+    /* each neutron independently (labels of protons are final here) */
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < N; ++i) {
         if (type[i] == 1) continue;
         int64_t best = -1;

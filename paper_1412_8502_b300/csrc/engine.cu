@@ -765,6 +765,7 @@ int Engine::run_graph(GraphRec& g) {
 int Engine::refresh(int only) {
     launch_rebuild(H_, stream_, 1, only);
     launch_force(H_, stream_, false, only, 0);
+    launch_mark_forces(H_, stream_, only);       // the forces' box side is the current one
     CK(cudaGetLastError());
     for (size_t s = 0; s < sys.size(); ++s)
         if (only < 0 || (int)s == only) sys[s]->dirty = false;

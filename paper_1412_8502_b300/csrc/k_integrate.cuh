@@ -550,6 +550,15 @@ __global__ void k_set_clock(EngineDev E, int only, const double* c) {
     st->last_build = st->step;
 }
 
+// The cached forces were just re-evaluated at the current box side (a
+// refresh outside a step): record it as their box side L_F.
+__global__ void k_mark_forces(EngineDev E, int only) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= E.nsys || (only >= 0 && s != only)) return;
+    SysState* st = E.sys[s].st;
+    st->L_F = st->L;
+}
+
 // Re-base Eq. (3) at the current time when the expansion rate changes.
 __global__ void k_set_rate(EngineDev E, int only, double xi) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -625,6 +634,12 @@ void launch_gather(const EngineHost& H, cudaStream_t s, int only, double* ox, do
 void launch_set_clock(const EngineHost& H, cudaStream_t s, int only, const double* d_clock) {
     const EngineDev& E = H.dev;
     k_set_clock<<<(E.nsys + 127) / 128, 128, 0, s>>>(E, only, d_clock);
+    H.count(1);
+}
+
+void launch_mark_forces(const EngineHost& H, cudaStream_t s, int only) {
+    const EngineDev& E = H.dev;
+    k_mark_forces<<<(E.nsys + 127) / 128, 128, 0, s>>>(E, only);
     H.count(1);
 }
 

@@ -74,6 +74,8 @@ void launch_scatter_state(const EngineHost& H, cudaStream_t s, int only, const d
 void launch_scatter_forces(const EngineHost& H, cudaStream_t s, int only, const double* iforce);
 void launch_set_clock(const EngineHost& H, cudaStream_t s, int only, const double* d_clock);
 void launch_set_rate(const EngineHost& H, cudaStream_t s, int only, double xi_dot);
+// After a force re-evaluation outside a step: L_F = L.
+void launch_mark_forces(const EngineHost& H, cudaStream_t s, int only);
 void launch_clusters(const EngineHost& H, cudaStream_t s, int only, int Np, int N, int Tp, int T,
                      int32_t* d_labels_out);
 void launch_mste(const EngineHost& H, cudaStream_t s, int only, int N, int T, int32_t* d_labels_out);

@@ -1,0 +1,83 @@
+"""Full-size parity in the late state of the expansion, where the dynamics
+have formed clusters (Sec. III.B-D): the 51,200- and 409,600-nucleon runs
+taken through their whole 20,000-step schedule (rho 0.080 -> 0.00125 fm^-3,
+Eq. 3), then checked against the FP64 oracle:
+  - cluster labels, size and charge histograms and statistics (Sec. II.C)
+    bit-exact, every 5,000 steps at 51,200 and at the end at 409,600
+    (brute-force oracle over all proton pairs);
+  - forces (Eq. 1) on 2,000 targets drawn at random (half protons, half
+    neutrons) against all N sources, relative L2 <= 1e-5, with each of the
+    three force-pass code variants fixed; the variants' forces are bitwise
+    the same.
+These are the states the device tuner switches the 409,600 run to the
+compact and minimal code for."""
+import numpy as np
+import pytest
+
+import oracle
+from test_gpu_parity import make, oparams, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+XI = 7.5e-5          # c/fm: 0.080 -> 0.00125 fm^-3 over 20,000 steps of 2 fm/c
+
+
+@pytest.fixture(scope="module")
+def md():
+    from paper_1412_8502_b300 import md as m
+    return m
+
+
+def sampled_force_error(s, g, F, n, seed):
+    rng = np.random.default_rng(seed)
+    Np, N = s.Np, s.N
+    idx = np.r_[rng.choice(Np, n // 2, replace=False), Np + rng.choice(N - Np, n - n // 2, replace=False)]
+    order = np.r_[idx, np.setdiff1d(np.arange(N), idx)]     # the sampled targets first
+    Fo, _ = oracle.forces(g["x"][order], g["type"][order], g["L_F"], oparams(s), 0, len(idx))
+    return rel_l2(F[idx], Fo[:len(idx)])
+
+
+def check_clusters(s, g):
+    lab, hA, hZ, st = s.clusters()
+    lo, hAo, hZo, sto = oracle.clusters(g["x"], g["type"], g["L"])
+    assert np.array_equal(lab, lo)
+    assert np.array_equal(hA, hAo) and np.array_equal(hZ, hZo)
+    assert st["n_clusters"] == sto[0] and st["m_free_n"] == sto[1]
+    assert st["A_mean"] == sto[2] and st["Z_mean"] == sto[3] and st["n_big"] == sto[4]
+    return st
+
+
+def variants_match_oracle(md, s, n, seed):
+    Fs = []
+    for fu in (4, 2, 1):
+        p = s.params
+        p.force_unroll = fu
+        s.params = p                 # the next force evaluation uses this code variant only
+        F = s.forces()               # re-evaluated at the current box side
+        g = s.state()                # (its L_F is that box side)
+        err = sampled_force_error(s, g, F, n, seed)
+        assert err <= 1e-5, (fu, err)
+        Fs.append(F)
+    assert np.array_equal(Fs[0], Fs[1]) and np.array_equal(Fs[0], Fs[2])
+
+
+def test_late_state_51200(md):
+    s = make(md, 51200, 0.30, 0.080, T=1.0, seed=2, relax=500)
+    for k in range(4):
+        s.step(5000, XI)
+        st = check_clusters(s, s.state())
+    g = s.state()
+    assert abs(g["L"] / (51200 / 0.00125) ** (1 / 3) - 1.0) < 1e-12      # the end density of Eq. (3)
+    assert st["n_big"] > 50                                               # nuclei have formed
+    variants_match_oracle(md, s, 2000, 7)
+    s.close()
+
+
+def test_late_state_409600(md):
+    s = make(md, 409600, 0.40, 0.080, T=0.5, seed=3, relax=500)
+    s.step(20000, XI)
+    g = s.state()
+    st = check_clusters(s, g)
+    assert st["n_big"] > 300
+    variants_match_oracle(md, s, 2000, 8)
+    s.close()
