@@ -14,11 +14,11 @@
 //   thermostat / affine rescale.
 // Force work items (the work list of (system, tile part) items of all
 // systems) are taken from a device counter in item order, heavy proton items
-// first, four at a time by each group of four warps.  Every barrier wait is bounded by %globaltimer: a wait
-// that exceeds the host-set limit (md_params.wait_limit_ns) raises an
-// error flag, after which every block leaves at its next barrier, and the
-// host reports MD_ETIMEOUT.  The barrier counter is cleared by a memset node
-// before each launch.
+// first, four at a time by each group of four warps.  Every barrier wait is
+// bounded by %globaltimer: a wait that exceeds the host-set limit
+// (md_params.wait_limit_ns) raises an error flag, after which every block
+// leaves at its next barrier, and the host reports MD_ETIMEOUT.  The barrier
+// counter is cleared by a memset node before each launch.
 //
 // Each system's arithmetic is that of the separate kernels, in the same
 // order: a system gives bitwise the same trajectory here as alone.
