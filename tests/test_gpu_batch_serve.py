@@ -119,6 +119,42 @@ def test_persistent_wait_limit_is_an_error_status(md):
     assert e.value.code == md.MD_EINVAL
 
 
+def test_persistent_mode_selection(md):
+    """persistent = -1 (default) runs a batch as one persistent launch per step
+    but falls back to the graph where the persistent step does not apply
+    (per-particle Verlet lists; FP64); persistent = 1 there is MD_EINVAL;
+    a single system defaults to the graph.  Results equal the same systems
+    alone in every case."""
+    p = params(md)
+    p.list_kind = 1
+    p.skin = 4.0
+    b = md.Batch(JOBS[:2], p)                    # falls back: graph of kernels
+    b.step(1)
+    n0 = b.systems[0].info()["launches"]
+    b.step(10)
+    assert b.systems[0].info()["launches"] - n0 > 10
+    a = alone(md, JOBS[0], 11, p)
+    assert np.array_equal(a.state()["x"], b.systems[0].state()["x"])
+    a.close()
+    b.close()
+    p.persistent = 1
+    with pytest.raises(md.MDError) as e:
+        md.Batch(JOBS[:2], p)
+    assert e.value.code == md.MD_EINVAL
+    q = params(md)
+    q.precision = 1
+    q.persistent = 1
+    with pytest.raises(md.MDError) as e:
+        md.Batch(JOBS[:2], q)
+    assert e.value.code == md.MD_EINVAL
+    s = md.System(1500, 0.3, 0.08, 1.0, 3, params(md))       # one system: the graph
+    s.step(1)
+    n0 = s.info()["launches"]
+    s.step(5)
+    assert s.info()["launches"] - n0 > 5
+    s.close()
+
+
 def test_batch_member_matches_oracle(md):
     p = params(md)
     b = md.Batch(JOBS[:3], p)
