@@ -24,6 +24,8 @@
 // order: a system gives bitwise the same trajectory here as alone.
 #pragma once
 
+#include <mutex>
+
 namespace pasta {
 
 constexpr int kPBlock = 256;     // threads per block of the persistent step kernel
@@ -220,8 +222,11 @@ int step_persistent_variant(const EngineHost& H, cudaStream_t s, PersistCtl* ctl
 
 // Dynamic shared memory and occupancy of the persistent step kernel: call
 // outside stream capture before its first launch; 0, or -1 if it cannot run
-// (the CUDA error is left for the caller to read).
+// (the CUDA error is left for the caller to read).  Done once per process, on
+// the device current at the first call (the library drives one device).
 int prepare_step_persistent() {
+    static std::mutex mu;                // engines may be created from several host threads
+    std::lock_guard<std::mutex> lk(mu);
     if (g_persist_blocks[0][0] >= 0) return g_persist_blocks[0][0] > 0 ? 0 : -1;
     int rc = prepare_variant<false, 0>();
     if (!rc) rc = prepare_variant<false, 1>();
