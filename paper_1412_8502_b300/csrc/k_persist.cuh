@@ -30,6 +30,9 @@ namespace pasta {
 
 constexpr int kPBlock = 256;     // threads per block of the persistent step kernel
 constexpr int kPWarps = kPBlock / 32;
+static_assert(kPBlock == kBlock, "the per-tile bodies play blocks of kBlock threads");
+static_assert(kPBlock == kRed, "the per-system reductions (finalisation) use kRed threads");
+static_assert(kPWarps % kForceWarps == 0, "whole groups of force warps per block");
 
 namespace {
 
