@@ -359,8 +359,15 @@ typedef struct {
     int64_t steps;      /* steps the job asks for (server) */
 } md_job;
 
-/* Create n independent systems (md_create semantics per job) advanced by
- * one graph launch per step that covers all of them. */
+/* Create n independent systems (md_create semantics per job; p applies to
+ * all, NULL for the defaults).  md_batch_step advances all of them: with
+ * p->persistent -1 (default) or 1 every step of every system is ONE persistent
+ * cooperative kernel launch (its phases separated by grid barriers bounded by
+ * p->wait_limit_ns; a barrier that gives up makes the step return
+ * MD_ETIMEOUT); with 0, one graph of separate kernels per step.  Each system's
+ * trajectory is bitwise the one it has alone.  Errors: MD_EINVAL (n <= 0, a
+ * job as md_create rejects, persistent = 1 with FP64, Verlet lists or the
+ * all-pairs Coulomb term), MD_ENOMEM, MD_ENODEV, MD_ECUDA. */
 MD_API int md_batch_create(int n, const md_job* jobs, const md_params* p, md_batch** out);
 MD_API int md_batch_step(md_batch* b, int64_t n);
 /* md_autotune for all systems of the batch (one setting shared by all). */
