@@ -17,10 +17,11 @@
  * (particle-major).  type[i] = 1 for a proton, 0 for a neutron.
  *
  * Parity status: every function below is pinned by a CPU test against closed
- * forms, invariants or an independent brute-force implementation, except the
+ * forms, invariants or an independent brute-force implementation.  The
  * steepest-descent relaxation (orc_relax), whose constants are a reading of
- * the paper's "equilibrated from random" start and have no closed form; it is
- * pinned only by the property that it lowers the potential energy.
+ * the paper's "equilibrated from random" start, is pinned by one iteration
+ * on two neutrons computed by hand from Table I (the clamp on the
+ * displacement vector active and inactive) and by the energy decrease.
  */
 #ifndef PASTA_ORACLE_H
 #define PASTA_ORACLE_H
