@@ -183,28 +183,38 @@ __global__ void __launch_bounds__(kPBlock, 2)
 #undef PASTA_BARRIER
 }
 
-// Blocks per SM of each instantiation (0: not possible), set by
-// prepare_step_persistent outside any stream capture.
-int g_persist_blocks[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
+// Blocks per SM of each instantiation (0: not possible; -1: not yet set) per
+// device, set by prepare_step_persistent outside any stream capture with the
+// device current (function attributes belong to a device's context).
+constexpr int kMaxDev = 64;
+int g_persist_blocks[kMaxDev][2][3];
+bool g_persist_init = false;
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return -1;
+    return dev;
+}
 
 template <bool kEnergy, int kVar>
-int prepare_variant() {
+int prepare_variant(int dev) {
     auto kern = k_step_persistent<kEnergy, kVar>;
     const size_t dsm = sizeof(WarpQueues) * kPWarps;
     int nb = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kPBlock, dsm) != cudaSuccess)
         return -1;
-    g_persist_blocks[kEnergy ? 1 : 0][kVar] = nb;
+    g_persist_blocks[dev][kEnergy ? 1 : 0][kVar] = nb;
     return nb > 0 ? 0 : -1;
 }
 
 template <bool kEnergy, int kVar>
 int step_persistent_variant(const EngineHost& H, cudaStream_t s, PersistCtl* ctl, unsigned long long limit_ns) {
-    const int bps = g_persist_blocks[kEnergy ? 1 : 0][kVar];
+    const int dev = current_device();
+    if (dev < 0) return -1;
+    const int bps = g_persist_blocks[dev][kEnergy ? 1 : 0][kVar];
     if (bps < 1) return -1;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(std::min(bps, 2) * sms));
@@ -225,18 +235,26 @@ int step_persistent_variant(const EngineHost& H, cudaStream_t s, PersistCtl* ctl
 
 // Dynamic shared memory and occupancy of the persistent step kernel: call
 // outside stream capture before its first launch; 0, or -1 if it cannot run
-// (the CUDA error is left for the caller to read).  Done once per process, on
-// the device current at the first call (the library drives one device).
+// (the CUDA error is left for the caller to read).  Done once per device, for
+// the device current at the call.
 int prepare_step_persistent() {
     static std::mutex mu;                // engines may be created from several host threads
     std::lock_guard<std::mutex> lk(mu);
-    if (g_persist_blocks[0][0] >= 0) return g_persist_blocks[0][0] > 0 ? 0 : -1;
-    int rc = prepare_variant<false, 0>();
-    if (!rc) rc = prepare_variant<false, 1>();
-    if (!rc) rc = prepare_variant<false, 2>();
-    if (!rc) rc = prepare_variant<true, 0>();
-    if (!rc) rc = prepare_variant<true, 1>();
-    if (!rc) rc = prepare_variant<true, 2>();
+    if (!g_persist_init) {
+        for (auto& d : g_persist_blocks)
+            for (auto& e : d)
+                for (int& v : e) v = -1;
+        g_persist_init = true;
+    }
+    const int dev = current_device();
+    if (dev < 0) return -1;
+    if (g_persist_blocks[dev][0][0] >= 0) return g_persist_blocks[dev][0][0] > 0 ? 0 : -1;
+    int rc = prepare_variant<false, 0>(dev);
+    if (!rc) rc = prepare_variant<false, 1>(dev);
+    if (!rc) rc = prepare_variant<false, 2>(dev);
+    if (!rc) rc = prepare_variant<true, 0>(dev);
+    if (!rc) rc = prepare_variant<true, 1>(dev);
+    if (!rc) rc = prepare_variant<true, 2>(dev);
     return rc;
 }
 
