@@ -142,7 +142,7 @@ def force_pipes():
     if d.get("k_force_sha") != sha:
         return None
     keys = ("issue_active", "fma_pipe_active", "alu_pipe_active", "lsu_pipe_active", "xu_pipe_active",
-            "fp64_pipe_active")
+            "fp64_pipe_active", "thread_inst_per_candidate", "thread_inst_per_in_range_pair")
     out = {k: d[k] for k in keys if k in d}
     out["source"] = "ncu, " + d.get("workload", "")
     return out
