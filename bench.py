@@ -548,6 +548,10 @@ def run_full(args):
         p.precision = md.MD_PREC_FP64
     if args.force_unroll is not None:
         p.force_unroll = args.force_unroll
+    if args.sort_bits is not None:
+        p.sort_bits = args.sort_bits
+    if args.skin is not None:
+        p.skin = args.skin
     s = md.System(N, W["Yp"], W["rho"], W["T"], W["seed"], p)
     stream = torch.cuda.Stream()
     s.set_stream(stream)
