@@ -185,6 +185,11 @@ __global__ void k_decide(EngineDev E, int forced_only, int only, cudaGraphCondit
 }
 
 // ---------------------------------------------------------------- histogram
+// Bins of kScanChunk consecutive global bins form the chunks of the bin scan.
+constexpr int kScanPer = 8;
+constexpr int kScanChunk = 1024 * kScanPer;
+
+// Key and bin count of every particle of a rebuilding system.
 __device__ __forceinline__ void hist_body(const EngineDev& E, int bx) {
     if (!*E.any_rebuild) return;
     const int g = bx * kTilesPerBlock + (threadIdx.x >> 5);
@@ -208,9 +213,11 @@ __device__ __forceinline__ void hist_body(const EngineDev& E, int bx) {
 __global__ void k_hist(EngineDev E) { hist_body(E, blockIdx.x); }
 
 // ---------------------------------------------------------------- bin scan
-// Three-pass exclusive scan of hist over all systems' bins (8192 per block).
-constexpr int kScanPer = 8;
-constexpr int kScanChunk = 1024 * kScanPer;
+// Exclusive scan of hist over all systems' bins in two passes: the count of
+// each chunk of kScanChunk bins (k_scan_reduce), then each chunk scanned by a
+// block of 1024 threads from the sum of the counts of the chunks before it
+// (k_scan_bins).  Exact integer sums: the result is that of any other order
+// of summation.
 
 static_assert(kScanPer == 8, "a thread's bins are two 16-byte vectors");
 
@@ -249,34 +256,25 @@ __global__ void k_scan_reduce(EngineDev E) {
     if (threadIdx.x == 0) E.blocksum[blockIdx.x] = tot;
 }
 
-__device__ __forceinline__ void scan_top_body(const EngineDev& E, int nblk) {
-    if (!*E.any_rebuild) return;
-    __shared__ unsigned sm[33];
-    const int per = (nblk + blockDim.x - 1) / blockDim.x;
-    const int b0 = threadIdx.x * per;
-    unsigned s = 0;
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < nblk) s += E.blocksum[b0 + k];
-    unsigned run = block_exscan(s, sm, nullptr);
-    for (int k = 0; k < per; ++k)
-        if (b0 + k < nblk) {
-            unsigned v = E.blocksum[b0 + k];
-            E.blocksum[b0 + k] = run;
-            run += v;
-        }
+// Sum of the chunk counts before chunk vb, in every thread of the block.
+__device__ __forceinline__ unsigned chunk_offset(const EngineDev& E, int vb, unsigned* sm) {
+    unsigned o = 0;
+    for (int c = threadIdx.x; c < vb; c += blockDim.x) o += E.blocksum[c];
+    unsigned tot;
+    block_exscan(o, sm, &tot);
+    return tot;
 }
 
-__global__ void k_scan_top(EngineDev E, int nblk) { scan_top_body(E, nblk); }
-
-__global__ void k_scan_down(EngineDev E) {
+__global__ void k_scan_bins(EngineDev E) {
     if (!*E.any_rebuild) return;
     __shared__ unsigned sm[33];
+    const unsigned off = chunk_offset(E, blockIdx.x, sm);
     const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
     unsigned v[kScanPer];
     load8(E.hist, base, E.nbins_total, v);
     unsigned s = 0;
     for (int k = 0; k < kScanPer; ++k) s += v[k];
-    unsigned run = block_exscan(s, sm, nullptr) + E.blocksum[blockIdx.x];
+    unsigned run = block_exscan(s, sm, nullptr) + off;
     unsigned o[kScanPer];
     for (int k = 0; k < kScanPer; ++k) {
         o[k] = run;
@@ -899,15 +897,14 @@ void launch_cell_build(const EngineHost& H, cudaStream_t s, bool rec) {
     k_hist<<<nb, kBlock, 0, s>>>(E);
     if (rec) H.rec("scan", s);
     k_scan_reduce<<<nscan, 1024, 0, s>>>(E);
-    k_scan_top<<<1, 1024, 0, s>>>(E, nscan);
-    k_scan_down<<<nscan, 1024, 0, s>>>(E);
+    k_scan_bins<<<nscan, 1024, 0, s>>>(E);
     if (rec) H.rec("scatter", s);
     k_scatter<<<nb, kBlock, 0, s>>>(E);
     if (rec) H.rec("move", s);
     k_move<<<nb, kBlock, 0, s>>>(E);
     if (rec) H.rec("tiles", s);
     k_tiles<<<nb, kBlock, 0, s>>>(E);
-    H.count(7);
+    H.count(6);
 }
 
 // Super-tile boxes and tile-pair lists (+ per-particle Verlet lists).

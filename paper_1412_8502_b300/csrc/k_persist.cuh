@@ -7,7 +7,7 @@
 // a step in order, each phase spread over them (the same device code as the
 // separate kernels, each block playing the blocks of the separate launch in
 // turn), with a grid-wide barrier between phases:
-//   kick-drift | rebuild decision | [cell build: histogram, bin scan (three
+//   kick-drift | rebuild decision | [cell build: histogram, bin scan (two
 //   passes), scatter, move, tiles | lists: super-tiles, tile-pair lists]
 //   (only when some system rebuilds) | pair forces | closing kick with the
 //   force conversion | finalisation (clock, box, thermostat, energies) |
@@ -75,7 +75,8 @@ __device__ __forceinline__ bool grid_barrier(PersistCtl* ctl, unsigned& target, 
 }
 
 // The bin scan for 256-thread blocks: chunks of kScanChunk bins (as the
-// 1024-thread kernels), 32 bins per thread.  Exact integer prefix sums: the
+// 1024-thread kernels), 32 bins per thread; the chunk counts, then each chunk
+// from the sum of the counts before it.  Exact integer prefix sums: the
 // result does not depend on the chunking.
 constexpr int kPScanPer = kScanChunk / kPBlock;
 static_assert(kPScanPer % kScanPer == 0, "whole groups of 8 bins per thread");
@@ -95,8 +96,9 @@ __device__ __forceinline__ void pscan_reduce(const EngineDev& E, int vb) {
     if (threadIdx.x == 0) E.blocksum[vb] = tot;
 }
 
-__device__ __forceinline__ void pscan_down(const EngineDev& E, int vb) {
+__device__ __forceinline__ void pscan_bins(const EngineDev& E, int vb) {
     __shared__ unsigned sm[33];
+    const unsigned off = chunk_offset(E, vb, sm);
     const long long base = (long long)vb * kScanChunk + threadIdx.x * kPScanPer;
     unsigned v[kPScanPer / kScanPer][kScanPer];
     unsigned s = 0;
@@ -105,7 +107,7 @@ __device__ __forceinline__ void pscan_down(const EngineDev& E, int vb) {
         load8(E.hist, base + q * kScanPer, E.nbins_total, v[q]);
         for (int k = 0; k < kScanPer; ++k) s += v[q][k];
     }
-    unsigned run = block_exscan(s, sm, nullptr) + E.blocksum[vb];
+    unsigned run = block_exscan(s, sm, nullptr) + off;
 #pragma unroll
     for (int q = 0; q < kPScanPer / kScanPer; ++q) {
         unsigned o[kScanPer];
@@ -144,9 +146,7 @@ __global__ void __launch_bounds__(kPBlock, 2)
         PASTA_BARRIER();
         for (int b = b0; b < nscan; b += G) pscan_reduce(E, b);
         PASTA_BARRIER();
-        if (b0 == 0) scan_top_body(E, nscan);
-        PASTA_BARRIER();
-        for (int b = b0; b < nscan; b += G) pscan_down(E, b);
+        for (int b = b0; b < nscan; b += G) pscan_bins(E, b);
         PASTA_BARRIER();
         for (int b = b0; b < nb; b += G) scatter_body(E, b);
         PASTA_BARRIER();
