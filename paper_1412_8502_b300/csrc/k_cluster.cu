@@ -95,13 +95,26 @@ __device__ inline Frame frame_of(const SysState* st) {
     return f;
 }
 
-// Stage source tile J (moved to the image next to tile I) for this lane.
-__device__ inline void stage_src(const SysConst& S, int I, int J, int lane, const Frame& F, float4& h, float4& l) {
-    h = S.xhi[J * kTile + lane];
-    l = S.xlo[J * kTile + lane];
-    const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
-    const float4 oJ = *reinterpret_cast<const float4*>(&S.torgf[4 * J]);
-    const float s[3] = {rintf((oI.x - oJ.x) * F.iL), rintf((oI.y - oJ.y) * F.iL), rintf((oI.z - oJ.z) * F.iL)};
+// Source data of tile J for this lane, loaded ahead of its use (the loads of
+// the next list entry are in flight while the current one is evaluated).
+struct SrcLoad {
+    float4 h, l, oJ;
+};
+
+__device__ __forceinline__ SrcLoad load_src(const SysConst& S, int J, int lane) {
+    SrcLoad r;
+    r.h = S.xhi[J * kTile + lane];
+    r.l = S.xlo[J * kTile + lane];
+    r.oJ = *reinterpret_cast<const float4*>(&S.torgf[4 * J]);
+    return r;
+}
+
+// The loaded source moved to the image next to tile I (origin oI): an
+// error-free two-sum on the hi + lo pair.
+__device__ inline void shift_src(const SrcLoad& r, const float4& oI, const Frame& F, float4& h, float4& l) {
+    h = r.h;
+    l = r.l;
+    const float s[3] = {rintf((oI.x - r.oJ.x) * F.iL), rintf((oI.y - r.oJ.y) * F.iL), rintf((oI.z - r.oJ.z) * F.iL)};
     float* hp = &h.x;
     float* lp = &l.x;
     for (int a = 0; a < 3; ++a) {
@@ -114,6 +127,43 @@ __device__ inline void stage_src(const SysConst& S, int I, int J, int lane, cons
             lp[a] = lp[a] + s[a] * F.Llo + e;
         }
     }
+}
+
+// Bounding box of the warp's valid targets (FP32 high parts) and the test
+// of a source against it: a source farther than the reach from the box has
+// no pair inside the cutoff with any target, so it is not queued.  The high
+// parts are within 2^-24 |x| (< 1e-4 fm below 1000 fm) of the positions,
+// far inside the reach margin kReachMargin.
+struct WBox {
+    float cx, cy, cz, hx, hy, hz;
+};
+constexpr float kReachMargin = 0.01f;   // fm
+
+__device__ inline WBox warp_box(const float4& hi, bool valid) {
+    float mn[3] = {valid ? hi.x : INFINITY, valid ? hi.y : INFINITY, valid ? hi.z : INFINITY};
+    float mx[3] = {valid ? hi.x : -INFINITY, valid ? hi.y : -INFINITY, valid ? hi.z : -INFINITY};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    WBox b;
+    b.cx = 0.5f * (mn[0] + mx[0]);
+    b.cy = 0.5f * (mn[1] + mx[1]);
+    b.cz = 0.5f * (mn[2] + mx[2]);
+    b.hx = 0.5f * (mx[0] - mn[0]);
+    b.hy = 0.5f * (mx[1] - mn[1]);
+    b.hz = 0.5f * (mx[2] - mn[2]);
+    return b;
+}
+
+__device__ __forceinline__ bool near_box(const WBox& b, const float4& q, float reach2) {
+    const float gx = fmaxf(fabsf(q.x - b.cx) - b.hx, 0.0f);
+    const float gy = fmaxf(fabsf(q.y - b.cy) - b.hy, 0.0f);
+    const float gz = fmaxf(fabsf(q.z - b.cz) - b.hz, 0.0f);
+    return fmaf(gz, gz, fmaf(gy, gy, gx * gx)) < reach2;
 }
 
 __device__ inline float d2_screen(const float4& hi, const float4& lo, const float4& q, const float4& u,
@@ -148,9 +198,31 @@ __global__ void k_cl_init(EngineDev E, int only) {
     if (i < 8) B.stats[i] = 0;
 }
 
-// Warp per proton tile: link proton pairs closer than r_pp.
+// Warp per proton tile: proton pairs closer than r_pp.  Each unordered pair
+// is found once, from the tile of its smaller slot (source tiles J < I hold
+// no such pair and are skipped; the lists are in increasing J).  The pairs
+// found collect in a per-warp shared buffer that is appended to the edge
+// buffer with one atomic per flush, and k_cl_union unites them, one thread
+// per edge; a pair beyond the edge buffer's capacity is united here.
+constexpr int kEB = 96;   // per-warp shared edge buffer (a flush leaves room for a full warp)
+
+__device__ __forceinline__ void flush_edges(const ClusterBufs& B, const SysConst& S, int2* buf, int& ne, int lane) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(&B.stats[6]), (unsigned long long)ne);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int i = lane; i < ne; i += 32) {
+        const int2 ed = buf[i];
+        if (base + i < (unsigned long long)B.ecap) B.edges[base + i] = ed;
+        else uf_union(B.parent, ed.x, ed.y, S.uf_limit, &B.stats[7]);
+    }
+    __syncwarp();
+    ne = 0;
+}
+
 __global__ void k_cl_link(EngineDev E, int only) {
     __shared__ float4 sh[kCW][kTile], sl[kCW][kTile];
+    __shared__ int sq[kCW][kTile];
+    __shared__ int2 sedge[kCW][kEB];
     const SysConst& S = E.sys[only];
     const ClusterBufs& B = *S.cl;
     const int I = blockIdx.x * kCW + (threadIdx.x >> 5);
@@ -165,38 +237,82 @@ __global__ void k_cl_link(EngineDev E, int only) {
     const int p = I * kTile + lane;
     const bool valid = p < S.Np;
     const float4 hi = S.xhi[I * kTile + lane], lo = S.xlo[I * kTile + lane];
-    for (int e = B.start[I]; e < B.start[I + 1]; ++e) {
-        const int J = B.list[e];
-        float4 h, l;
-        stage_src(S, I, J, lane, F, h, l);
-        __syncwarp();
-        sh[w][lane] = h;
-        sl[w][lane] = l;
-        __syncwarp();
-        if (!valid) continue;
-        const int nq = min(kTile, S.Np - J * kTile);
-        for (int k = 0; k < nq; ++k) {
-            const int qq = J * kTile + k;
-            if (qq <= p) continue;
-            const float d2 = d2_screen(hi, lo, sh[w][k], sl[w][k], F);
-            if (d2 >= hi2) continue;
-            bool link = d2 < lo2;
-            if (!link)
-                link = d2_exact(x[p], x[N + p], x[2 * N + p], x[qq], x[N + qq], x[2 * N + qq], L, hL) < r2c;
-            if (link) uf_union(B.parent, p, qq, S.uf_limit, &B.stats[7]);
+    const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
+    const WBox box = warp_box(hi, valid);
+    const float reach = sqrtf(hi2) + kReachMargin, reach2 = reach * reach;
+    int2* buf = sedge[w];
+    int ne = 0;
+    const int e1 = B.start[I + 1];
+    int e = B.start[I];
+    while (e < e1 && B.list[e] < I) ++e;
+    int Jn = e < e1 ? B.list[e] : 0;
+    SrcLoad nx;
+    if (e < e1) nx = load_src(S, Jn, lane);
+    while (e < e1) {
+        const int J = Jn;
+        const SrcLoad cur = nx;
+        if (++e < e1) {
+            Jn = B.list[e];
+            nx = load_src(S, Jn, lane);
         }
+        float4 h, l;
+        shift_src(cur, oI, F, h, l);
+        const int q = J * kTile + lane;
+        const bool pass = q < S.Np && (F.wrap || near_box(box, h, reach2));
+        const unsigned mp = __ballot_sync(0xffffffffu, pass);
+        if (!mp) continue;
+        __syncwarp();
+        if (pass) {
+            const int at = __popc(mp & ((1u << lane) - 1u));
+            sh[w][at] = h;
+            sl[w][at] = l;
+            sq[w][at] = q;
+        }
+        __syncwarp();
+        const int nq = __popc(mp);
+        for (int k = 0; k < nq; ++k) {
+            const int qq = sq[w][k];
+            bool link = false;
+            if (valid && qq > p) {
+                const float d2 = d2_screen(hi, lo, sh[w][k], sl[w][k], F);
+                link = d2 < lo2;
+                if (!link && d2 < hi2)
+                    link = d2_exact(x[p], x[N + p], x[2 * N + p], x[qq], x[N + qq], x[2 * N + qq], L, hL) < r2c;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, link);
+            if (!m) continue;
+            if (ne + 32 > kEB) flush_edges(B, S, buf, ne, lane);
+            if (link) buf[ne + __popc(m & ((1u << lane) - 1u))] = make_int2(p, qq);
+            __syncwarp();
+            ne += __popc(m);
+        }
+    }
+    if (ne) flush_edges(B, S, buf, ne, lane);
+}
+
+// One thread per buffered link: unite its two protons.
+__global__ void k_cl_union(EngineDev E, int only) {
+    const SysConst& S = E.sys[only];
+    const ClusterBufs& B = *S.cl;
+    const long long n = min((long long)B.stats[6], B.ecap);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int2 ed = B.edges[i];
+        uf_union(B.parent, ed.x, ed.y, S.uf_limit, &B.stats[7]);
     }
 }
 
-// Smallest original index per component.  Lanes of a warp with the same
-// root combine first (one atomic per root and warp: a large cluster would
-// otherwise serialise every proton's atomic on one address).
+// Smallest original index per component (and each proton pointed at its
+// root).  Lanes of a warp with the same root combine first (one atomic per
+// root and warp: a large cluster would otherwise serialise every proton's
+// atomic on one address).
 __global__ void k_cl_minid(EngineDev E, int only) {
     const SysConst& S = E.sys[only];
     const ClusterBufs& B = *S.cl;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const bool ok = q < S.Np;
     const int r = ok ? uf_find(B.parent, q, S.uf_limit, &B.stats[7]) : -1 - (int)(threadIdx.x & 31);
+    // the links are all united: point q at its root, so later finds take one step
+    if (ok && r != q) B.parent[q] = r;
     int id = ok ? S.id[S.st->cur][q] : 0x7fffffff;
     const unsigned same = __match_any_sync(0xffffffffu, r);
     const int lane = threadIdx.x & 31;
@@ -207,7 +323,7 @@ __global__ void k_cl_minid(EngineDev E, int only) {
 // Proton labels; neutron assignment (warp per neutron tile).
 __global__ void k_cl_assign(EngineDev E, int only) {
     __shared__ float4 sh[kCW][kTile], sl[kCW][kTile];
-    __shared__ int sid[kCW][kTile];
+    __shared__ int sid[kCW][kTile], sq[kCW][kTile];
     const SysConst& S = E.sys[only];
     const ClusterBufs& B = *S.cl;
     const int I = blockIdx.x * kCW + (threadIdx.x >> 5);
@@ -226,34 +342,67 @@ __global__ void k_cl_assign(EngineDev E, int only) {
     const double L = st->L, hL = 0.5 * L, r2c = S.r_np * S.r_np;
     const float hi2 = (float)r2c + kBand;
     const float4 hi = S.xhi[I * kTile + lane], lo = S.xlo[I * kTile + lane];
+    const float4 oI = *reinterpret_cast<const float4*>(&S.torgf[4 * I]);
     const double xi = valid ? x[p] : 0, yi = valid ? x[N + p] : 0, zi = valid ? x[2 * N + p] : 0;
+    const WBox box = warp_box(hi, valid);
+    const float reach = sqrtf(hi2) + kReachMargin, reach2 = reach * reach;
+    // The nearest candidate by the exact rule (FP64 squared distance, then the
+    // smaller original index), with the FP64 distance evaluated only where the
+    // FP32 screen cannot decide: the screened value is within a few ulp of
+    // the FP64 one, far inside kBand, so a candidate more than kBand below
+    // (above) the best is nearer (farther) in FP64 as well.  The best is the
+    // exact minimum of the candidates; if it lies beyond r_np, so do all.
+    float best_f = 0.0f;
     double best_d2 = 0.0;
+    bool best_exact = false;
     int best_id = -1, best_slot = -1;
     for (int e = B.start[I]; e < B.start[I + 1]; ++e) {
         const int J = B.list[e];
         float4 h, l;
-        stage_src(S, I, J, lane, F, h, l);
+        shift_src(load_src(S, J, lane), oI, F, h, l);
         const int q = J * kTile + lane;
+        const bool pass = q < S.Np && (F.wrap || near_box(box, h, reach2));
+        const unsigned mp = __ballot_sync(0xffffffffu, pass);
+        if (!mp) continue;
         __syncwarp();
-        sh[w][lane] = h;
-        sl[w][lane] = l;
-        sid[w][lane] = q < S.Np ? S.id[c][q] : 0;
+        if (pass) {
+            const int at = __popc(mp & ((1u << lane) - 1u));
+            sh[w][at] = h;
+            sl[w][at] = l;
+            sid[w][at] = S.id[c][q];
+            sq[w][at] = q;
+        }
         __syncwarp();
         if (!valid) continue;
-        const int nq = min(kTile, S.Np - J * kTile);
+        const int nq = __popc(mp);
         for (int k = 0; k < nq; ++k) {
-            if (d2_screen(hi, lo, sh[w][k], sl[w][k], F) >= hi2) continue;
-            const int qq = J * kTile + k;
-            const double d2 = d2_exact(xi, yi, zi, x[qq], x[N + qq], x[2 * N + qq], L, hL);
-            if (d2 < r2c) {
-                const int oid = sid[w][k];
-                if (best_id < 0 || d2 < best_d2 || (d2 == best_d2 && oid < best_id)) {
+            const float d2f = d2_screen(hi, lo, sh[w][k], sl[w][k], F);
+            if (d2f >= hi2) continue;
+            const int qq = sq[w][k];
+            const int oid = sid[w][k];
+            if (best_slot < 0 || d2f < best_f - kBand) {
+                best_f = d2f;
+                best_exact = false;
+                best_id = oid;
+                best_slot = qq;
+            } else if (d2f <= best_f + kBand) {
+                const double d2 = d2_exact(xi, yi, zi, x[qq], x[N + qq], x[2 * N + qq], L, hL);
+                if (!best_exact) {
+                    best_d2 = d2_exact(xi, yi, zi, x[best_slot], x[N + best_slot], x[2 * N + best_slot], L, hL);
+                    best_exact = true;
+                }
+                if (d2 < best_d2 || (d2 == best_d2 && oid < best_id)) {
+                    best_f = d2f;
                     best_d2 = d2;
                     best_id = oid;
                     best_slot = qq;
                 }
             }
         }
+    }
+    if (best_slot >= 0 && best_f >= (float)r2c - kBand) {
+        if (!best_exact) best_d2 = d2_exact(xi, yi, zi, x[best_slot], x[N + best_slot], x[2 * N + best_slot], L, hL);
+        if (!(best_d2 < r2c)) best_slot = -1;
     }
     if (valid) B.label[p] = best_slot < 0 ? -1 : B.minid[uf_find(B.parent, best_slot, S.uf_limit, &B.stats[7])];
 }
@@ -520,7 +669,10 @@ void launch_clusters(const EngineHost& H, cudaStream_t s, int only, int Np, int 
     H.rec("cl_init", s);
     k_cl_init<<<n1, 256, 0, s>>>(E, only);
     H.rec("cl_link", s);
-    if (Tp > 0) k_cl_link<<<(Tp + kCW - 1) / kCW, kCW * 32, 0, s>>>(E, only);
+    if (Tp > 0) {
+        k_cl_link<<<(Tp + kCW - 1) / kCW, kCW * 32, 0, s>>>(E, only);
+        k_cl_union<<<std::min((Np + 255) / 256, 148 * 16), 256, 0, s>>>(E, only);
+    }
     H.rec("cl_minid", s);
     if (Np > 0) k_cl_minid<<<(Np + 255) / 256, 256, 0, s>>>(E, only);
     H.rec("cl_assign", s);
@@ -529,7 +681,7 @@ void launch_clusters(const EngineHost& H, cudaStream_t s, int only, int Np, int 
     k_cl_count<<<(N + 255) / 256, 256, 0, s>>>(E, only);
     H.rec("cl_hist", s);
     k_cl_hist<<<(N + 255) / 256, 256, 0, s>>>(E, only, d_labels_out);
-    H.count(6);
+    H.count(Tp > 0 ? 7 : 4);
 }
 
 }  // namespace pasta
