@@ -231,8 +231,10 @@ def run_gpu(args):
     sys_.set_timing(False)
 
     # energy-criterion (MSTE) clusters of the final state, timed on their own
+    # (after one untimed call: the first launch of a kernel loads its code)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
+        sys_.clusters_mste(labels=False)
         flush.zero_()
         ev0.record(stream)
         _, _, _, mst = sys_.clusters_mste(labels=False)
@@ -240,7 +242,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     mste = {"ms": ev0.elapsed_time(ev1), "n_clusters": mst["n_clusters"], "n_big": mst["n_big"],
             "m_free_n": mst["m_free_n"], "distance_clusters_n_big": cst["n_big"],
-            "note": "outside the timed region; bound when V_ij + (M/4)|v_i - v_j|^2 < 0"}
+            "note": "outside the timed region, second call; bound when V_ij + (M/4)|v_i - v_j|^2 < 0"}
 
     # end to end through the public API with pinned host buffers
     e2e = None

@@ -947,10 +947,11 @@ int Engine::ensure_cluster_bufs(SysHost& h, long long need) {
         A(&B.count, (size_t)h.T);
         A(&B.start, (size_t)h.T + 1);
         A(&B.total, 1);
-        // links of the distance clusters: about 6 per proton in the dense start,
-        // 12 inside nuclei at saturation density; beyond the capacity the link
-        // pass unites the pair itself
-        B.ecap = std::max<long long>(16 * (long long)h.Np, 1024);
+        // links: about 6 per proton for the distance clusters in the dense
+        // start, 12 inside nuclei at saturation density (the energy-criterion
+        // clusters link all species); beyond the capacity the link pass unites
+        // the pair itself
+        B.ecap = std::max<long long>(16 * (long long)h.N, 1024);
         A(&B.edges, (size_t)B.ecap);
         if (rc) return rc;
         h.cl_ready = true;

@@ -509,11 +509,17 @@ __global__ void k_ms_init(EngineDev E, int only) {
     if (i < 8) B.stats[i] = 0;
 }
 
-// Warp per tile: union of every bound pair (i in I, j in I or a near entry).
+// Warp per tile: every bound pair (i in I, j in I or a near entry).  Each
+// source is queued only when it lies within the nuclear range of the box of
+// the warp's targets (pairs beyond it are not bound: V >= 0 there); the bound
+// pairs go to the edge buffer (united afterwards by k_cl_union, one thread
+// per edge; beyond its capacity they are united here).
 // half: the force lists hold each tile pair once and leave the tile itself
 // out (split precision, tile lists); otherwise they are full.
 __global__ void k_ms_link(EngineDev E, int only, int prec) {
     __shared__ float4 sh[kCW][kTile], sl[kCW][kTile], sv[kCW][kTile];
+    __shared__ int sq[kCW][kTile];
+    __shared__ int2 sedge[kCW][kEB];
     const SysConst& S = E.sys[only];
     const ClusterBufs& B = *S.cl;
     const int I = blockIdx.x * kCW + (threadIdx.x >> 5);
@@ -534,6 +540,10 @@ __global__ void k_ms_link(EngineDev E, int only, int prec) {
     const bool Ip = I < S.Tp;
     const float4 hi = S.xhi[I * kTile + lane], lo = S.xlo[I * kTile + lane];
     const float vx = valid ? (float)v[p] : 0.f, vy = valid ? (float)v[N + p] : 0.f, vz = valid ? (float)v[2 * N + p] : 0.f;
+    const WBox box = warp_box(hi, valid);
+    const float reach = sqrtf(far2) + kReachMargin, reach2 = reach * reach;
+    int2* buf = sedge[w];
+    int ne = 0;
     const int* lst = S.list + (long long)I * S.T;
     const int nnear = S.lnear[I];
     // source 0 .. nnear (+1 for the tile itself when the lists leave it out)
@@ -549,46 +559,60 @@ __global__ void k_ms_link(EngineDev E, int only, int prec) {
         if (shk != kShiftNone) apply_shift(shk, F.Lhi, F.Llo, h, l);
         const int q0 = tile_slot0(S, J), nJ = tile_end(S, J) - q0;
         const int qs = q0 + lane;
-        float4 vq = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lane < nJ) vq = make_float4((float)v[qs], (float)v[N + qs], (float)v[2 * N + qs], 0.f);
+        const bool pass = lane < nJ && (F.wrap || near_box(box, h, reach2));
+        const unsigned mp = __ballot_sync(0xffffffffu, pass);
+        if (!mp) continue;
         __syncwarp();
-        sh[w][lane] = h;
-        sl[w][lane] = l;
-        sv[w][lane] = vq;
+        if (pass) {
+            const int at = __popc(mp & ((1u << lane) - 1u));
+            sh[w][at] = h;
+            sl[w][at] = l;
+            sv[w][at] = make_float4((float)v[qs], (float)v[N + qs], (float)v[2 * N + qs], 0.f);
+            sq[w][at] = qs;
+        }
         __syncwarp();
-        if (!valid) continue;
         const bool Jp = J < S.Tp;
         const bool pp = Ip && Jp;
         const bool coul = pp && S.coulomb != 0;
         const float sfac = (Ip == Jp) ? (float)(S.b + S.c) : (float)(S.b - S.c);
-        for (int k = 0; k < nJ; ++k) {
-            const int q = q0 + k;
-            if (J == I && q <= p) continue;            // each pair of the tile once
-            const float r2 = d2_screen(hi, lo, sh[w][k], sl[w][k], F);
-            if (r2 >= far2) continue;
-            const float g = ex2f_approx(r2 * P.kq);
-            float V = g * fmaf(a, g, sfac);
-            float mag = g * fmaf(a, g, fabsf(sfac));
-            if (coul && (S.coulomb == 2 || r2 < P.rc2)) {
-                const float ri = rsqrtf(r2);
-                const float vc = ex2f_approx(fmaf(r2 * ri, P.kc, P.l2a)) * ri;
-                V += vc;
-                mag += vc;
+        const int nq = __popc(mp);
+        for (int k = 0; k < nq; ++k) {
+            const int q = sq[w][k];
+            bool bound = false;
+            // each pair of the tile with itself once
+            if (valid && (J != I || q > p)) {
+                const float r2 = d2_screen(hi, lo, sh[w][k], sl[w][k], F);
+                if (r2 < far2) {
+                    const float g = ex2f_approx(r2 * P.kq);
+                    float V = g * fmaf(a, g, sfac);
+                    float mag = g * fmaf(a, g, fabsf(sfac));
+                    if (coul && (S.coulomb == 2 || r2 < P.rc2)) {
+                        const float ri = rsqrtf(r2);
+                        const float vc = ex2f_approx(fmaf(r2 * ri, P.kc, P.l2a)) * ri;
+                        V += vc;
+                        mag += vc;
+                    }
+                    const float4 u = sv[w][k];
+                    const float dx = vx - u.x, dy = vy - u.y, dz = vz - u.z;
+                    const float ke = qM * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    const float en = V + ke, band = kMsRel * (mag + ke) + kMsAbs;
+                    // (a Coulomb cutoff inside the nuclear range: its edge is decided in FP64)
+                    const bool cedge = coul && S.coulomb == 1 && fabsf(r2 - P.rc2) < kBand;
+                    if (cedge) bound = ms_bound_exact(S, x, v, p, q, L, hL);
+                    else if (en > band) bound = false;
+                    else if (en < -band && r2 < near2) bound = true;
+                    else bound = ms_bound_exact(S, x, v, p, q, L, hL);
+                }
             }
-            const float4 u = sv[w][k];
-            const float dx = vx - u.x, dy = vy - u.y, dz = vz - u.z;
-            const float ke = qM * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float e = V + ke, band = kMsRel * (mag + ke) + kMsAbs;
-            // (a Coulomb cutoff inside the nuclear range: its edge is decided in FP64)
-            const bool cedge = coul && S.coulomb == 1 && fabsf(r2 - P.rc2) < kBand;
-            bool bound;
-            if (cedge) bound = ms_bound_exact(S, x, v, p, q, L, hL);
-            else if (e > band) bound = false;
-            else if (e < -band && r2 < near2) bound = true;
-            else bound = ms_bound_exact(S, x, v, p, q, L, hL);
-            if (bound) uf_union(B.parent, p, q, S.uf_limit, &B.stats[7]);
+            const unsigned m = __ballot_sync(0xffffffffu, bound);
+            if (!m) continue;
+            if (ne + 32 > kEB) flush_edges(B, S, buf, ne, lane);
+            if (bound) buf[ne + __popc(m & ((1u << lane) - 1u))] = make_int2(p, q);
+            __syncwarp();
+            ne += __popc(m);
         }
     }
+    if (ne) flush_edges(B, S, buf, ne, lane);
 }
 
 // Per root: smallest original index and component size.
@@ -652,6 +676,7 @@ void launch_mste(const EngineHost& H, cudaStream_t s, int only, int N, int T, in
     k_ms_init<<<n1, 256, 0, s>>>(E, only);
     H.rec("ms_link", s);
     k_ms_link<<<(T + kCW - 1) / kCW, kCW * 32, 0, s>>>(E, only, H.precision);
+    k_cl_union<<<std::min((N + 255) / 256, 148 * 16), 256, 0, s>>>(E, only);
     H.rec("ms_label", s);
     k_ms_root<<<n, 256, 0, s>>>(E, only);
     k_ms_label<<<n, 256, 0, s>>>(E, only);
@@ -659,7 +684,7 @@ void launch_mste(const EngineHost& H, cudaStream_t s, int only, int N, int T, in
     k_cl_count<<<n, 256, 0, s>>>(E, only);
     H.rec("ms_hist", s);
     k_ms_hist<<<n, 256, 0, s>>>(E, only, d_labels_out);
-    H.count(7);
+    H.count(8);
 }
 
 void launch_clusters(const EngineHost& H, cudaStream_t s, int only, int Np, int N, int Tp, int T,

@@ -17,7 +17,7 @@ struct ClusterBufs {
     long long* hist_A;       // [N+1]
     long long* hist_Z;       // [Np+1]
     long long* stats;        // [8]: clusters, free, big, sumA, sumZ; [6] links found; [7] a loop gave up
-    int2* edges;             // [ecap] proton links (slot pairs) found by the link pass
+    int2* edges;             // [ecap] links (slot pairs) found by a link pass, united afterwards
     long long ecap;
     int* count;              // [T] candidate tiles per tile
     int* start;              // [T+1]

@@ -345,6 +345,16 @@ def test_clusters_bit_exact(md, name):
     _check_clusters(s, x, t, L)
 
 
+def test_clusters_beyond_the_link_buffer(md):
+    """Matter dense enough (0.15 protons per fm^3: about 28 proton pairs
+    inside r_pp per proton) that the links found outnumber the link buffer
+    (16 per proton): the link pass unites the pairs beyond it itself.  Labels,
+    histograms and statistics stay bit-exact with the oracle."""
+    x, t, L = cfg_liquid(6000, 0.60, 0.25, 12)
+    s, _ = load(md, x, t, L, 0)
+    _check_clusters(s, x, t, L)
+
+
 def test_clusters_after_dynamics_and_edges(md):
     x, t, L = cfg_drops(3000, 0.30, 0.005, 31)
     s, _ = load(md, x, t, L, 0, T=0.5)
