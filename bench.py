@@ -512,6 +512,15 @@ def run_serve(n_jobs, steps, rate, seed=5):
     for a, d in zip(arrivals, dur):
         t_free = max(a, t_free) + d
     serial_wall = t_free
+    # per size class (the server's stream priorities): worst per-job p99 and median per-job p50
+    classes = {"N<20k": (0, 20000), "20k<=N<100k": (20000, 100000), "N>=100k": (100000, 1 << 40)}
+    by_class = {}
+    for name, (lo, hi) in classes.items():
+        rc = [r for r in ok if lo <= r["N"] < hi]
+        if rc:
+            p50s = sorted(r["step_p50_ms"] for r in rc)
+            by_class[name] = {"jobs": len(rc), "step_p50_ms": round(p50s[len(p50s) // 2], 3),
+                              "step_p99_ms": round(max(r["step_p99_ms"] for r in rc), 3)}
     return {"jobs": n_jobs, "completed": len(ok), "steps_per_job": steps, "arrival_rate_per_s": rate,
             "served": work / wall, "serial": work / serial_wall, "speedup": serial_wall / wall,
             "served_wall_s": wall, "serial_wall_s": serial_wall, "serial_busy_s": float(sum(dur)),
@@ -519,6 +528,7 @@ def run_serve(n_jobs, steps, rate, seed=5):
                     "relaxation included)",
             "step_p50_ms": lat[len(lat) // 2] if lat else None, "step_p99_ms": p99,
             "wait_ms_max": max(r["wait_ms"] for r in ok) if ok else None,
+            "by_size_class": by_class,
             "job_N": [j["N"] for j in jobs],
             "job_step_p99_ms": {int(r["N"]): round(r["step_p99_ms"], 3) for r in ok},
             "job_run_s": {int(r["N"]): round(r["run_ms"] / 1e3, 3) for r in ok},
