@@ -250,7 +250,10 @@ MD_API int md_step_energy(md_system* s, md_energy_t* out);
  * labels [N] (may be NULL): smallest original proton index of the cluster,
  * -1 for a free neutron.  hist_A [N+1], hist_Z [Np+1] (may be NULL): number
  * of clusters with mass number A / charge Z.  Distances are FP64 nearest
- * images; results are exact (bit-identical to a serial FP64 evaluation). */
+ * images; results are exact (bit-identical to a serial FP64 evaluation).
+ * The first cluster call of a system allocates its cluster buffers (about
+ * 160 B per nucleon, plus the candidate tile lists); MD_ENOMEM if that
+ * fails, after which the system stays usable. */
 MD_API int md_clusters(md_system* s, int32_t* labels, int64_t* hist_A, int64_t* hist_Z,
                 md_cluster_stats* stats);
 
