@@ -7,10 +7,11 @@
 // every target over all its sources, Sec. II.B.1).  Work unit: one warp per
 // work item, a part of a 32-particle target tile I's half tile-pair list
 // (each unordered tile pair is listed once): a proton tile gives four items
-// (its near entries with the tile itself, and three parts of its Coulomb-only
-// entries), a neutron tile one; the four warps of a block take the same part
-// of four adjacent tiles.  The item with the near entries first evaluates the
-// tile with itself (broadcast sources, no reaction).  For each listed source
+// (two halves of its near entries, and two of its Coulomb-only entries), a
+// neutron tile one, or two halves of its list in dilute systems; the four
+// warps of a block take the same part of four adjacent tiles.  A tile's
+// first item first evaluates the tile with itself (broadcast sources, no
+// reaction).  For each listed source
 // tile J every lane loads one source (cp.async, two entries in flight), moves
 // it to the periodic image next to I, and tests it against two boxes around
 // the current positions of I's targets 0-15 and 16-31 with the bare cutoffs.
@@ -460,25 +461,38 @@ __device__ __forceinline__ void push(WarpQueues& Q, int q, bool pred, int& cnt, 
     cnt += __popc(m);
 }
 
-// Work item v of a system (see item_index): the near entries of a proton
-// tile with the tile itself, a third of its Coulomb-only entries, or the
-// whole list of a neutron tile with the tile itself.
+// Work item v of a system (see item_index): a part of a proton tile's near
+// entries (the first with the tile itself) or of its Coulomb-only entries, or
+// a part of a neutron tile's list (the first with the tile itself).
 template <bool kWrap, bool kEnergy, int kU>
 __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, int v, WarpQueues& Q) {
     const int lane = threadIdx.x & 31;
     const int Pi = proton_items(S.Tp);
-    int I, c;                      // c: -1 whole list, 0 near part, 1.. Coulomb-only part c
+    SysState* st = S.st;
+    const double L = st->L;
+    int I, c, nparts;              // proton tiles: part c of kPChunks; neutron tiles: part c of nparts
     if (v < Pi) {
         const int b = v / kItemGroup;
         I = (b / kPChunks) * kItemGroup + v % kItemGroup;
         c = b % kPChunks;
+        nparts = kPChunks;
         if (I >= S.Tp) return;     // past the last proton tile of the group
     } else {
-        I = S.Tp + (v - Pi);
-        c = -1;
+        // split: the halves of kItemGroup adjacent tiles side by side; whole
+        // lists: one item per tile, the unused items at the end of the pass
+        const int w = v - Pi;
+        if ((double)S.N < kSplitRho * L * L * L) {
+            const int b = w / kItemGroup;
+            I = S.Tp + (b / kNChunks) * kItemGroup + w % kItemGroup;
+            c = b % kNChunks;
+            nparts = kNChunks;
+        } else {
+            I = S.Tp + w;
+            c = 0;
+            nparts = 1;
+        }
+        if (I >= S.T) return;
     }
-    SysState* st = S.st;
-    const double L = st->L;
     const int N = S.N;
     long long* facc = S.facc;
 
@@ -554,13 +568,18 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
     const int cls0 = (Ip && S.coulomb == 1) ? kPPNuc : kNucSame;
     const int* lst = S.list + (long long)I * S.T;
     const int nl = S.lcount[I], nn = S.lnear[I];
-    int e0 = 0, e1 = nl;
-    if (c == 0) {
-        e1 = nn;
-    } else if (c > 0) {
+    int e0, e1;
+    if (!Ip) {
+        static_assert(kNChunks == 2, "neutron tiles: the whole list or its two halves");
+        e0 = (nparts == 1 || c == 0) ? 0 : nl / 2;
+        e1 = (nparts == 2 && c == 0) ? nl / 2 : nl;
+    } else if (c < kPNear) {
+        e0 = (int)((long long)nn * c / kPNear);
+        e1 = (int)((long long)nn * (c + 1) / kPNear);
+    } else {
         const int nf = nl - nn;
-        e0 = nn + (int)((long long)nf * (c - 1) / (kPChunks - 1));
-        e1 = nn + (int)((long long)nf * c / (kPChunks - 1));
+        e0 = nn + (int)((long long)nf * (c - kPNear) / (kPChunks - kPNear));
+        e1 = nn + (int)((long long)nf * (c - kPNear + 1) / (kPChunks - kPNear));
     }
 
     Totals T;
@@ -586,7 +605,7 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
     // against every particle of the tile, so no reaction is added and the
     // energies count each pair twice.
     float sfx = 0.0f, sfy = 0.0f, sfz = 0.0f;
-    if (c <= 0) {
+    if (c == 0) {
         const float4 hs = (lane & 16) ? X.h1 : X.h0, ls = (lane & 16) ? X.l1 : X.l0;
         Q.dh[lane] = hs;
         Q.dl[lane] = ls;

@@ -91,7 +91,7 @@ struct SysConst {
     int N, Np, T, Tp;        // particles, protons, tiles, proton tiles
     int tile_base;           // first global tile (multiple of kTilesPerBlock)
     int item_base;           // first global force work item (multiple of 4)
-    int n_items;             // force work items: kPChunks per proton tile, 1 per neutron tile
+    int n_items;             // force work items: kPChunks per proton tile, kNChunks per neutron tile
     int nbits;               // spatial-sort bits per axis
     long long bin_base;      // first global bin (2 species x 2^(3 nbits) bins)
     long long nbins;         // bins per species
@@ -209,18 +209,33 @@ struct PersistCtl {
 
 // Force work items of a system.  A proton tile's list holds its near
 // entries (nuclear range) first and its Coulomb-only entries from the back of
-// its region; it gives kPChunks items: item 0 the near entries (and the tile
-// with itself), items 1.. equal parts of the Coulomb-only entries.  A neutron
-// tile is one item.  Proton items come first, item c of kItemGroup adjacent
-// tiles side by side (one block of the force kernel).
+// its region; it gives kPChunks items: items 0 .. kPNear-1 equal parts of the
+// near entries (item 0 also the tile with itself), the others equal parts of
+// the Coulomb-only entries.  A neutron tile gives kNChunks items: in a system
+// below kSplitRho the halves of its list (item 0 with the tile itself), in a
+// denser one the whole list and an empty item (there neutron tiles are light:
+// their entries pass few sources; in clustered, dilute states the tiles inside
+// nuclei are among the heaviest items, and halving them shortens the tail of
+// the pass).  Items c of kItemGroup adjacent tiles sit side by side (one block
+// of the force kernel); proton items come first; with whole neutron lists the
+// unused items are the last ones.
 constexpr int kPChunks = 4;
+constexpr int kPNear = 2;
+constexpr int kNChunks = 2;
+constexpr double kSplitRho = 0.02;      // fm^-3
 constexpr int kItemGroup = 4;
 __host__ __device__ inline int proton_items(int Tp) {
     return (Tp + kItemGroup - 1) / kItemGroup * kItemGroup * kPChunks;
 }
-__host__ __device__ inline int sys_items(int T, int Tp) { return proton_items(Tp) + (T - Tp); }
+__host__ __device__ inline int neutron_items(int Tn) {
+    return (Tn + kItemGroup - 1) / kItemGroup * kItemGroup * kNChunks;
+}
+__host__ __device__ inline int sys_items(int T, int Tp) { return proton_items(Tp) + neutron_items(T - Tp); }
 __host__ __device__ inline int item_index(const SysConst& s, int t, int c) {
-    if (t >= s.Tp) return proton_items(s.Tp) + (t - s.Tp);
+    if (t >= s.Tp) {
+        const int u = t - s.Tp;
+        return proton_items(s.Tp) + ((u / kItemGroup) * kNChunks + c) * kItemGroup + u % kItemGroup;
+    }
     return ((t / kItemGroup) * kPChunks + c) * kItemGroup + t % kItemGroup;
 }
 // Position in tile I's list region of its e-th entry (near entries first).
