@@ -240,30 +240,45 @@ def test_split_trajectory_50_steps_vs_oracle(md):
     """Split precision (FP32 pair arithmetic) over 50 steps from an oracle
     state, 2,000-nucleon liquid, NVE, against the FP64 oracle (Sec. II.A).
     While the trajectories are close (through step 5) positions agree within
-    1e-6 fm and velocities within 1e-6 relative; the total energy agrees
-    within 1e-6 relative through step 50.  The positions then separate
-    exponentially (measured: 1.3e-7 fm after 1 step, 1.5e-6 after 10, 1e-5
-    after 20, 2.7e-3 after 50): the dynamics amplify differences at the FP32
-    rounding level.  The oracle shows the same: started from positions moved
-    by 1e-7 fm (random signs), it separates from its own unperturbed run by
-    the same order after 50 steps.  Beyond the first steps the split mode is
-    therefore compared statistically (test_gpu_statistics)."""
+    1e-6 fm and velocities within 1e-6 relative; the total energy of the two
+    trajectories agrees within 1e-6 relative through step 20.  The positions
+    then separate exponentially (measured: 1.3e-7 fm after 1 step, 1.5e-6
+    after 10, 1e-5 after 20, 2.7e-3 after 50): the dynamics amplify
+    differences at the FP32 rounding level.  The oracle shows the same:
+    started from positions moved by 1e-7 fm (random signs), it separates from
+    its own unperturbed run by the same order after 50 steps.  At step 50 the
+    two runs are therefore different states, whose total energies differ by
+    the integrator's own fluctuation (the oracle's total energy moves by
+    1e-3 relative between steps 20 and 50 of this start); there the energies
+    the GPU records are compared with the oracle's on the GPU's own state,
+    and the separation with the oracle's own amplification.  Beyond the
+    first steps the split mode is compared statistically
+    (test_gpu_statistics)."""
     x, t, L = cfg_liquid(2000, 0.30, 0.080, 21)
     s, v = load(md, x, t, L, 0, T=1.0, thermostat_every=0)
     op = oparams(s)
+
+    def e_oracle(xx, vv):
+        _, (en, ec, _) = oracle.forces(xx, t, L, op)
+        ke = oracle.kinetic(vv)
+        return ke + en + ec, ke + abs(en) + abs(ec)
+
     s.step(5, 0.0)
     g = s.state()
     r5 = oracle.run(x, v, t, L, op, 5)
     assert np.abs(min_img(g["x"] - r5["x"], L)).max() < 1e-6
     assert rel_l2(g["v"], r5["v"]) < 1e-6
-    s.step(45, 0.0)
+    s.step(15, 0.0)
+    e = s.energy()
+    r20 = oracle.run(r5["x"], r5["v"], t, L, op, 15, t=r5["t"], step=r5["step"], F=r5["F"])
+    eo, scale = e_oracle(r20["x"], r20["v"])
+    assert abs(e["KE"] + e["PE_nuc"] + e["PE_coul"] - eo) < 1e-6 * scale
+    s.step(30, 0.0)
     g = s.state()
     e = s.energy()
-    r = oracle.run(r5["x"], r5["v"], t, L, op, 45, t=r5["t"], step=r5["step"], F=r5["F"])
-    _, (en, ec, _) = oracle.forces(r["x"], t, L, op)
-    ke = oracle.kinetic(r["v"])
-    scale = ke + abs(en) + abs(ec)
-    assert abs(e["KE"] + e["PE_nuc"] + e["PE_coul"] - (ke + en + ec)) < 1e-6 * scale
+    eg, scale = e_oracle(g["x"], g["v"])
+    assert abs(e["KE"] + e["PE_nuc"] + e["PE_coul"] - eg) < 1e-6 * scale
+    r = oracle.run(r20["x"], r20["v"], t, L, op, 30, t=r20["t"], step=r20["step"], F=r20["F"])
     d_split = np.abs(min_img(g["x"] - r["x"], L)).max()
     rng = np.random.default_rng(5)
     xp = x + 1e-7 * rng.choice([-1.0, 1.0], x.shape)
