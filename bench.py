@@ -309,9 +309,9 @@ def run_gpu(args):
                                      "candidate_pairs_per_step": cand / K,
                                      "candidate_efficiency": (pairs_nuc + pairs_coul) / max(cand, 1)}},
         "force_code": {"variant": info["force_code"], "tuner_trials": info["force_trials"],
-                       "note": "split force-pass code in use: 4 long unrolled loops, 2 compact, 1 minimal; chosen on "
-                               "the device by timing all three every 500 steps from step 500 (bitwise the same "
-                               "results)"},
+                       "note": "split force-pass code in use: 4 long unrolled loops, 2 compact, 1 minimal, 3 minimal "
+                               "in one-warp blocks; chosen on the device by timing all four every 500 steps from step "
+                               "500 (bitwise the same results)"},
         "tiles": {"count": info["tiles"], "list_entries": info["list_entries"], "rebuilds": info["rebuilds"],
                   "halfext_mean_fm": info["tile_halfext_mean"], "halfext_max_fm": info["tile_halfext_max"],
                   "need_wrap": info["need_wrap"]},
@@ -711,7 +711,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=4.0)
     ap.add_argument("--precision", default="split", choices=["split", "fp64"],
                     help="with --full-steps: split FP32/FP64 (default) or the FP64 mode")
-    ap.add_argument("--force-unroll", type=int, default=None, choices=[0, 1, 2, 4],
+    ap.add_argument("--force-unroll", type=int, default=None, choices=[0, 1, 2, 3, 4],
                     help="with --full-steps: fix the force-pass code variant (md_params.force_unroll)")
     ap.add_argument("--late-pass", action="store_true",
                     help="with --full-steps: one more force pass of the final state in an NVTX range 'late'")

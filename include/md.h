@@ -103,7 +103,9 @@ typedef struct {
                                 (fastest where the far Coulomb field dominates:
                                 dense states); 2 = compact, 1 = minimal (fit the
                                 instruction cache where several pair classes run
-                                at once: clustered, dilute states); 0 (default) =
+                                at once: clustered, dilute states); 3 = minimal,
+                                one warp per block (no warp waits for the others
+                                of a block: items of uneven cost); 0 (default) =
                                 chosen on the device every 500 steps (from step
                                 500 on; the long one before) by timing 4 force
                                 passes of each, in engines of at least 131,072
@@ -130,7 +132,9 @@ typedef struct {
                                 split precision, tile lists and coulomb 0 or 1
                                 (MD_EINVAL otherwise when 1; -1 falls back to
                                 the graph).  It runs the force-pass code
-                                variant force_unroll fixes (0: the long one).
+                                variant force_unroll fixes (0: the long one;
+                                3: the minimal one, its warps in groups of four
+                                as every variant there).
                                 Results are bitwise those of the graph. */
 } md_params;
 
@@ -192,9 +196,10 @@ typedef struct {
                                 the per-tile blocks) / available */
     int64_t verlet_capacity;
     int32_t force_code;      /* code variant of the split force pass now in use:
-                                4 long unrolled loops, 2 compact, 1 minimal
-                                (md_params force_unroll; 0 there: the device
-                                tuner's choice) */
+                                4 long unrolled loops, 2 compact, 1 minimal,
+                                3 minimal in one-warp blocks (md_params
+                                force_unroll; 0 there: the device tuner's
+                                choice) */
     int32_t pad0;
     int64_t force_trials;    /* trials the device tuner has completed */
 } md_info_t;

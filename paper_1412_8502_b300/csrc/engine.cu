@@ -244,8 +244,8 @@ int Engine::add_system(int64_t N, double Yp, double rho, double T, uint64_t seed
     if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
     if (p.coulomb < 0 || p.coulomb > 2) return fail(MD_EINVAL, "coulomb must be 0, 1 or 2");
     if (p.affine != 0 && p.affine != 1) return fail(MD_EINVAL, "affine must be 0 or 1");
-    if (p.force_unroll != 0 && p.force_unroll != 1 && p.force_unroll != 2 && p.force_unroll != 4)
-        return fail(MD_EINVAL, "force_unroll must be 0, 1, 2 or 4");
+    if (p.force_unroll < 0 || p.force_unroll > 4)
+        return fail(MD_EINVAL, "force_unroll must be 0, 1, 2, 3 or 4");
     if (p.list_kind != 0 && p.list_kind != 1) return fail(MD_EINVAL, "list_kind must be 0 or 1");
     if (p.list_kind == 1 && p.precision != MD_PREC_SPLIT)
         return fail(MD_EINVAL, "Verlet lists (list_kind 1) need split precision");
@@ -496,7 +496,7 @@ int Engine::build_tables() {
     E.tune_variants = (precision != MD_PREC_FP64 && ntot >= kVariantMinN && !persistent_) ? 1 : 0;
     {
         const int fu = sys.empty() ? 0 : (int)sys[0]->prm.force_unroll;
-        H_.fixed_var = fu == 2 ? 1 : fu == 1 ? 2 : 0;
+        H_.fixed_var = fu == 2 ? 1 : fu == 1 ? 2 : fu == 3 ? 3 : 0;
     }
     H_.precision = precision;
     H_.any_pp = false;
@@ -585,7 +585,7 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
     const bool multi = split && H_.dev.tune_variants;     // the step selects the force-pass variant
     // otherwise the variant md_params.force_unroll fixes (0: the long one)
     const int fu = sys.empty() ? 0 : (int)sys[0]->prm.force_unroll;
-    const int fixed_var = fu == 2 ? 1 : fu == 1 ? 2 : 0;
+    const int fixed_var = fu == 2 ? 1 : fu == 1 ? 2 : fu == 3 ? 3 : 0;
     if (kind == 0 && persistent_) {
         // the whole step of every system: one persistent launch
         CK(cudaStreamBeginCaptureToGraph(stream_, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -697,7 +697,7 @@ int Engine::build_step_graph(cudaGraph_t& graph, int kind, bool energy) {
             launch_list_build(H_, stream_, false);
         });
         if (rc) return rc;
-        // all three force-pass variants (two return at once), or the fixed one
+        // all force-pass variants (all but one return at once), or the fixed one
         return segment([&] {
             if (split) {
                 launch_force_pre(H_, stream_, fe, -1, false);
@@ -1101,8 +1101,8 @@ int Engine::set_params(int idx, const md_params& p) {
     if (!(p.dt > 0.0) || !(p.r_nuc > 0.0) || !(p.skin > 0.0) || !(p.lambda_s >= 0.0))
         return fail(MD_EINVAL, "dt, r_nuc, skin must be > 0 and lambda_s >= 0");
     if (p.affine != 0 && p.affine != 1) return fail(MD_EINVAL, "affine must be 0 or 1");
-    if (p.force_unroll != 0 && p.force_unroll != 1 && p.force_unroll != 2 && p.force_unroll != 4)
-        return fail(MD_EINVAL, "force_unroll must be 0, 1, 2 or 4");
+    if (p.force_unroll < 0 || p.force_unroll > 4)
+        return fail(MD_EINVAL, "force_unroll must be 0, 1, 2, 3 or 4");
     if (p.precision != MD_PREC_SPLIT && p.precision != MD_PREC_FP64) return fail(MD_EINVAL, "bad precision");
     if (p.sort_bits != 0 && (p.sort_bits < 2 || p.sort_bits > 7)) return fail(MD_EINVAL, "sort_bits in 2..7");
     if (p.list_kind != 0 && p.list_kind != 1) return fail(MD_EINVAL, "list_kind must be 0 or 1");
@@ -1147,7 +1147,7 @@ int Engine::set_params(int idx, const md_params& p) {
         cudaStreamSynchronize(stream_);
         drop_graphs();
     }
-    if (idx == 0) H_.fixed_var = p.force_unroll == 2 ? 1 : p.force_unroll == 1 ? 2 : 0;
+    if (idx == 0) H_.fixed_var = p.force_unroll == 2 ? 1 : p.force_unroll == 1 ? 2 : p.force_unroll == 3 ? 3 : 0;
     if ((h.prm.cond_graph != 0) != (p.cond_graph != 0) || h.prm.force_unroll != p.force_unroll) {   // graph layout
         cudaStreamSynchronize(stream_);
         drop_graphs();
@@ -1322,7 +1322,7 @@ int Engine::info(int idx, md_info_t* out) {
     ForceTune tu{};
     CK(cudaMemcpyAsync(&tu, d_tune_, sizeof(tu), cudaMemcpyDeviceToHost, stream_));
     CK(cudaStreamSynchronize(stream_));
-    static const int code[kVariants] = {4, 2, 1};
+    static const int code[kVariants] = {4, 2, 1, 3};
     const int fu = (int)h.prm.force_unroll;
     out->force_code = H_.dev.tune_variants ? code[tu.sel < 0 || tu.sel >= kVariants ? 0 : tu.sel] : (fu ? fu : 4);
     out->force_trials = tu.trials;

@@ -172,7 +172,7 @@ __device__ __forceinline__ void decide_body(const EngineDev& E, int forced_only,
         // force_unroll, else the tuner's
         ForceTune* tu = E.tune;
         const int fu = E.nsys > 0 ? E.sys[0].force_unroll : 0;
-        const int sel = fu == 4 ? 0 : fu == 2 ? 1 : fu == 1 ? 2 : tu->cur;
+        const int sel = fu == 4 ? 0 : fu == 2 ? 1 : fu == 1 ? 2 : fu == 3 ? 3 : tu->cur;
         tu->sel = sel;
         if (set_var) cudaGraphSetConditional(cond_var, (unsigned)sel);
     }

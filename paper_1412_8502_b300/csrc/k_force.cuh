@@ -721,7 +721,7 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
 // kernel so that the variants do not share one register allocation and code
 // layout (one kernel holding all three made the long variant 1.8% slower).
 // gate: the launch returns at once unless kVar is this step's selection
-// (plain graphs launch all three).  Block 0 records the start of the pass
+// (plain graphs launch all of them).  Block 0 records the start of the pass
 // for the tuner.
 // Global work item g of the split force pass, taken by one warp (queues Q).
 template <bool kEnergy, int kVar>
@@ -749,6 +749,18 @@ __global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS)
     if (blockIdx.x == 0 && threadIdx.x == 0) tu->t_start = global_ns();   // k_force_fix takes the end
     const int g = blockIdx.x * kForceWarps + (threadIdx.x >> 5);
     force_split_item<kEnergy, kVar>(E, only, g, qs[threadIdx.x >> 5]);
+}
+
+// The fourth variant: the minimal code, one warp (work item) per block, 16
+// blocks per SM (registers), so that no warp waits for the others of a block.
+constexpr int kVarOneWarp = 3;
+template <bool kEnergy>
+__global__ void __launch_bounds__(32, 16) k_force_split1(EngineDev E, int only, int gate) {
+    __shared__ WarpQueues qs;
+    ForceTune* tu = E.tune;
+    if (gate && tu->sel != kVarOneWarp) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) tu->t_start = global_ns();
+    force_split_item<kEnergy, 2>(E, only, blockIdx.x, qs);
 }
 
 // ---------------------------------------------------------------- Verlet
@@ -1146,7 +1158,8 @@ void split_variant(const EngineHost& H, cudaStream_t s, int only, int var, bool 
     const int g = gate ? 1 : 0;
     if (var == 0) k_force_split<kEnergy, 0><<<nbi, kForceWarps * 32, 0, s>>>(E, only, g);
     else if (var == 1) k_force_split<kEnergy, 1><<<nbi, kForceWarps * 32, 0, s>>>(E, only, g);
-    else k_force_split<kEnergy, 2><<<nbi, kForceWarps * 32, 0, s>>>(E, only, g);
+    else if (var == 2) k_force_split<kEnergy, 2><<<nbi, kForceWarps * 32, 0, s>>>(E, only, g);
+    else k_force_split1<kEnergy><<<E.nitems, 32, 0, s>>>(E, only, g);
 }
 }  // namespace
 

@@ -148,15 +148,20 @@ struct SysConst {
 // start of the k_force_fix launch that follows it) are summed, and the
 // fastest variant is kept until the next trial.  Each variant is its own
 // kernel: in a step graph a SWITCH node launches the selected one (k_decide
-// sets it); in plain graphs all three are launched and two return at once.  The first trial comes at
-// step kTuneEvery: until then the long variant runs (systems start dense).
+// sets it); in plain graphs all of them are launched and all but one return at
+// once.  The first trial comes at step kTuneEvery: until then the long variant
+// runs (systems start dense).  The fourth variant runs the minimal code with
+// one warp per block, so that a warp whose work item ends frees its slot
+// without waiting for the other warps of a block (faster where items differ
+// much in cost, as in clustered states; slower in dense ones, where the four
+// adjacent tiles of a block share their source tiles in L1).
 constexpr int kTuneEvery = 500;
 constexpr int kTuneSteps = 4;
-constexpr int kVariants = 3;         // long, compact, minimal
+constexpr int kVariants = 4;         // long, compact, minimal, minimal in one-warp blocks
 struct ForceTune {
     unsigned long long t_start;  // start of the running force pass, ns
     unsigned long long t_last;   // duration of the last force pass, ns
-    int cur;                     // tuner: variant to run next: 0 long, 1 compact, 2 minimal
+    int cur;                     // tuner: variant to run next: 0 long, 1 compact, 2 minimal, 3 minimal (one-warp blocks)
     int sel;                     // variant of this step's pass (set by k_decide from cur or force_unroll)
     int phase;                   // 0 idle, 1 + v timing variant v
     int trials;                  // trials completed

@@ -453,13 +453,14 @@ def test_state_round_trip_with_forces(md, precision):
 # --------------------------------------------------------------- code variants
 @pytest.mark.parametrize("name", ["liquid_2000", "drops_3000_dilute", "liquid_4096_yp005"])
 def test_force_code_variants_agree_bitwise(md, name):
-    """The long, compact and minimal code variants of the split force pass do
-    the same arithmetic in the same order: identical forces, energies and
+    """The long, compact and minimal code variants of the split force pass
+    (the minimal one also in one-warp blocks) do the same arithmetic in the
+    same order: identical forces, energies and
     pair counts, before and after steps (force_unroll = 0: the device tuner's
     choice)."""
     x, t, L = PARITY_CASES[name]()
     outs = []
-    for fu in (4, 2, 1, 0):
+    for fu in (4, 2, 1, 3, 0):
         s, _ = load(md, x, t, L, 0, force_unroll=fu, energy_every=1)
         F0, e0 = s.forces(), s.energy()
         s.step(12, 7.5e-5)
@@ -474,7 +475,7 @@ def test_force_code_variants_agree_bitwise(md, name):
 
 def test_force_code_tuner_reports_its_choice(md):
     """Engines of at least 131,072 nucleons select the force-pass variant per
-    step (a SWITCH graph node) and the device tuner times all three every 500
+    step (a SWITCH graph node) and the device tuner times all four every 500
     steps from step 500: the trial runs every variant and the trajectory is
     bitwise that of the fixed long variant.  Smaller engines run the variant
     force_unroll fixes (the long one by default)."""
@@ -486,19 +487,19 @@ def test_force_code_tuner_reports_its_choice(md):
         assert s.info()["force_trials"] == 0 and s.info()["force_code"] == 4     # long until step 500
         s.step(510, 7.5e-5)                  # the trial: steps 501-512, four passes of each variant
         info = s.info()
-        assert info["force_trials"] == (1 if fu == 0 else 0) and info["force_code"] in (1, 2, 4)
+        assert info["force_trials"] == (1 if fu == 0 else 0) and info["force_code"] in (1, 2, 3, 4)
         outs.append(s.state(f=True))
         s.close()
     for k in ("x", "v", "f"):
         assert np.array_equal(outs[0][k], outs[1][k])
     x, t, L = PARITY_CASES["liquid_2000"]()
-    for fu in (0, 1, 2, 4):
+    for fu in (0, 1, 2, 3, 4):
         s, _ = load(md, x, t, L, 0, force_unroll=fu)
         s.step(520, 0.0)
         assert s.info()["force_code"] == (fu or 4) and s.info()["force_trials"] == 0
         s.close()
     with pytest.raises(md.MDError):
-        load(md, x, t, L, 0, force_unroll=3)
+        load(md, x, t, L, 0, force_unroll=5)
 
 
 def test_step_async_matches_step(md):
