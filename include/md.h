@@ -109,7 +109,8 @@ typedef struct {
                                 chosen on the device every 500 steps (from step
                                 500 on; the long one before) by timing 4 force
                                 passes of each, in engines of at least 131,072
-                                nucleons (smaller ones run the long variant).
+                                nucleons (smaller ones, and persistent steps,
+                                run the minimal variant).
                                 Results are bitwise the same. */
     int64_t uf_iter_limit;   /* bound on the iterations of every union-find loop
                                 of the cluster analyses (a root walk, or the
@@ -132,9 +133,9 @@ typedef struct {
                                 split precision, tile lists and coulomb 0 or 1
                                 (MD_EINVAL otherwise when 1; -1 falls back to
                                 the graph).  It runs the force-pass code
-                                variant force_unroll fixes (0: the long one;
-                                3: the minimal one, its warps in groups of four
-                                as every variant there).
+                                variant force_unroll fixes (0 and 3: the
+                                minimal one, its warps in groups of four as
+                                every variant there).
                                 Results are bitwise those of the graph. */
 } md_params;
 

@@ -478,7 +478,7 @@ def test_force_code_tuner_reports_its_choice(md):
     step (a SWITCH graph node) and the device tuner times all four every 500
     steps from step 500: the trial runs every variant and the trajectory is
     bitwise that of the fixed long variant.  Smaller engines run the variant
-    force_unroll fixes (the long one by default)."""
+    force_unroll fixes (the minimal one by default)."""
     x, t, L = cfg_liquid(135000, 0.40, 0.080, 12)
     outs = []
     for fu in (4, 0):
@@ -496,7 +496,7 @@ def test_force_code_tuner_reports_its_choice(md):
     for fu in (0, 1, 2, 3, 4):
         s, _ = load(md, x, t, L, 0, force_unroll=fu)
         s.step(520, 0.0)
-        assert s.info()["force_code"] == (fu or 4) and s.info()["force_trials"] == 0
+        assert s.info()["force_code"] == (fu or 1) and s.info()["force_trials"] == 0
         s.close()
     with pytest.raises(md.MDError):
         load(md, x, t, L, 0, force_unroll=5)
