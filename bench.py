@@ -362,18 +362,18 @@ def cell_build_roofline(kt, rebuilds, N, info, peaks):
     alg = 232.0 * N + 12.0 * bins
     per = ms / rebuilds
     gbs = alg / (per * 1e-3) / 1e9
-    # the survey's accounting of the minimum a counting sort must move: read x (24 B) + type,
+    # the minimum a counting sort must move: read x (24 B) + type,
     # write a key (4 B), read x + key again and write the sorted x, local coordinates, type and
     # id (about 100 B per particle in all)
-    survey = 100.0 * N
+    minimal = 100.0 * N
     # DRAM bytes per rebuild measured by ncu on the 307,200 case (profiles/step_kernels_md307200_ncu.md:
     # hist 9.50, two scan passes 4.21, scatter 3.35, move 22.67, tiles 7.43 MB), scaled by N
     dram = 47.16e6 * N / 307200.0
     return {"bound": "hbm", "rebuilds": rebuilds, "ms_per_rebuild": per, "bytes_per_rebuild": alg,
             "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
-            "frac_survey_bytes": survey / (per * 1e-3) / 1e9 / peaks["hbm_gbs"],
+            "frac_min_bytes": minimal / (per * 1e-3) / 1e9 / peaks["hbm_gbs"],
             "frac_ncu_dram_bytes": dram / (per * 1e-3) / 1e9 / peaks["hbm_gbs"],
-            "note": "frac: the builder's own 232 B per particle + 12 B per bin; frac_survey_bytes: the minimum "
+            "note": "frac: the builder's own 232 B per particle + 12 B per bin; frac_min_bytes: the minimum "
                     "of about 100 B per particle; frac_ncu_dram_bytes: the DRAM bytes ncu measured for these "
                     "kernels (the rest of their traffic is served by L2). Six chained kernels of 4-16 us: "
                     "launch latency and the dependent gathers of the move bound it, not HBM bandwidth"}
