@@ -263,9 +263,9 @@ def run_gpu(args):
         wall = time.perf_counter() - t0
         e2e = {"value": N * Ke / wall, "unit": "nucleon-steps/s", "h2d_bytes_per_step": 3 * 24 * N,
                "d2h_bytes_per_step": 3 * 24 * N + 8 * 9, "steps": Ke,
-               "note": "per step: md_set_state from pinned host x, v, f (restores the cached forces: "
-                       "re-sort and list rebuild, no force pass); md_step; md_get_state of x, v, f to pinned "
-                       "host; md_step_energy"}
+               "note": "per step: md_set_state from pinned host x, v, f (restores the cached forces, no "
+                       "force pass; the state goes into the current particle order and the rebuild rule "
+                       "decides on the tiles); md_step; md_get_state of x, v, f to pinned host; md_step_energy"}
 
     if rank != 0:
         replicas.finalize()

@@ -286,7 +286,11 @@ MD_API int md_get_state(md_system* s, md_state_view* view);
  * x is wrapped into [0, L).  With f == NULL the forces are re-evaluated at
  * the new state (box side L); otherwise f (evaluated with box side L_F, as
  * md_get_state returns them) become the cached forces and no force pass
- * runs.  Used for resume and for parity checks. */
+ * runs; the state then goes into the system's current particle order, and
+ * with the same box side its tiles and pair lists are kept unless the
+ * rebuild rule (displacement since the last rebuild) asks for new ones, so a
+ * state saved from the system and loaded back continues bitwise as if it
+ * had not left.  Used for resume and for parity checks. */
 MD_API int md_set_state(md_system* s, const md_state_view* view);
 
 MD_API int md_get_info(const md_system* s, md_info_t* info);

@@ -1087,17 +1087,29 @@ int Engine::set_state(int idx, const md_state_view* v) {
     if (v->f)
         CK(cudaMemcpyAsync(h.d_stage + 6 * h.N, v->f, sizeof(double) * 3 * h.N, cudaMemcpyHostToDevice, stream_));
     CK(cudaMemcpyAsync(d_clock_, clock, sizeof(clock), cudaMemcpyHostToDevice, stream_));
-    launch_set_clock(H_, stream_, idx, d_clock_);
-    launch_scatter_state(H_, stream_, idx, h.d_stage, h.d_stage + 3 * h.N);
     int rc;
-    if (v->f) {
-        // the caller's forces: sort into tiles, then place them by particle id
+    if (v->f && !h.dirty) {
+        // the caller's forces: the state goes into the current slot order and
+        // the rebuild rule decides (a state saved from this system keeps its
+        // tiles), then the forces are placed by particle id
+        launch_load_sorted(H_, stream_, idx, h.d_stage, h.d_stage + 3 * h.N, v->L);
+        launch_set_clock(H_, stream_, idx, d_clock_, true);
+        launch_rebuild(H_, stream_, 0, idx);
+        launch_scatter_forces(H_, stream_, idx, h.d_stage + 6 * h.N);
+        CK(cudaGetLastError());
+        h.dirty = false;
+    } else if (v->f) {
+        // (a system whose tiles are not current: sort into tiles from the original order)
+        launch_set_clock(H_, stream_, idx, d_clock_);
+        launch_scatter_state(H_, stream_, idx, h.d_stage, h.d_stage + 3 * h.N);
         launch_rebuild(H_, stream_, 1, idx);
         launch_scatter_forces(H_, stream_, idx, h.d_stage + 6 * h.N);
         CK(cudaGetLastError());
         h.dirty = false;
-    } else if ((rc = refresh(idx))) {
-        return rc;
+    } else {
+        launch_set_clock(H_, stream_, idx, d_clock_);
+        launch_scatter_state(H_, stream_, idx, h.d_stage, h.d_stage + 3 * h.N);
+        if ((rc = refresh(idx))) return rc;
     }
     h.host_step = v->step;
     h.xi = v->xi_dot;

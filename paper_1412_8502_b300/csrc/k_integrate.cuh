@@ -513,6 +513,46 @@ __global__ void k_scatter_state(EngineDev E, int only, const double* ix, const d
     S.id[0][p] = p;
 }
 
+// A loaded state (AoS, original order) placed in the current slot order:
+// slot p takes particle id[p].  Its displacement since the last rebuild grows
+// by the move from the position it replaces (nearest image), and the maximum
+// goes to the rebuild decision that follows, so the tiles and lists are kept
+// while the rebuild rule allows it (a state saved from this system and loaded
+// back keeps them).  With another box side than the current one (Lnew) the
+// rebuild is forced.
+__global__ void k_load_sorted(EngineDev E, int only, const double* ix, const double* iv, double Lnew) {
+    Slot o;
+    if (!slot_of(E, only, o)) return;        // whole block: systems start on block boundaries
+    const SysConst& S = E.sys[o.s];
+    SysState* st = S.st;
+    const int lane = threadIdx.x & 31;
+    const double L = st->L;
+    const bool same_box = Lnew == L;
+    float d2 = 0.0f;
+    if (o.valid) {
+        const int c = st->cur, N = S.N, p = o.p;
+        const int i = S.id[c][p];
+        const float4 prev = S.xhi[o.t * kTile + lane];
+        double xs[3];
+        for (int a = 0; a < 3; ++a) {
+            const double xn = wrap_box(ix[3 * i + a], Lnew);
+            double d = xn - S.x[c][a * N + p];
+            if (d > 0.5 * Lnew) d -= Lnew;
+            else if (d < -0.5 * Lnew) d += Lnew;
+            const float dd = S.disp[a * N + p] + (float)d;
+            S.disp[a * N + p] = dd;
+            d2 = fmaf(dd, dd, d2);
+            S.x[c][a * N + p] = xn;
+            S.v[c][a * N + p] = iv[3 * i + a];
+            xs[a] = xn;
+        }
+        if (same_box) write_xt_moved(S, o.t, lane, xs, L, narrow_trunc(L), prev);
+    }
+    d2 = warp_max(d2);
+    block_atomic_max(&st->maxdisp2, d2);
+    if (!same_box && threadIdx.x == 0) st->force_rebuild = 1;
+}
+
 // Load caller forces (AoS, original order) into the cached force array of
 // the current slot order (after the rebuild that follows a loaded state):
 // slot p holds particle id[p].
@@ -529,7 +569,10 @@ __global__ void k_scatter_forces(EngineDev E, int only, const double* f) {
 
 // Clock and bookkeeping of a loaded state: d_clock = {L, L_base, t, t_base,
 // xi_dot, step, L_F}.  Slot order becomes the identity; forces are stale.
-__global__ void k_set_clock(EngineDev E, int only, const double* c) {
+// keep_tiles: the state was loaded into the current slot order (k_load_sorted)
+// and the rebuild rule decides; otherwise it sits in the original order and a
+// rebuild follows.
+__global__ void k_set_clock(EngineDev E, int only, const double* c, int keep_tiles) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= E.nsys || (only >= 0 && s != only)) return;
     SysState* st = E.sys[s].st;
@@ -540,14 +583,16 @@ __global__ void k_set_clock(EngineDev E, int only, const double* c) {
     st->xi_dot = c[4];
     st->step = (int64_t)c[5];
     st->L_F = c[6];
-    st->cur = 0;
-    st->cur_next = 0;
-    st->force_rebuild = 1;
-    st->maxdisp2 = 0u;
     st->vscale = 1.0;
     st->xscale = 1.0;
     st->have_energy = 0;
-    st->last_build = st->step;
+    if (!keep_tiles) {
+        st->cur = 0;
+        st->cur_next = 0;
+        st->force_rebuild = 1;
+        st->maxdisp2 = 0u;
+        st->last_build = st->step;
+    }
 }
 
 // The cached forces were just re-evaluated at the current box side (a
@@ -631,9 +676,9 @@ void launch_gather(const EngineHost& H, cudaStream_t s, int only, double* ox, do
     H.count(1);
 }
 
-void launch_set_clock(const EngineHost& H, cudaStream_t s, int only, const double* d_clock) {
+void launch_set_clock(const EngineHost& H, cudaStream_t s, int only, const double* d_clock, bool keep_tiles) {
     const EngineDev& E = H.dev;
-    k_set_clock<<<(E.nsys + 127) / 128, 128, 0, s>>>(E, only, d_clock);
+    k_set_clock<<<(E.nsys + 127) / 128, 128, 0, s>>>(E, only, d_clock, keep_tiles ? 1 : 0);
     H.count(1);
 }
 
@@ -652,6 +697,13 @@ void launch_set_rate(const EngineHost& H, cudaStream_t s, int only, double xi_do
 void launch_scatter_state(const EngineHost& H, cudaStream_t s, int only, const double* ix, const double* iv) {
     const EngineDev& E = H.dev;
     k_scatter_state<<<nblk(E), kBlock, 0, s>>>(E, only, ix, iv);
+    H.count(1);
+}
+
+void launch_load_sorted(const EngineHost& H, cudaStream_t s, int only, const double* ix, const double* iv,
+                        double L) {
+    const EngineDev& E = H.dev;
+    k_load_sorted<<<nblk(E), kBlock, 0, s>>>(E, only, ix, iv, L);
     H.count(1);
 }
 

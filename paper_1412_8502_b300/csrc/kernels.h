@@ -73,8 +73,11 @@ void launch_energy_now(const EngineHost& H, cudaStream_t s, int only, double* d_
 void launch_gather(const EngineHost& H, cudaStream_t s, int only, double* ox, double* ov, double* of,
                    int8_t* otype);
 void launch_scatter_state(const EngineHost& H, cudaStream_t s, int only, const double* ix, const double* iv);
+void launch_load_sorted(const EngineHost& H, cudaStream_t s, int only, const double* ix, const double* iv,
+                        double L);
 void launch_scatter_forces(const EngineHost& H, cudaStream_t s, int only, const double* iforce);
-void launch_set_clock(const EngineHost& H, cudaStream_t s, int only, const double* d_clock);
+void launch_set_clock(const EngineHost& H, cudaStream_t s, int only, const double* d_clock,
+                      bool keep_tiles = false);
 void launch_set_rate(const EngineHost& H, cudaStream_t s, int only, double xi_dot);
 // After a force re-evaluation outside a step: L_F = L.
 void launch_mark_forces(const EngineHost& H, cudaStream_t s, int only);
