@@ -288,9 +288,9 @@ MD_API int md_get_state(md_system* s, md_state_view* view);
  * md_get_state returns them) become the cached forces and no force pass
  * runs; the state then goes into the system's current particle order, and
  * with the same box side its tiles and pair lists are kept unless the
- * rebuild rule (displacement since the last rebuild) asks for new ones, so a
- * state saved from the system and loaded back continues bitwise as if it
- * had not left.  Used for resume and for parity checks. */
+ * rebuild rule (displacement since the last rebuild, steps since it) asks
+ * for new ones: a state saved from the system and loaded back keeps its
+ * tiles.  Used for resume and for parity checks. */
 MD_API int md_set_state(md_system* s, const md_state_view* view);
 
 MD_API int md_get_info(const md_system* s, md_info_t* info);
