@@ -63,9 +63,11 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 
 enum PairClass { kPPNuc = 0, kPPCoul = 1, kNucCross = 2, kNucSame = 3 };
 
-// Three code variants of the split force pass, chosen per system and step:
-// long unrolled loops (kULong: rotated blocks 4 steps, the tile with itself
-// 8 sources), compact (2 and 2) and minimal (1 and 2).  Where the far
+// Code variants of the split force pass, chosen per system and step: long
+// unrolled loops (kULong: rotated blocks 4 steps, the tile with itself 8
+// sources), compact (2 and 2) and minimal (1 and 2), the last also in blocks
+// of one warp (k_force_split1: a warp whose item ends frees its slot without
+// waiting for the other warps of a block).  Where the far
 // Coulomb field dominates (dense states), one block kind runs on most warps
 // and the long loops issue best; where nuclear pairs are a large part of the
 // work (clustered, dilute states), warps of one SM run several block kinds
