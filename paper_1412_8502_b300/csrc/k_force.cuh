@@ -398,11 +398,12 @@ __device__ __forceinline__ void n3_block(const WarpQueues& Q, int n, int lane, c
     T.f1y += f1y;
     T.f1z += f1z;
     if (kEnergy) {
-        T.ken.add(e.en);
-        T.kec.add(e.ec);
+        // a class without a term adds nothing to that term's sums
+        if (kClass != kPPCoul) T.ken.add(e.en);
+        if (kClass == kPPNuc || kClass == kPPCoul) T.kec.add(e.ec);
         T.kw.add(e.w);
-        T.nn += (int)e.nn;
-        T.nc += (int)e.nc;
+        if (kClass != kPPCoul) T.nn += (int)e.nn;
+        if (kClass == kPPNuc || kClass == kPPCoul) T.nc += (int)e.nc;
     }
     T.cand += n * kTile;
 }
@@ -566,8 +567,15 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
         }
         __syncwarp();
     }
-    const bool Ip = I < S.Tp;
-    const int cls0 = (Ip && S.coulomb == 1) ? kPPNuc : kNucSame;
+    // The system's constants the entry loop needs, read once: the loop's
+    // stores and atomics would otherwise have them loaded again for every
+    // entry (3% of the dense pass).
+    const int Tp = S.Tp, Tl = S.T;
+    const bool Ip = I < Tp;
+    const bool ppc = Ip && S.coulomb == 1;     // proton tile, Coulomb term on the lists
+    const int cls0 = ppc ? kPPNuc : kNucSame;
+    const float4* const xhi_g = S.xhi;
+    const float4* const xlo_g = S.xlo;
     const int* lst = S.list + (long long)I * S.T;
     const int nl = S.lcount[I], nn = S.lnear[I];
     int e0, e1;
@@ -591,12 +599,12 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
     // (lane 0 stores them), then this lane's source coordinates (cp.async;
     // the low parts only when the nuclear term is reachable).
     auto stage = [&](int e) {
-        const int slot = (e - e0) % kStages;
-        const int ent = lst[list_pos(S, e, nn)];
+        const int slot = (int)((unsigned)(e - e0) % kStages);
+        const int ent = lst[e < nn ? e : Tl - 1 - (e - nn)];
         const int J = ent & kJMask;
         if (lane == 0) Q.sJ[slot] = ent;
-        cp_async16(&Q.sh[slot][lane], &S.xhi[J * kTile + lane]);
-        if ((ent & kNucBit) || !(Ip && J < S.Tp && S.coulomb == 1)) cp_async16(&Q.sl[slot][lane], &S.xlo[J * kTile + lane]);
+        cp_async16(&Q.sh[slot][lane], &xhi_g[J * kTile + lane]);
+        if ((ent & kNucBit) || !(ppc && J < Tp)) cp_async16(&Q.sl[slot][lane], &xlo_g[J * kTile + lane]);
     };
     for (int d = 0; d < kStages - 1; ++d) {
         if (e0 + d < e1) stage(e0 + d);
@@ -633,14 +641,14 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
         cp_async_commit();
         cp_async_wait<kStages - 1>();
         __syncwarp();
-        const int slot = (e - e0) % kStages;
+        const int slot = (int)((unsigned)(e - e0) % kStages);
         const int tag = Q.sJ[slot];
         const int Jk = tag & kJMask;
         const int shk = (tag >> kShiftPos) & 63;
         const bool nucflag = (tag & kNucBit) != 0;
         float4 h = Q.sh[slot][lane];
-        const bool Jp = Jk < S.Tp;
-        const bool farc = Ip && Jp && S.coulomb == 1 && !nucflag;   // Coulomb-only entry
+        const bool Jp = Jk < Tp;
+        const bool farc = ppc && Jp && !nucflag;   // Coulomb-only entry
         float4 l = farc ? make_float4(0.f, 0.f, 0.f, 0.f) : Q.sl[slot][lane];
         __syncwarp();
         const bool src_ok = h.x != kPad;
@@ -667,7 +675,7 @@ __device__ __forceinline__ void force_item(const SysConst& S, const PairF& P, in
         if (farc) {                // Coulomb-only entry: every source goes to PPC or nowhere
             push(Q, 1, src_ok && d2 < Rc2, c1, lane, h, l);
             if (c1 >= kTile) drain<kWrap, kEnergy, kU>(Q, 1, kPPCoul, c1, lane, X, C, T, facc, N);
-        } else if (Ip && Jp && S.coulomb == 1) {
+        } else if (ppc && Jp) {
             const bool nuc = src_ok && d2 < Rn2;
             push(Q, 0, nuc, c0, lane, h, l);
             push(Q, 1, src_ok && !nuc && d2 < Rc2, c1, lane, h, l);
