@@ -181,6 +181,7 @@ __device__ __forceinline__ void decide_body(const EngineDev& E, int forced_only,
 __global__ void k_decide(EngineDev E, int forced_only, int only, cudaGraphConditionalHandle cond_cell,
                          cudaGraphConditionalHandle cond_list, int set_cond, cudaGraphConditionalHandle cond_var,
                          int set_var) {
+    griddep_wait();
     decide_body(E, forced_only, only, cond_cell, cond_list, set_cond, cond_var, set_var);
 }
 
@@ -210,7 +211,10 @@ __device__ __forceinline__ void hist_body(const EngineDev& E, int bx) {
     atomicAdd(&E.hist[S.bin_base + k], 1u);
 }
 
-__global__ void k_hist(EngineDev E) { hist_body(E, blockIdx.x); }
+__global__ void k_hist(EngineDev E) {
+    griddep_wait();
+    hist_body(E, blockIdx.x);
+}
 
 // ---------------------------------------------------------------- bin scan
 // Exclusive scan of hist over all systems' bins in two passes: the count of
@@ -244,6 +248,7 @@ __device__ __forceinline__ void store8(unsigned* a, long long base, long long n,
 }
 
 __global__ void k_scan_reduce(EngineDev E) {
+    griddep_wait();
     if (!*E.any_rebuild) return;
     __shared__ unsigned sm[33];
     const long long base = (long long)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
@@ -266,6 +271,7 @@ __device__ __forceinline__ unsigned chunk_offset(const EngineDev& E, int vb, uns
 }
 
 __global__ void k_scan_bins(EngineDev E) {
+    griddep_wait();
     if (!*E.any_rebuild) return;
     __shared__ unsigned sm[33];
     const unsigned off = chunk_offset(E, blockIdx.x, sm);
@@ -304,7 +310,10 @@ __device__ __forceinline__ void scatter_body(const EngineDev& E, int bx) {
     S.slot[pos] = p;
 }
 
-__global__ void k_scatter(EngineDev E) { scatter_body(E, blockIdx.x); }
+__global__ void k_scatter(EngineDev E) {
+    griddep_wait();
+    scatter_body(E, blockIdx.x);
+}
 
 // Destination of slot q's particle: its bin start plus the number of
 // particles of the same bin with a smaller previous slot index (stable,
@@ -341,7 +350,10 @@ __device__ __forceinline__ void move_body(const EngineDev& E, int bx) {
     S.id[cn][d] = S.id[c][j];
 }
 
-__global__ void k_move(EngineDev E) { move_body(E, blockIdx.x); }
+__global__ void k_move(EngineDev E) {
+    griddep_wait();
+    move_body(E, blockIdx.x);
+}
 
 // ---------------------------------------------------------------- tiles
 // Warp per tile: bounding box, FP64 origin (box centre), FP32 local
@@ -435,7 +447,10 @@ __device__ __forceinline__ void tiles_body(const EngineDev& E, int bx) {
     }
 }
 
-__global__ void k_tiles(EngineDev E) { tiles_body(E, blockIdx.x); }
+__global__ void k_tiles(EngineDev E) {
+    griddep_wait();
+    tiles_body(E, blockIdx.x);
+}
 
 // ---------------------------------------------------------------- lists
 // FP32 test "bounding boxes of I and J (nearest image) closer than R".
@@ -547,7 +562,10 @@ __device__ __forceinline__ void super_body(const EngineDev& E, int bx) {
                                      0.5f * (hi[2] - lo[2]) * (1.0f + 1e-6f) + 1e-4f, 0.f);
 }
 
-__global__ void k_super(EngineDev E) { super_body(E, blockIdx.x); }
+__global__ void k_super(EngineDev E) {
+    griddep_wait();
+    super_body(E, blockIdx.x);
+}
 
 // Force lists in one pass: tile I's entries go to list[I*T ...], its count
 // to lcount[I] (the list buffer holds T entries per tile, the worst case).
@@ -650,7 +668,10 @@ __device__ __forceinline__ void lbuild_body(const EngineDev& E, int half, int bx
     }
 }
 
-__global__ void k_lbuild(EngineDev E, int half) { lbuild_body(E, half, blockIdx.x); }
+__global__ void k_lbuild(EngineDev E, int half) {
+    griddep_wait();
+    lbuild_body(E, half, blockIdx.x);
+}
 
 // Per-particle Verlet lists (list_kind 1), built from the full tile-pair
 // lists: one block of kVB warps per tile I; lane l keeps every particle j of
@@ -666,6 +687,7 @@ __global__ void k_lbuild(EngineDev E, int half) { lbuild_body(E, half, blockIdx.
 constexpr int kVB = 4;
 
 __global__ void __launch_bounds__(kVB * 32) k_vbuild(EngineDev E) {
+    griddep_wait();
     __shared__ float4 sh[kVB][kTile], sl[kVB][kTile];
     __shared__ int cnts[kVB][kTile];
     __shared__ long long s_base;
@@ -882,8 +904,8 @@ void launch_decide(const EngineHost& H, cudaStream_t s, int forced_only, int onl
                    cudaGraphConditionalHandle cond_cell, cudaGraphConditionalHandle cond_list, bool set_cond,
                    cudaGraphConditionalHandle cond_var, bool set_var) {
     H.rec("decide", s);
-    k_decide<<<1, 1024, 0, s>>>(H.dev, forced_only, only, cond_cell, cond_list, set_cond ? 1 : 0, cond_var,
-                                set_var ? 1 : 0);
+    launch_dep(k_decide, 1, 1024, s, H.dev, forced_only, only, cond_cell, cond_list, set_cond ? 1 : 0, cond_var,
+               set_var ? 1 : 0);
     H.count(1);
 }
 
@@ -894,16 +916,16 @@ void launch_cell_build(const EngineHost& H, cudaStream_t s, bool rec) {
     const int nb = (E.ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
     const int nscan = (int)((E.nbins_total + kScanChunk - 1) / kScanChunk);
     if (rec) H.rec("hist", s);
-    k_hist<<<nb, kBlock, 0, s>>>(E);
+    launch_dep(k_hist, nb, kBlock, s, E);
     if (rec) H.rec("scan", s);
-    k_scan_reduce<<<nscan, 1024, 0, s>>>(E);
-    k_scan_bins<<<nscan, 1024, 0, s>>>(E);
+    launch_dep(k_scan_reduce, nscan, 1024, s, E);
+    launch_dep(k_scan_bins, nscan, 1024, s, E);
     if (rec) H.rec("scatter", s);
-    k_scatter<<<nb, kBlock, 0, s>>>(E);
+    launch_dep(k_scatter, nb, kBlock, s, E);
     if (rec) H.rec("move", s);
-    k_move<<<nb, kBlock, 0, s>>>(E);
+    launch_dep(k_move, nb, kBlock, s, E);
     if (rec) H.rec("tiles", s);
-    k_tiles<<<nb, kBlock, 0, s>>>(E);
+    launch_dep(k_tiles, nb, kBlock, s, E);
     H.count(6);
 }
 
@@ -912,12 +934,12 @@ void launch_list_build(const EngineHost& H, cudaStream_t s, bool rec) {
     const EngineDev& E = H.dev;
     const int nb = (E.ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
     if (rec) H.rec("lists", s);
-    k_super<<<nb, kBlock, 0, s>>>(E);
-    k_lbuild<<<nb, kBlock, 0, s>>>(E, H.precision == 0 ? 1 : 0);
+    launch_dep(k_super, nb, kBlock, s, E);
+    launch_dep(k_lbuild, nb, kBlock, s, E, H.precision == 0 ? 1 : 0);
     H.count(2);
     if (H.any_verlet) {
         if (rec) H.rec("verlet_lists", s);
-        k_vbuild<<<E.ntiles, kVB * 32, 0, s>>>(E);
+        launch_dep(k_vbuild, E.ntiles, kVB * 32, s, E);
         H.count(1);
     }
 }

@@ -253,7 +253,10 @@ __device__ __forceinline__ void rescale_body(const EngineDev& E, int only, int b
     }
 }
 
-__global__ void k_rescale(EngineDev E, int only) { rescale_body(E, only, blockIdx.x, gridDim.x); }
+__global__ void k_rescale(EngineDev E, int only) {
+    griddep_wait();
+    rescale_body(E, only, blockIdx.x, gridDim.x);
+}
 
 // ---------------------------------------------------------------- relax
 // Steepest descent (reading of the paper's equilibration from random
@@ -325,11 +328,13 @@ __device__ __forceinline__ void kick_drift_body(const EngineDev& E, int bx) {
 
 template <typename FT>
 __global__ void k_kick_drift(EngineDev E) {
+    griddep_wait();
     kick_drift_body<FT>(E, blockIdx.x);
 }
 
 template <typename FT>
 __global__ void k_kick(EngineDev E) {
+    griddep_wait();
     Slot o;
     if (!slot_of(E, -1, o)) return;
     const SysConst& S = E.sys[o.s];
@@ -380,7 +385,10 @@ __device__ __forceinline__ void kick_fix_body(const EngineDev& E, int bx) {
     block_sum1(S, v2, bx);
 }
 
-__global__ void k_kick_fix(EngineDev E) { kick_fix_body(E, blockIdx.x); }
+__global__ void k_kick_fix(EngineDev E) {
+    griddep_wait();
+    kick_fix_body(E, blockIdx.x);
+}
 
 // One block per system.  energy: also record the energy pass's totals.
 // Force-pass code variant (ForceTune): account the pass of the step just
@@ -453,7 +461,10 @@ __device__ __forceinline__ void finalize_body(const EngineDev& E, int energy, in
     if (s == 0 && E.tune) tune_step(E.tune, st->step, E.tune_variants && S.force_unroll == 0 && S.list_kind == 0);
 }
 
-__global__ void k_finalize(EngineDev E, int energy) { finalize_body(E, energy, blockIdx.x); }
+__global__ void k_finalize(EngineDev E, int energy) {
+    griddep_wait();
+    finalize_body(E, energy, blockIdx.x);
+}
 
 // Energies at the current state (md_energy): KE from the block partials of
 // k_vsum(mode 1), PE from the record of an energy force pass.
@@ -642,21 +653,21 @@ void launch_sd_update(const EngineHost& H, cudaStream_t s) {
 void launch_kick_drift(const EngineHost& H, cudaStream_t s) {
     const EngineDev& E = H.dev;
     H.rec("kick_drift", s);
-    if (H.precision == 1) k_kick_drift<double><<<nblk(E), kBlock, 0, s>>>(E);
-    else k_kick_drift<float><<<nblk(E), kBlock, 0, s>>>(E);
+    if (H.precision == 1) launch_dep(k_kick_drift<double>, nblk(E), kBlock, s, E);
+    else launch_dep(k_kick_drift<float>, nblk(E), kBlock, s, E);
     H.count(1);
 }
 
 void launch_kick_finalize(const EngineHost& H, cudaStream_t s, bool energy, bool fused_fix) {
     const EngineDev& E = H.dev;
     H.rec("kick", s);
-    if (H.precision == 1) k_kick<double><<<nblk(E), kBlock, 0, s>>>(E);
-    else if (fused_fix) k_kick_fix<<<nblk(E), kBlock, 0, s>>>(E);
-    else k_kick<float><<<nblk(E), kBlock, 0, s>>>(E);
+    if (H.precision == 1) launch_dep(k_kick<double>, nblk(E), kBlock, s, E);
+    else if (fused_fix) launch_dep(k_kick_fix, nblk(E), kBlock, s, E);
+    else launch_dep(k_kick<float>, nblk(E), kBlock, s, E);
     H.rec("finalize", s);
-    k_finalize<<<E.nsys, kRed, 0, s>>>(E, energy ? 1 : 0);
+    launch_dep(k_finalize, E.nsys, kRed, s, E, energy ? 1 : 0);
     H.rec("rescale", s);
-    k_rescale<<<std::min(nblk(E), 2 * 148), kBlock, 0, s>>>(E, -1);
+    launch_dep(k_rescale, std::min(nblk(E), 2 * 148), kBlock, s, E, -1);
     H.count(3);
 }
 

@@ -170,6 +170,17 @@ struct ForceTune {
     double acc[kVariants];       // summed durations per variant, ns
 };
 
+// Programmatic dependent launch (launch_dep): wait for the kernel ahead on
+// the stream to finish and its writes to be visible (a no-op for a kernel
+// launched without the attribute), then let the kernel behind be scheduled
+// at once, so that its launch overlaps this one's run (its blocks wait here
+// in turn before touching any data).  The first statement of every kernel
+// launched with launch_dep.
+__device__ __forceinline__ void griddep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
