@@ -195,8 +195,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 constexpr int kForceWarps = 4;   // warps (work items) per block
 static_assert(kForceWarps == kItemGroup, "a block takes one item of each tile of a group");
+// Resident blocks per SM asked of the register allocator: 5 for the passes
+// without energies (96 registers, 12-24 bytes of spills; 409,600 dense
+// start: long 2.127 -> 2.088 ms, compact 2.237 -> 2.104, minimal 2.274 ->
+// 2.137; step 4,000: compact and minimal 8% faster, long 0.7% slower), 4 for
+// the energy passes (at 5 their spills and the smaller L1 beside the queues
+// made them 1-14% slower).
 #ifndef PASTA_FORCE_MIN_BLOCKS
-#define PASTA_FORCE_MIN_BLOCKS 4     // resident blocks per SM asked of the register allocator
+#define PASTA_FORCE_MIN_BLOCKS 4
+#endif
+#ifndef PASTA_FORCE_MIN_BLOCKS_NOENERGY
+#define PASTA_FORCE_MIN_BLOCKS_NOENERGY 5
 #endif
 constexpr int kQ = 2 * kTile;    // queue capacity
 #ifndef PASTA_FORCE_STAGES
@@ -751,7 +760,7 @@ __device__ __forceinline__ void force_split_item(const EngineDev& E, int only, i
 }
 
 template <bool kEnergy, int kVar>
-__global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS)
+__global__ void __launch_bounds__(kForceWarps * 32, kEnergy ? PASTA_FORCE_MIN_BLOCKS : PASTA_FORCE_MIN_BLOCKS_NOENERGY)
     k_force_split(EngineDev E, int only, int gate) {
     __shared__ WarpQueues qs[kForceWarps];
     ForceTune* tu = E.tune;
@@ -762,10 +771,12 @@ __global__ void __launch_bounds__(kForceWarps * 32, PASTA_FORCE_MIN_BLOCKS)
 }
 
 // The fourth variant: the minimal code, one warp (work item) per block, 16
-// blocks per SM (registers), so that no warp waits for the others of a block.
+// blocks per SM with energies, 20 without (96 registers: 0.330 -> 0.310 ms
+// at step 19,000 of the 409,600 expansion; with energies 20 were 3-7% slower),
+// so that no warp waits for the others of a block.
 constexpr int kVarOneWarp = 3;
 template <bool kEnergy>
-__global__ void __launch_bounds__(32, 16) k_force_split1(EngineDev E, int only, int gate) {
+__global__ void __launch_bounds__(32, kEnergy ? 16 : 20) k_force_split1(EngineDev E, int only, int gate) {
     __shared__ WarpQueues qs;
     ForceTune* tu = E.tune;
     if (gate && tu->sel != kVarOneWarp) return;
