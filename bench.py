@@ -455,6 +455,75 @@ def run_batch(steps, cmp_steps=1000):
                     "over compare_steps steps from the state the batched run reached"}
 
 
+def serve_trace_jobs(rng, n_jobs, steps):
+    """The serving workload's jobs: N log-uniform in [2,000, 409,600], Y_p and T
+    from the sweep, density 0.080 falling to U[0.005, 0.02] fm^-3 over the steps."""
+    import numpy as np
+    jobs = []
+    for _ in range(n_jobs):
+        N = int(round(float(np.exp(rng.uniform(np.log(2000), np.log(args_serve_nmax))))))
+        rho_f = float(rng.uniform(0.005, 0.02))
+        xi = ((0.08 / rho_f) ** (1 / 3) - 1.0) / (2.0 * 2000)
+        jobs.append(dict(N=N, Yp=float(rng.choice([0.05, 0.1, 0.2, 0.3, 0.4])), rho=0.08,
+                         T=float(rng.choice([0.5, 0.75, 1.0])), seed=int(rng.integers(1 << 30)),
+                         xi_dot=xi, steps=steps))
+    return jobs
+
+
+def run_serve_split(n_jobs, steps, seed=5):
+    """Where the serving speed-up is bounded: the serving trace's four largest
+    jobs and its other jobs, each set run one job at a time and submitted to
+    the server at once (wall clock, CUDA-synchronised), and the creation
+    (relaxation) and steps of the largest job apart."""
+    import numpy as np
+    import torch
+    from paper_1412_8502_b300 import md
+    jobs = serve_trace_jobs(np.random.default_rng(seed), n_jobs, steps)
+    big = sorted(jobs, key=lambda j: -j["N"])[:4]
+    small = [j for j in jobs if j not in big]
+    p = md.md_params_default()
+
+    def alone(js):
+        t = 0.0
+        for j in js:
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            s = md.System(j["N"], j["Yp"], j["rho"], j["T"], j["seed"], p)
+            s.step(j["steps"], j["xi_dot"])
+            s.energy()
+            s.close()
+            torch.cuda.synchronize()
+            t += time.perf_counter() - t1
+        return t
+
+    def served(js):
+        free, _ = torch.cuda.mem_get_info()
+        sv = md.md_server_create(int(0.5 * free), p)
+        t0 = time.perf_counter()
+        for j in js:
+            md.md_server_submit(sv, j)
+        md.md_server_drain(sv, 1800.0)
+        w = time.perf_counter() - t0
+        md.md_server_destroy(sv)
+        return w
+
+    out = {"mode": "serve split", "big_N": [j["N"] for j in big], "big_alone_s": alone(big),
+           "big_served_s": served(big), "small_N": sorted(j["N"] for j in small),
+           "small_alone_s": alone(small), "small_served_s": served(small)}
+    j = big[0]
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    s = md.System(j["N"], j["Yp"], j["rho"], j["T"], j["seed"], p)
+    torch.cuda.synchronize()
+    out["big0_create_s"] = time.perf_counter() - t1
+    t1 = time.perf_counter()
+    s.step(j["steps"], j["xi_dot"])
+    torch.cuda.synchronize()
+    out["big0_steps_s"] = time.perf_counter() - t1
+    s.close()
+    return out
+
+
 def run_serve(n_jobs, steps, rate, seed=5):
     """Poisson stream of MD jobs into the server (continuous batching, HBM
     budget, device-resident state, interleaved steps); per-step latency from
@@ -465,14 +534,7 @@ def run_serve(n_jobs, steps, rate, seed=5):
     import torch
     from paper_1412_8502_b300 import md
     rng = np.random.default_rng(seed)
-    jobs = []
-    for _ in range(n_jobs):
-        N = int(round(float(np.exp(rng.uniform(np.log(2000), np.log(args_serve_nmax))))))
-        rho_f = float(rng.uniform(0.005, 0.02))
-        xi = ((0.08 / rho_f) ** (1 / 3) - 1.0) / (2.0 * 2000)
-        jobs.append(dict(N=N, Yp=float(rng.choice([0.05, 0.1, 0.2, 0.3, 0.4])), rho=0.08,
-                         T=float(rng.choice([0.5, 0.75, 1.0])), seed=int(rng.integers(1 << 30)),
-                         xi_dot=xi, steps=steps))
+    jobs = serve_trace_jobs(rng, n_jobs, steps)
     gaps = rng.exponential(1.0 / rate, n_jobs)
     arrivals = np.concatenate([[0.0], np.cumsum(gaps[:-1])])
     p = md.md_params_default()
@@ -709,6 +771,8 @@ def main():
     ap.add_argument("--serve-jobs", type=int, default=12)
     ap.add_argument("--serve-steps", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=4.0)
+    ap.add_argument("--serve-split", action="store_true",
+                    help="time the serving trace's four largest jobs and the others apart, alone and served")
     ap.add_argument("--precision", default="split", choices=["split", "fp64"],
                     help="with --full-steps: split FP32/FP64 (default) or the FP64 mode")
     ap.add_argument("--force-unroll", type=int, default=None, choices=[0, 1, 2, 3, 4],
@@ -721,7 +785,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.full_steps:
+    if args.serve_split:
+        line = run_serve_split(args.serve_jobs, args.serve_steps)
+    elif args.full_steps:
         line = run_full(args)
     else:
         line = run_reference(args) if args.impl == "reference" else run_gpu(args)
