@@ -452,19 +452,21 @@ def test_state_round_trip_with_forces(md, precision):
 
 # --------------------------------------------------------------- code variants
 @pytest.mark.parametrize("name", ["liquid_2000", "drops_3000_dilute", "liquid_4096_yp005"])
-def test_force_code_variants_agree_bitwise(md, name):
+@pytest.mark.parametrize("energy_every", [1, 0])
+def test_force_code_variants_agree_bitwise(md, name, energy_every):
     """The long, compact and minimal code variants of the split force pass
     (the minimal one also in one-warp blocks) do the same arithmetic in the
     same order: identical forces, energies and
     pair counts, before and after steps (force_unroll = 0: the device tuner's
-    choice)."""
+    choice), in steps with the energy pass and in steps without it (whose
+    kernels are compiled for more resident blocks)."""
     x, t, L = PARITY_CASES[name]()
     outs = []
     for fu in (4, 2, 1, 3, 0):
-        s, _ = load(md, x, t, L, 0, force_unroll=fu, energy_every=1)
+        s, _ = load(md, x, t, L, 0, force_unroll=fu, energy_every=energy_every)
         F0, e0 = s.forces(), s.energy()
         s.step(12, 7.5e-5)
-        outs.append((F0, e0, s.state(f=True), s.step_energy()))
+        outs.append((F0, e0, s.state(f=True), s.step_energy() if energy_every else None))
         s.close()
     for o in outs[1:]:
         assert np.array_equal(o[0], outs[0][0]) and o[1] == outs[0][1]
